@@ -1,0 +1,136 @@
+"""Pins for the translation operator (Eq. 7), its embedding and the translation (Eq. 5).
+
+* Gegenbauer / plane-wave expansion: the quadrature of e^{-jk k.d} T_L(k, X)
+  over the direction grid reproduces the free-space Green's function
+  e^{-jk|X+d|}/|X+d| (this fixes the l = 0 term, the (-j)^l phase and the
+  Hankel kind of Eq. 7);
+* symmetry: T depends only on k.R^ and |R|, so it is unchanged by any signed
+  axis permutation applied to both k and R, and by k -> -k, R -> -R;
+* near offsets are zero;
+* the FFT route of Eq. 5 equals the brute-force Toeplitz sum.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import directions as dr
+from oracle import operator as op
+from oracle import pipeline as pl
+from oracle import translate as tr
+from oracle.special import legendre_all, spherical_hankel2_all
+
+
+def _T_point(khat, X, k, L):
+    R = np.linalg.norm(X)
+    h = spherical_hankel2_all(L, np.array([k * R]))[:, 0]
+    P = legendre_all(L, np.asarray(khat) @ (X / R))
+    l = np.arange(L + 1)
+    return ((-1j) ** l * (2 * l + 1) * h) @ P
+
+
+@pytest.mark.parametrize("X,d", [((1.0, 1.5, 0.5), (0.1, -0.15, 0.2)),
+                                 ((2.0, 0.0, 0.0), (0.0, 0.25, -0.2)),
+                                 ((0.0, -1.5, 1.5), (0.2, 0.2, 0.2))])
+def test_plane_wave_expansion_reproduces_green_function(X, d):
+    k = 2 * np.pi
+    L = 16
+    kh, w = dr.direction_grid(L, "paper")
+    X, d = np.array(X), np.array(d)
+    # operator_at takes integer offsets scaled by a: use a = 1 and X itself
+    T = np.array([_T_point(kh[p], X, k, L) for p in range(len(kh))])
+    # the same values through operator_at (X on an a = 0.5 grid)
+    Xi = (X / 0.5).round().astype(int)
+    T2 = np.array([op.operator_at(kh[p], Xi[0], Xi[1], Xi[2], 0.5, k, L, near_rule="kappa", kappa=0.0)
+                   for p in range(len(kh))])
+    np.testing.assert_allclose(T2, T, rtol=1e-11)
+    q = (-1j * k / (4 * np.pi)) * np.sum(w * np.exp(-1j * k * (kh @ d)) * T)
+    R = np.linalg.norm(X + d)
+    np.testing.assert_allclose(q, np.exp(-1j * k * R) / R, rtol=1e-8)
+
+
+def test_dropping_monopole_breaks_expansion():
+    # a summation from l = 1 (the printed lower limit) misses the Green's function
+    k, L = 2 * np.pi, 16
+    kh, w = dr.direction_grid(L, "paper")
+    X, d = np.array([1.0, 1.5, 0.5]), np.array([0.1, -0.15, 0.2])
+    T = np.array([_T_point(kh[p], X, k, L) for p in range(len(kh))])
+    h0 = spherical_hankel2_all(0, np.array([k * np.linalg.norm(X)]))[0, 0]
+    q = (-1j * k / (4 * np.pi)) * np.sum(w * np.exp(-1j * k * (kh @ d)) * (T - h0))
+    R = np.linalg.norm(X + d)
+    assert abs(q - np.exp(-1j * k * R) / R) > 1e-2
+
+
+def _signed_perms():
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            M = np.zeros((3, 3), dtype=int)
+            for i, j in enumerate(perm):
+                M[i, j] = signs[i]
+            yield M
+
+
+def test_operator_symmetries():
+    K = (4, 3, 5)
+    kh, _ = dr.direction_grid(4)
+    rng = np.random.default_rng(3)
+    ax = op.offset_axes((6, 6, 6))
+    dx, dy, dz = np.meshgrid(*ax, indexing="ij")
+    for p in rng.choice(len(kh), 4, replace=False):
+        base = op.operator_at(kh[p], dx, dy, dz, 0.5, 2 * np.pi, 4)
+        for M in list(_signed_perms())[::5]:
+            k2 = M @ kh[p]
+            D = np.einsum("ij,jxyz->ixyz", M, np.stack([dx, dy, dz]))
+            rot = op.operator_at(k2, D[0], D[1], D[2], 0.5, 2 * np.pi, 4)
+            np.testing.assert_allclose(rot, base, rtol=1e-12, atol=1e-14)
+        anti = op.operator_at(-kh[p], -dx, -dy, -dz, 0.5, 2 * np.pi, 4)
+        np.testing.assert_allclose(anti, base, rtol=1e-12, atol=1e-14)
+    del K
+
+
+def test_near_offsets_are_zero_and_far_are_not():
+    kh, _ = dr.direction_grid(3)
+    T = op.operator_grid(kh[5], (4, 4, 4), 0.5, 2 * np.pi, 3)
+    c = 3  # index of offset 0
+    assert np.all(T[c - 1:c + 2, c - 1:c + 2, c - 1:c + 2] == 0)
+    far = np.ones(T.shape, bool)
+    far[c - 1:c + 2, c - 1:c + 2, c - 1:c + 2] = False
+    assert np.all(np.abs(T[far]) > 0)
+    Tk = op.operator_grid(kh[5], (4, 4, 4), 0.5, 2 * np.pi, 3, near_rule="kappa")
+    # kappa rule: |Delta|^2 < 12 is near, so (2,2,1) (|.|^2 = 9) is near, (3,2,0) (13) is far
+    assert Tk[c + 2, c + 2, c + 1] == 0 and Tk[c + 3, c + 2, c] != 0
+
+
+def test_embedding_places_offsets_circularly():
+    K, n = (3, 2, 4), (6, 4, 8)
+    g = np.arange(5 * 3 * 7).reshape(5, 3, 7) + 1.0
+    E = op.embed(g, K, n)
+    for ix, dx in enumerate(range(-2, 3)):
+        for iy, dy in enumerate(range(-1, 2)):
+            for iz, dz in enumerate(range(-3, 4)):
+                assert E[dx % 6, dy % 4, dz % 8] == g[ix, iy, iz]
+    assert np.all(E[3, :, :] == 0) and np.all(E[:, 2, :] == 0) and np.all(E[:, :, 4] == 0)
+
+
+@pytest.mark.parametrize("K", [(3, 3, 3), (3, 4, 5), (5, 2, 6), (4, 4, 4)])
+def test_fft_translation_equals_direct_sum(K):
+    plan = pl.Plan(K=K, L=3)
+    kh = plan.directions()
+    rng = np.random.default_rng(sum(K))
+    for p in (0, len(kh) // 3):
+        Tg = op.operator_grid(kh[p], K, plan.a, plan.k0, plan.L)
+        Th = op.fft_operator(kh[p], K, plan.n, plan.a, plan.k0, plan.L)
+        A = rng.standard_normal(K[::-1]) + 1j * rng.standard_normal(K[::-1])
+        Bf = tr.translate_field_fft(Th, A)
+        Bd = tr.translate_field_direct(Tg, A)
+        np.testing.assert_allclose(Bf, Bd, rtol=0, atol=1e-12 * np.abs(Bd).max())
+        # one output box through the pointwise direct sum
+        v = (K[0] - 1, 0, K[2] // 2)
+        f = lambda a, b, c: op.operator_at(kh[p], a, b, c, plan.a, plan.k0, plan.L)
+        np.testing.assert_allclose(tr.translate_point_direct(f, A, v), Bd[v[2], v[1], v[0]],
+                                   rtol=1e-10)
+
+
+def test_embed_extent_rule():
+    assert [pl.embed_extent(k) for k in (2, 3, 4, 5, 8, 12, 17, 32, 33, 64, 128)] == \
+        [4, 8, 8, 16, 16, 32, 64, 64, 128, 128, 256]
