@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the compressed FMM-FFT translation stage on GPUs of one node.
+
+One step = one fmmfft_translate call: every field of the workload (all
+directions, both polarisations, every RHS) translated through Eq. 5 with the
+operator restored from its Tucker-3D compression (Sec. II.C).  The
+uncompressed (plain) translation of the same workload is timed beside it.
+
+Workload (default): 32^3 boxes of edge 0.5 wavelength (k0 = 2 pi), L = 8,
+162 directions (Gauss-Legendre x 18 uniform phi), FFT grid 64^3, Tucker-3D
+HOSVD at tol 1e-4, complex64 fields with FP32 FFTs and restores, 2
+polarisations x 4 RHS of seeded i.i.d. complex Gaussian box spectra
+(synthetic stand-ins for the aggregated fields of a meshed structure).
+
+Metric: Gvoxel.dir/s = n1 n2 n3 * n_dir * 2 * nrhs / t / 1e9 (padded voxels
+times fields translated per second).  Inputs (340 MB) and outputs (340 MB) are
+each larger than the 129 MB L2, so no flush is needed between steps.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] (torchrun for N > 1:
+every rank translates its own copy of the workload, weak scaling, no
+collective on the data path).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "translation Gvoxel·dir/s, compressed vs plain on one GB300, at rel err ≤1e-4"
+UNIT = "Gvoxel·dir/s"
+WL = dict(name="tucker3d_32cube_L8_tol1e-4_2pol_4rhs", K=(32, 32, 32), L=8, a=0.5, k0=2 * math.pi,
+          tol=1e-4, nrhs=4, seed=1002)
+CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
+
+
+def _units(n, n_dir, nrhs):
+    return n[0] * n[1] * n[2] * n_dir * 2 * nrhs
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, one thread, on a bounded sample
+# ---------------------------------------------------------------------------
+def cpu_baseline_child(ndirs: int):
+    """Runs in a subprocess with one BLAS/OpenMP thread.  Times the oracle's
+    compressed translation (Tucker-3D restore of each sampled direction, Fig.
+    3(a), then Eq. 5 for its 8 fields); the oracle's HOSVD set-up is not
+    timed, as the GPU arm's set-up is not."""
+    import numpy as np
+    from oracle import decomp as D
+    from oracle import pipeline as pl
+    from oracle import translate as tr
+    from seeded_inputs import field_spectra_rows
+
+    K, L, nrhs, seed = WL["K"], WL["L"], WL["nrhs"], WL["seed"]
+    plan = pl.Plan(K=K, L=L)
+    dirs = [int(round(i * (plan.n_dir - 1) / max(ndirs - 1, 1))) for i in range(ndirs)]
+    ops = pl.operators(plan, dirs)
+    tks = [D.tucker_hosvd(T, WL["tol"]) for T in ops]
+    nf = 2 * nrhs
+    fields = np.array([p * nf + j for p in dirs for j in range(nf)])
+    A = field_spectra_rows(seed, plan.n_dir, nrhs, K, fields)
+    t0 = time.perf_counter()
+    i = 0
+    for tk in tks:
+        That = D.tucker3d_restore_steps(tk.core, *tk.factors)
+        for _ in range(nf):
+            tr.translate_field_fft(That, A[i])
+            i += 1
+    dt = time.perf_counter() - t0
+    n = plan.n
+    units = n[0] * n[1] * n[2] * len(fields)
+    print(json.dumps({"seconds": dt, "units": units, "fields": int(len(fields)), "dirs": len(dirs)}))
+
+
+def run_cpu_baseline(ndirs: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", str(ndirs)],
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["units"] / d["seconds"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds": d["seconds"],
+            "sample": f"{d['dirs']} of 162 directions x 8 fields (2 pol x 4 RHS) of the 32^3-box L=8 "
+                      f"workload: Tucker-3D restore + FFT translation, FP64 NumPy, 1 thread"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as the reference implementation
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    cpu = None
+    for i in range(args.warmup + args.steps):
+        cpu = run_cpu_baseline(1)
+        if i >= args.warmup:
+            steps.append(cpu)
+    if any(s["value"] is None for s in steps):
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + steps[0].get("error", "")}))
+        return
+    secs = [s["seconds"] for s in steps]
+    val = sum(8 * 64 ** 3 for _ in steps) / sum(secs) / 1e9
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WL["name"], "K": list(WL["K"]), "L": WL["L"], "n_dir": 162,
+                      "nrhs": WL["nrhs"], "tol": WL["tol"],
+                      "step": "1 of 162 directions (8 fields) per step: the full workload takes ~3 min of CPU"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": steps[0]["sample"].replace("1 of 162", "1 of 162")},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# flop / byte models of one step (nominal 5 N log2 N flops per complex DFT)
+# ---------------------------------------------------------------------------
+def yz_flops(K, n, n_dir, nrhs, ranks=None):
+    Kx, Ky, Kz = K
+    n1, n2, n3 = n
+    lg2, lg3 = math.log2(n2), math.log2(n3)
+    per_field_slab = 2 * Kz * 5 * n2 * lg2 + n2 * (2 * 5 * n3 * lg3 + 6 * n3)
+    f = n1 * n_dir * 2 * nrhs * per_field_slab
+    if ranks is not None:
+        # slab restore per block: (n2 x r2)(r2 x r3) and (n3 x r3)(r3 x n2), 8 flops per complex MAC
+        f += n1 * sum(8 * (n2 * r2 * r3 + n3 * n2 * r3) for (_, r2, r3) in ranks)
+    return f
+
+
+def step_flops(K, n, n_dir, nrhs, ranks=None):
+    Kx, Ky, Kz = K
+    n1, n2, n3 = n
+    F = n_dir * 2 * nrhs
+    x = F * 2 * Ky * Kz * 5 * n1 * math.log2(n1)
+    f = x + yz_flops(K, n, n_dir, nrhs, ranks)
+    if ranks is not None:
+        f += sum(8 * n1 * r1 * r2 * r3 for (r1, r2, r3) in ranks)
+    return f
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-child", type=int, default=0)
+    args = ap.parse_args()
+    if args.cpu_baseline_child:
+        cpu_baseline_child(args.cpu_baseline_child)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+
+    import paper_2010_00520_gb300 as F
+    from seeded_inputs import field_spectra
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(F.LIB_PATH):
+        from paper_2010_00520_gb300 import build as _b
+        _b.build()
+
+    K, L, nrhs = WL["K"], WL["L"], WL["nrhs"]
+    plans = {}
+    for name, fmt, dec, tol in (("compressed", 3, 1, WL["tol"]), ("plain", 0, 0, 0.0)):
+        h = F.fmmfft_plan_create(K[0], K[1], K[2], WL["a"], WL["k0"], L, fmt, dec, tol)
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64)
+        F.fmmfft_compress(h)
+        plans[name] = h
+    st = F.fmmfft_plan_stats(plans["compressed"])
+    n, n_dir = tuple(st["n"]), st["n_dir"]
+    ranks = [tuple(int(v) for v in r) for r in F.fmmfft_plan_ranks(plans["compressed"])]
+    S_host = field_spectra(WL["seed"], n_dir, nrhs, K).astype(np.complex64)
+    x = torch.from_numpy(S_host).to("cuda")
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(h, steps):
+        for _ in range(args.warmup):
+            F.fmmfft_translate(h, x, y, nrhs, stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            F.fmmfft_translate(h, x, y, nrhs, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_comp = timed(plans["compressed"], args.steps)
+    ms_plain = timed(plans["plain"], args.steps)
+    clk = clocks.stop()
+    units = _units(n, n_dir, nrhs)
+    value = world * units / (ms_comp * 1e-3) / 1e9
+    value_plain = world * units / (ms_plain * 1e-3) / 1e9
+    for h in plans.values():
+        assert F.fmmfft_poll_status(h) == 0
+
+    # per-stage device times of the compressed step (events on the launch stream)
+    stage = {}
+    for name, h in plans.items():
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PROFILE, 1)
+        acc = [0.0] * F.FMMFFT_NUM_STAGES
+        for _ in range(args.steps):
+            F.fmmfft_translate(h, x, y, nrhs, stream)
+            t = F.fmmfft_stage_times(h)
+            acc = [a + b for a, b in zip(acc, t)]
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PROFILE, 0)
+        stage[name] = {k: v / args.steps for k, v in zip(("restore", "xfwd", "yz", "xinv"), acc)}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    hin = torch.from_numpy(S_host).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(2):
+        F.fmmfft_translate_host(plans["compressed"], hin, hout, nrhs, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F.fmmfft_translate_host(plans["compressed"], hin, hout, nrhs, stream)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    io_bytes = S_host.nbytes
+
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s, FMA = 2 flops
+    yz_ms = stage["compressed"]["yz"]
+    yz_fl = yz_flops(K, n, n_dir, nrhs, ranks)
+    achieved = yz_fl / (yz_ms * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "yz_kernel_tucker3d_32cube_L8.traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("dram_bytes_per_launch")
+    step_bytes = 2 * io_bytes + st["device_bytes_operator"]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_comp, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
+        "config": {"workload": WL["name"], "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
+                   "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d", "tol": WL["tol"],
+                   "precision": "FP32 FFTs and FP32 restores",
+                   "l2": "inputs (340 MB) and outputs (340 MB) each larger than the 129 MB L2; no flush"},
+        "plain": {"value": value_plain, "ms_per_step": ms_plain},
+        "ratio_compressed_over_plain_time": ms_comp / ms_plain,
+        "memory": {"operator_bytes_compressed": st["device_bytes_operator"],
+                   "operator_bytes_plain": F.fmmfft_plan_stats(plans["plain"])["device_bytes_operator"],
+                   "saving": st["saving"], "max_rank": st["max_rank"][:3],
+                   "mean_rank": [round(v, 2) for v in st["mean_rank"]]},
+        "stages_ms": stage,
+        "roofline": {"kernel": "yz_kernel (Tucker-3D slab restore + y/z FFTs + Hadamard)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic,
+                     "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({peak_src} clock)",
+                     "flops_model": "nominal 5 N log2 N per complex DFT line + 6 per Hadamard point + 8 per complex MAC of the restore"},
+        "hbm": {"algorithmic_bytes_per_step": step_bytes,
+                "achieved_gbs": step_bytes / (ms_comp * 1e-3) / 1e9,
+                "peak_gbs": peaks.get("hbm_gbs"), "frac": step_bytes / (ms_comp * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+        "step_tflops_nominal": step_flops(K, n, n_dir, nrhs, ranks) / (ms_comp * 1e-3) / 1e12,
+        "clocks": clk,
+        "e2e": {"value": world * units / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": 4 * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = run_cpu_baseline(CPU_SAMPLE_DIRS)
+    for h in plans.values():
+        F.fmmfft_plan_destroy(h)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * fmmfft.h -- C ABI of the compressed FMM-FFT translation library.
+ *
+ * The library implements the translation stage of an FMM-FFT matrix-vector
+ * product (Qian & Yucel, "On the Compression of Translation Operator Tensors
+ * in FMM-FFT-Accelerated SIE Simulators via Tensor Decompositions"):
+ *
+ *   B_v'(k_p) = IFFT( T~_p . FFT(A_v(k_p)) )                       (Eq. 5)
+ *
+ * for every plane-wave direction k_p, both field polarisations (theta, phi)
+ * and every right-hand side, where T~_p is the FFT'ed translation operator of
+ * Eq. 7 on the box-offset grid.  The operators are either stored as they are
+ * (format NONE) or compressed at set-up by Tucker, tensor-train (TT) or
+ * hierarchical-Tucker (H-Tucker) decompositions in the 3D per-direction or
+ * the 4D all-directions format (Sec. II.B, Eqs. 8-14, Algs. 1-3) and restored
+ * one direction at a time during the translation (Sec. II.C, Figs. 3-4).
+ *
+ * Conventions shared by every entry point
+ *   - All functions return an int status: FMMFFT_OK (0) or a negative
+ *     FMMFFT_ERR_* code.  No C++ exception crosses this interface.
+ *   - Complex numbers are interleaved (re, im).  Precision FMMFFT_PREC_C128
+ *     uses double pairs (16 bytes); every other precision uses float pairs
+ *     (8 bytes).  Host-side import arrays are always double pairs.
+ *   - Box grid K = (Kx, Ky, Kz) (the paper's K_x, K_y, K_z, Sec. II.A).  FFT
+ *     extents n_i are the smallest powers of two >= 2 K_i - 1 (the circulant
+ *     embedding of Sec. II.B; n_i = 2 K_i whenever K_i is a power of two).
+ *   - Directions: Gauss-Legendre in cos(theta) (L + 1 nodes, ascending) times
+ *     N_phi uniform phi_j = 2 pi j / N_phi, theta-major: p = i * N_phi + j.
+ *     N_phi = 2 (L + 1) by default, 2 L + 1 (the paper's N_dir = (L+1)(2L+1),
+ *     Sec. II.A) with FMMFFT_KEY_NPHI_RULE = 1.
+ *   - Field layout (S_in, S_out): [n_dir][2][nrhs][Kz][Ky][Kx], x fastest,
+ *     polarisation 0 = theta, 1 = phi.  One T~_p serves the 2 * nrhs fields
+ *     of direction p (Sec. II.A: only the theta and phi components are
+ *     translated, with the same scalar operator).
+ *   - Operator offsets: offset index d_i = v'_i - v_i in (-K_i, K_i); T~_p is
+ *     the unnormalised forward DFT (kernel exp(-2 pi i m k / n)) of the
+ *     operator embedded at index d_i mod n_i; near offsets are zero.
+ *   - A plan is not thread-safe: calls on one plan must not overlap (its
+ *     scratch buffers are shared by all its calls).  Different plans are
+ *     independent.
+ *   - Device memory for operators and scratch is owned by the plan and freed
+ *     by fmmfft_plan_destroy.  Field buffers are owned by the caller.
+ */
+#ifndef FMMFFT_H_
+#define FMMFFT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmmfft_plan_s* fmmfft_plan;
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  FMMFFT_OK = 0,
+  FMMFFT_ERR_INVALID_ARG = -1,   /* bad size, null pointer, aliasing, ...   */
+  FMMFFT_ERR_NOT_COMPRESSED = -2,/* translate before compress / import      */
+  FMMFFT_ERR_OOM = -3,           /* device or host allocation failed        */
+  FMMFFT_ERR_CUDA = -4,          /* a CUDA runtime call or launch failed    */
+  FMMFFT_ERR_UNSUPPORTED = -5,   /* valid request outside this build's limits */
+  FMMFFT_ERR_DEVICE = -6,        /* a kernel reported a failure (status word) */
+  FMMFFT_ERR_IO = -7             /* file could not be read or written       */
+};
+
+/* ---- storage format and decomposition (Sec. II.B) ---------------------- */
+enum {
+  FMMFFT_FORMAT_NONE = 0,        /* uncompressed T~_p, n1 x n2 x n3 each    */
+  FMMFFT_FORMAT_3D = 3,          /* one decomposition per direction         */
+  FMMFFT_FORMAT_4D = 4           /* one decomposition of T_4D (n1,n2,n3,n_dir) */
+};
+enum {
+  FMMFFT_DECOMP_NONE = 0,
+  FMMFFT_DECOMP_TUCKER = 1,      /* Eqs. 8-9, Alg. 1                        */
+  FMMFFT_DECOMP_TT = 2,          /* Eqs. 13-14, Alg. 3                      */
+  FMMFFT_DECOMP_HTUCKER = 3      /* Eq. 11, Alg. 2 (4D format only)         */
+};
+
+/* ---- arithmetic of the translation ------------------------------------- */
+enum {
+  FMMFFT_PREC_C128 = 0,          /* FP64 fields, operators and FFTs          */
+  FMMFFT_PREC_C64 = 1,           /* FP32 fields and FFTs, FP32 restores     */
+  FMMFFT_PREC_C64_3XTF32 = 2,    /* FP32 fields and FFTs, restores on the tensor
+                                    cores as three TF32 products (big x big,
+                                    big x small, small x big), FP32 accumulate */
+  FMMFFT_PREC_C64_BF16X3 = 3     /* as above with bf16 hi/lo splits         */
+};
+
+/* ---- keys of fmmfft_plan_set (all before fmmfft_compress) -------------- */
+enum {
+  FMMFFT_KEY_PRECISION = 1,      /* one of FMMFFT_PREC_* (default C64)          */
+  FMMFFT_KEY_NPHI_RULE = 2,      /* 0: N_phi = 2(L+1) (default); 1: 2L+1       */
+  FMMFFT_KEY_NEAR_RULE = 3,      /* 0: near iff max|d_i| <= 1 (default);
+                                    1: near iff a|d| < kappa * a sqrt(3)/2 (Sec. II.A) */
+  FMMFFT_KEY_KAPPA = 4,          /* kappa of near rule 1 (default 4)           */
+  FMMFFT_KEY_PREFACTOR = 5,      /* 0: c = 1 (default); 1: c = -k^2 eta/(16 pi^2) (Eq. 7) */
+  FMMFFT_KEY_TRUNC_RULE = 6,     /* 0: discarded-energy rule (default);
+                                    1: normalised singular value < gamma/sqrt(d) */
+  FMMFFT_KEY_PROFILE = 7         /* 1: record CUDA events between the kernels of
+                                    each translation (fmmfft_stage_times); may
+                                    be changed at any time                      */
+};
+
+/* Stages of one translation, in launch order (fmmfft_stage_times). */
+enum {
+  FMMFFT_STAGE_RESTORE = 0,      /* restore step 1 of compressed formats      */
+  FMMFFT_STAGE_XFWD = 1,         /* forward DFT along x                       */
+  FMMFFT_STAGE_YZ = 2,           /* y/z DFTs, Hadamard product, slab restore  */
+  FMMFFT_STAGE_XINV = 3,         /* inverse DFT along x                       */
+  FMMFFT_NUM_STAGES = 4
+};
+
+/* ---- statistics ---------------------------------------------------------- */
+typedef struct fmmfft_stats {
+  int n_dir;                     /* number of plane-wave directions          */
+  int L;                         /* multipole count                          */
+  int K[3];                      /* boxes per axis                           */
+  int n[3];                      /* FFT extents per axis                     */
+  int format, decomp, precision;
+  int max_rank[6];               /* largest rank per mode over directions (3D)
+                                    or the ranks of the single 4D decomposition;
+                                    H-Tucker: r1 r2 r3 r4 r12 r34; TT: r1 r2 r3 */
+  double mean_rank[3];           /* mean per-mode rank over directions (3D)   */
+  int64_t elements_plain;        /* complex elements of the uncompressed store */
+  int64_t elements_compressed;   /* complex elements of the compressed store */
+  double saving;                 /* 1 - compressed / plain (Sec. III)        */
+  int64_t device_bytes_operator; /* device bytes of the stored operator      */
+  int64_t device_bytes_scratch;  /* device bytes of scratch buffers currently held */
+  double setup_seconds;          /* wall time of the last fmmfft_compress    */
+} fmmfft_stats;
+
+/*
+ * Create a plan (host-only; touches no GPU).
+ *   Nx, Ny, Nz  boxes per axis, each in [2, 128]        (Sec. II.A, K_x K_y K_z)
+ *   a           box edge length (same length unit as 1/k0), > 0
+ *   k0          real wavenumber, > 0 (2 pi / wavelength)
+ *   L           multipole count, 0 <= L <= 64            (Sec. II.A)
+ *   format      FMMFFT_FORMAT_*; decomp FMMFFT_DECOMP_*; format NONE needs
+ *               decomp NONE and vice versa; H-Tucker needs format 4D.
+ *   tol         relative tolerance gamma of the decomposition (> 0 unless
+ *               decomp is NONE)                           (Algs. 1-3)
+ * Errors: FMMFFT_ERR_INVALID_ARG for any violation above, FMMFFT_ERR_OOM.
+ */
+int fmmfft_plan_create(fmmfft_plan* out, int Nx, int Ny, int Nz, double a, double k0,
+                       int L, int format, int decomp, double tol);
+
+/* Set an option (FMMFFT_KEY_*) before fmmfft_compress; INVALID_ARG for an
+ * unknown key or value, or when the plan is already compressed. */
+int fmmfft_plan_set(fmmfft_plan plan, int key, double value);
+
+/*
+ * Set-up on the current CUDA device, blocking: evaluates the translation
+ * operator of Eq. 7 in FP64 on the host, embeds and FFTs it (Sec. II.B),
+ * decomposes it to tolerance gamma (Algs. 1-3) when decomp != NONE, and
+ * uploads the stored form to device memory owned by the plan.
+ * Errors: UNSUPPORTED (a size outside this build's kernels), OOM, CUDA.
+ */
+int fmmfft_compress(fmmfft_plan plan);
+
+/*
+ * Load an externally computed uncompressed operator instead of calling
+ * fmmfft_compress (format NONE plans only).  That: host array of n_dir * n1 *
+ * n2 * n3 complex doubles, index ((p * n1 + x) * n2 + y) * n3 + z, holding
+ * T~_p[x][y][z] as defined in the header comment.  Copied; caller keeps it.
+ */
+int fmmfft_import_plain(fmmfft_plan plan, const double* That);
+
+/*
+ * Load externally computed per-direction Tucker factors (format 3D, decomp
+ * TUCKER plans only), the representation of Eq. 8 for each direction p:
+ *   T~_p[x][y][z] = sum_{a,b,c} C_p[a][b][c] U1_p[x][a] U2_p[y][b] U3_p[z][c].
+ * ranks: n_dir * 3 ints (r1, r2, r3 of each direction), each in [1, n_i].
+ * core/U1/U2/U3: complex doubles, the directions' arrays concatenated in
+ * direction order; C_p is r1 x r2 x r3 (c fastest), U_i_p is n_i x r_i
+ * (row-major).  Copied; caller keeps them.
+ */
+int fmmfft_import_tucker3d(fmmfft_plan plan, const int* ranks, const double* core,
+                           const double* U1, const double* U2, const double* U3);
+
+/*
+ * The translation (Eq. 5) of every field, asynchronous on `stream`
+ * (a cudaStream_t; NULL = legacy default stream):
+ *   S_out[p][pol][rhs] = crop( IFFT( T~_p . FFT( pad(S_in[p][pol][rhs]) ) ) )
+ * restoring T~_p from the stored decomposition when the plan is compressed
+ * (Sec. II.C).  S_in, S_out: device pointers, layout and element type as in
+ * the header comment, n_dir * 2 * nrhs * Kx * Ky * Kz complex each, must not
+ * overlap.  nrhs >= 1.  The first call with a given nrhs (or a larger one than
+ * before) allocates the plan's scratch; later calls allocate nothing.
+ * Errors: NOT_COMPRESSED, INVALID_ARG, OOM, CUDA (launch failure), DEVICE
+ * (a failure a kernel of an earlier call reported through the status word).
+ */
+int fmmfft_translate(fmmfft_plan plan, const void* S_in, void* S_out, int nrhs, void* stream);
+
+/*
+ * As fmmfft_translate with HOST field buffers: copies S_in to the device,
+ * translates and copies the result back, all on `stream`, and waits for the
+ * stream before returning.  Page-locked host buffers give full copy speed.
+ */
+int fmmfft_translate_host(fmmfft_plan plan, const void* S_in_host, void* S_out_host,
+                          int nrhs, void* stream);
+
+/*
+ * Host-only FP64 evaluation of one direction's FFT'ed operator T~_p (Eq. 7,
+ * embedded and transformed as in Sec. II.B), exactly as fmmfft_compress
+ * computes it, without touching a GPU.  That_out: n1 * n2 * n3 complex
+ * doubles, index (x * n2 + y) * n3 + z.  0 <= p < n_dir.
+ */
+int fmmfft_operator_host(fmmfft_plan plan, int p, double* That_out);
+
+/*
+ * Host-only FP64 compression of one direction as fmmfft_compress does it for
+ * 3D-format plans (Tucker: Alg. 1), returned restored: ranks_out receives
+ * (r1, r2, r3) and restored_out (optional, n1 * n2 * n3 complex doubles,
+ * layout as fmmfft_operator_host) the tensor rebuilt from the kept factors.
+ * INVALID_ARG for plans of another format; touches no GPU.
+ */
+int fmmfft_compress_direction_host(fmmfft_plan plan, int p, int* ranks_out, double* restored_out);
+
+/* Fill *out (see fmmfft_stats). */
+int fmmfft_plan_stats(fmmfft_plan plan, fmmfft_stats* out);
+
+/* Per-direction ranks of a compressed 3D-format plan: n_dir * 3 ints
+ * (r1, r2, r3 of each direction).  INVALID_ARG for other formats or before
+ * the plan holds an operator. */
+int fmmfft_plan_ranks(fmmfft_plan plan, int* ranks);
+
+/* Unit direction vectors k_p (n_dir x 3 doubles) and quadrature weights w_p
+ * (n_dir doubles, summing to 4 pi); either pointer may be NULL. */
+int fmmfft_plan_directions(fmmfft_plan plan, double* khat, double* weights);
+
+/* Device milliseconds of each stage (FMMFFT_STAGE_*) of the plan's last
+ * translation, from CUDA events recorded on its stream while
+ * FMMFFT_KEY_PROFILE was 1 (0 for a stage the format does not run).  Waits for
+ * that translation.  INVALID_ARG when no profiled translation has run. */
+int fmmfft_stage_times(fmmfft_plan plan, float* ms);
+
+/* Read and clear the plan's device status word (0 = no failure reported).
+ * Synchronises the plan's last stream. */
+int fmmfft_poll_status(fmmfft_plan plan, int* device_status);
+
+/* Release every resource of the plan (device memory included). */
+int fmmfft_plan_destroy(fmmfft_plan plan);
+
+/* Static text for a status code. */
+const char* fmmfft_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMMFFT_H_ */

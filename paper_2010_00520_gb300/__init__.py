@@ -1,0 +1,288 @@
+"""Python binding of the compressed FMM-FFT translation library (libfmmfft.so).
+
+The functions below carry the names of the C entry points declared in
+include/fmmfft.h and only marshal arguments: every step of the translation
+runs in the library's CUDA kernels.  Device buffers may be given as torch
+tensors (their data_ptr() is used) or as integer addresses; streams as torch
+streams, integer handles or None (the current torch stream when torch is
+loaded, else the legacy default stream).
+
+Importing the package does not load the library; the first call does, and it
+raises if libfmmfft.so is missing (build it with
+``python -m paper_2010_00520_gb300.build``).  There is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfmmfft.so")
+
+FMMFFT_OK = 0
+FMMFFT_ERR_INVALID_ARG = -1
+FMMFFT_ERR_NOT_COMPRESSED = -2
+FMMFFT_ERR_OOM = -3
+FMMFFT_ERR_CUDA = -4
+FMMFFT_ERR_UNSUPPORTED = -5
+FMMFFT_ERR_DEVICE = -6
+FMMFFT_ERR_IO = -7
+
+FMMFFT_FORMAT_NONE, FMMFFT_FORMAT_3D, FMMFFT_FORMAT_4D = 0, 3, 4
+FMMFFT_DECOMP_NONE, FMMFFT_DECOMP_TUCKER, FMMFFT_DECOMP_TT, FMMFFT_DECOMP_HTUCKER = 0, 1, 2, 3
+FMMFFT_PREC_C128, FMMFFT_PREC_C64, FMMFFT_PREC_C64_3XTF32, FMMFFT_PREC_C64_BF16X3 = 0, 1, 2, 3
+FMMFFT_KEY_PRECISION = 1
+FMMFFT_KEY_NPHI_RULE = 2
+FMMFFT_KEY_NEAR_RULE = 3
+FMMFFT_KEY_KAPPA = 4
+FMMFFT_KEY_PREFACTOR = 5
+FMMFFT_KEY_TRUNC_RULE = 6
+FMMFFT_KEY_PROFILE = 7
+FMMFFT_STAGE_RESTORE, FMMFFT_STAGE_XFWD, FMMFFT_STAGE_YZ, FMMFFT_STAGE_XINV = 0, 1, 2, 3
+FMMFFT_NUM_STAGES = 4
+
+# every symbol the header declares
+EXPORTED = (
+    "fmmfft_plan_create", "fmmfft_plan_set", "fmmfft_compress", "fmmfft_import_plain",
+    "fmmfft_import_tucker3d", "fmmfft_translate", "fmmfft_translate_host", "fmmfft_plan_stats",
+    "fmmfft_plan_directions", "fmmfft_poll_status", "fmmfft_plan_destroy", "fmmfft_status_string",
+    "fmmfft_operator_host", "fmmfft_compress_direction_host", "fmmfft_stage_times",
+    "fmmfft_plan_ranks",
+)
+
+
+class FmmfftError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {fmmfft_status_string(status)} ({status})")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("n_dir", ctypes.c_int), ("L", ctypes.c_int), ("K", ctypes.c_int * 3), ("n", ctypes.c_int * 3),
+        ("format", ctypes.c_int), ("decomp", ctypes.c_int), ("precision", ctypes.c_int),
+        ("max_rank", ctypes.c_int * 6), ("mean_rank", ctypes.c_double * 3),
+        ("elements_plain", ctypes.c_int64), ("elements_compressed", ctypes.c_int64),
+        ("saving", ctypes.c_double), ("device_bytes_operator", ctypes.c_int64),
+        ("device_bytes_scratch", ctypes.c_int64), ("setup_seconds", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfmmfft.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2010_00520_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "fmmfft_plan_create": [ctypes.POINTER(vp), i, i, i, d, d, i, i, i, d],
+        "fmmfft_plan_set": [vp, i, d],
+        "fmmfft_compress": [vp],
+        "fmmfft_import_plain": [vp, dp],
+        "fmmfft_import_tucker3d": [vp, ip, dp, dp, dp, dp],
+        "fmmfft_translate": [vp, vp, vp, i, vp],
+        "fmmfft_translate_host": [vp, vp, vp, i, vp],
+        "fmmfft_plan_stats": [vp, ctypes.POINTER(_Stats)],
+        "fmmfft_plan_directions": [vp, dp, dp],
+        "fmmfft_poll_status": [vp, ip],
+        "fmmfft_plan_destroy": [vp],
+        "fmmfft_status_string": [i],
+        "fmmfft_operator_host": [vp, i, dp],
+        "fmmfft_compress_direction_host": [vp, i, ip, dp],
+        "fmmfft_stage_times": [vp, ctypes.POINTER(ctypes.c_float)],
+        "fmmfft_plan_ranks": [vp, ip],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "fmmfft_status_string" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != FMMFFT_OK:
+        raise FmmfftError(st, where)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        import sys
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+        return 0
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError(f"unsupported stream {type(s)}")
+
+
+def _cplx(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def fmmfft_status_string(status: int) -> str:
+    return lib().fmmfft_status_string(int(status)).decode()
+
+
+def fmmfft_plan_create(Nx, Ny, Nz, a, k0, L, format, decomp, tol) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fmmfft_plan_create(ctypes.byref(h), Nx, Ny, Nz, float(a), float(k0), L, format, decomp,
+                                    float(tol)), "fmmfft_plan_create")
+    return h.value
+
+
+def fmmfft_plan_set(plan, key, value):
+    _check(lib().fmmfft_plan_set(plan, key, float(value)), "fmmfft_plan_set")
+
+
+def fmmfft_compress(plan):
+    _check(lib().fmmfft_compress(plan), "fmmfft_compress")
+
+
+def fmmfft_import_plain(plan, That):
+    T = _cplx(That)
+    _check(lib().fmmfft_import_plain(plan, _dptr(T)), "fmmfft_import_plain")
+
+
+def fmmfft_import_tucker3d(plan, ranks, core, U1, U2, U3):
+    r = np.ascontiguousarray(ranks, dtype=np.int32)
+    arrs = [_cplx(x) for x in (core, U1, U2, U3)]
+    _check(lib().fmmfft_import_tucker3d(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        *[_dptr(x) for x in arrs]), "fmmfft_import_tucker3d")
+
+
+def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):
+    _check(lib().fmmfft_translate(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
+           "fmmfft_translate")
+
+
+def fmmfft_translate_host(plan, S_in, S_out, nrhs, stream=None):
+    _check(lib().fmmfft_translate_host(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
+           "fmmfft_translate_host")
+
+
+def fmmfft_plan_stats(plan) -> dict:
+    s = _Stats()
+    _check(lib().fmmfft_plan_stats(plan, ctypes.byref(s)), "fmmfft_plan_stats")
+    out = {}
+    for name, _ in _Stats._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
+
+
+def fmmfft_plan_ranks(plan):
+    n = fmmfft_plan_stats(plan)["n_dir"]
+    r = np.zeros((n, 3), dtype=np.int32)
+    _check(lib().fmmfft_plan_ranks(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "fmmfft_plan_ranks")
+    return r
+
+
+def fmmfft_plan_directions(plan):
+    n = fmmfft_plan_stats(plan)["n_dir"]
+    kh = np.zeros((n, 3))
+    w = np.zeros(n)
+    _check(lib().fmmfft_plan_directions(plan, _dptr(kh), _dptr(w)), "fmmfft_plan_directions")
+    return kh, w
+
+
+def fmmfft_operator_host(plan, p):
+    st = fmmfft_plan_stats(plan)
+    out = np.zeros(tuple(st["n"]), dtype=np.complex128)
+    _check(lib().fmmfft_operator_host(plan, int(p), _dptr(out)), "fmmfft_operator_host")
+    return out
+
+
+def fmmfft_compress_direction_host(plan, p, restored=True):
+    st = fmmfft_plan_stats(plan)
+    r = np.zeros(3, dtype=np.int32)
+    out = np.zeros(tuple(st["n"]), dtype=np.complex128) if restored else None
+    _check(lib().fmmfft_compress_direction_host(plan, int(p), r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                _dptr(out) if restored else None),
+           "fmmfft_compress_direction_host")
+    return tuple(int(v) for v in r), out
+
+
+def fmmfft_stage_times(plan):
+    ms = (ctypes.c_float * FMMFFT_NUM_STAGES)()
+    _check(lib().fmmfft_stage_times(plan, ms), "fmmfft_stage_times")
+    return [float(v) for v in ms]
+
+
+def fmmfft_poll_status(plan) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().fmmfft_poll_status(plan, ctypes.byref(v)), "fmmfft_poll_status")
+    return v.value
+
+
+def fmmfft_plan_destroy(plan):
+    _check(lib().fmmfft_plan_destroy(plan), "fmmfft_plan_destroy")
+
+
+class Plan:
+    """Owning wrapper around a plan handle (destroyed on close / exit)."""
+
+    def __init__(self, K, a, k0, L, format=FMMFFT_FORMAT_NONE, decomp=FMMFFT_DECOMP_NONE, tol=0.0, **opts):
+        self.handle = fmmfft_plan_create(K[0], K[1], K[2], a, k0, L, format, decomp, tol)
+        keys = {"precision": FMMFFT_KEY_PRECISION, "nphi_rule": FMMFFT_KEY_NPHI_RULE,
+                "near_rule": FMMFFT_KEY_NEAR_RULE, "kappa": FMMFFT_KEY_KAPPA,
+                "prefactor": FMMFFT_KEY_PREFACTOR, "trunc_rule": FMMFFT_KEY_TRUNC_RULE,
+                "profile": FMMFFT_KEY_PROFILE}
+        for k, v in opts.items():
+            fmmfft_plan_set(self.handle, keys[k], v)
+
+    def compress(self):
+        fmmfft_compress(self.handle)
+        return self
+
+    def stats(self) -> dict:
+        return fmmfft_plan_stats(self.handle)
+
+    def translate(self, S_in, S_out, nrhs, stream=None):
+        fmmfft_translate(self.handle, S_in, S_out, nrhs, stream)
+
+    def close(self):
+        if self.handle:
+            fmmfft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

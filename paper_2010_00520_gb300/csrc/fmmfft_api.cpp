@@ -1,0 +1,609 @@
+// C ABI of the translation library: plan life cycle, set-up, translation.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fmmfft.h"
+#include "host_setup.h"
+#include "plan_internal.h"
+
+using fmm::cdouble;
+
+struct fmmfft_plan_s {
+  int K[3] = {0, 0, 0};
+  int n[3] = {0, 0, 0};
+  int L = 0;
+  double a = 0, k0 = 0, tol = 0;
+  int format = 0, decomp = 0;
+  int precision = FMMFFT_PREC_C64;
+  int nphi_rule = 0, near_rule = 0, prefactor = 0, trunc_rule = 0;
+  double kappa = 4.0;
+  int n_dir = 0;
+  std::vector<double> khat, weights;
+  bool ready = false;
+  // device state
+  void* d_tw[3] = {nullptr, nullptr, nullptr};
+  void* d_op = nullptr;
+  void* d_pack = nullptr;
+  fmm::Tucker3DDesc* d_desc = nullptr;
+  void* d_h = nullptr;
+  void* d_inter = nullptr;
+  size_t inter_bytes = 0;
+  void* d_io = nullptr;       // device copies for fmmfft_translate_host
+  size_t io_bytes = 0;
+  int* d_status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool profile = false;
+  bool profiled_run = false;
+  cudaEvent_t events[FMMFFT_NUM_STAGES + 1] = {};
+  // host-side bookkeeping
+  std::vector<fmm::Tucker3DDesc> desc;
+  int rmax[6] = {0, 0, 0, 0, 0, 0};
+  double mean_rank[3] = {0, 0, 0};
+  int64_t elements_plain = 0, elements_compressed = 0;
+  int64_t bytes_operator = 0, bytes_h = 0;
+  double setup_seconds = 0;
+};
+
+namespace {
+
+int embed_extent(int K) {
+  int n = 1;
+  while (n < 2 * K - 1) n *= 2;
+  return n < 2 ? 2 : n;
+}
+
+size_t elem_bytes(const fmmfft_plan_s* p) { return p->precision == FMMFFT_PREC_C128 ? 16 : 8; }
+
+void free_dev(void*& ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+void release_operator(fmmfft_plan_s* p) {
+  for (auto& t : p->d_tw) free_dev(t);
+  free_dev(p->d_op);
+  free_dev(p->d_pack);
+  void* d = p->d_desc;
+  free_dev(d);
+  p->d_desc = nullptr;
+  free_dev(p->d_h);
+  p->ready = false;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FMMFFT_OK;
+  if (e == cudaErrorMemoryAllocation) return FMMFFT_ERR_OOM;
+  return FMMFFT_ERR_CUDA;
+}
+
+int dev_alloc(void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return FMMFFT_OK;
+}
+
+// host complex doubles -> device float2 / double2
+int upload_complex(void** dst, const std::vector<cdouble>& src, bool dbl) {
+  const size_t n = src.size();
+  int st;
+  if (dbl) {
+    if ((st = dev_alloc(dst, n * 16)) != FMMFFT_OK) return st;
+    return cuda_status(cudaMemcpy(*dst, src.data(), n * 16, cudaMemcpyHostToDevice));
+  }
+  std::vector<float> f(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    f[2 * i] = (float)src[i].real();
+    f[2 * i + 1] = (float)src[i].imag();
+  }
+  if ((st = dev_alloc(dst, n * 8)) != FMMFFT_OK) return st;
+  return cuda_status(cudaMemcpy(*dst, f.data(), n * 8, cudaMemcpyHostToDevice));
+}
+
+int ensure_common(fmmfft_plan_s* p) {
+  const bool dbl = p->precision == FMMFFT_PREC_C128;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (p->d_tw[ax]) continue;
+    const int m = p->n[ax];
+    std::vector<cdouble> tw(m);
+    for (int k = 0; k < m; ++k) tw[k] = std::polar(1.0, -2.0 * 3.14159265358979323846 * k / m);
+    int st = upload_complex(&p->d_tw[ax], tw, dbl);
+    if (st != FMMFFT_OK) return st;
+  }
+  if (!p->d_status) {
+    void* s = nullptr;
+    int st = dev_alloc(&s, sizeof(int));
+    if (st != FMMFFT_OK) return st;
+    p->d_status = (int*)s;
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
+fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
+  fmm::TranslateArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int i = 0; i < 3; ++i) {
+    a.K[i] = p->K[i];
+    a.n[i] = p->n[i];
+    a.tw[i] = p->d_tw[i];
+    a.t3_rmax[i] = p->rmax[i];
+  }
+  a.n_dir = p->n_dir;
+  a.precision = p->precision;
+  a.format = p->format;
+  a.decomp = p->decomp;
+  a.op_plain = p->d_op;
+  a.t3_desc = p->d_desc;
+  a.t3_pack = p->d_pack;
+  a.t3_h = p->d_h;
+  a.status = p->d_status;
+  return a;
+}
+
+// Plain store: T~_p scaled by 1/(n1 n2 n3), [p][x][z][y].  `That` is indexed
+// ((p n1 + x) n2 + y) n3 + z.
+int upload_plain(fmmfft_plan_s* p, const std::function<const cdouble*(int)>& slab_of) {
+  const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  const size_t per = (size_t)n1 * n2 * n3;
+  const double sc = 1.0 / (double)per;
+  std::vector<cdouble> h(per * p->n_dir);
+  fmm::parallel_for(p->n_dir, [&](int d) {
+    const cdouble* T = slab_of(d);
+    cdouble* o = &h[per * d];
+    for (int x = 0; x < n1; ++x)
+      for (int y = 0; y < n2; ++y)
+        for (int z = 0; z < n3; ++z) o[((size_t)x * n3 + z) * n2 + y] = T[((size_t)x * n2 + y) * n3 + z] * sc;
+  });
+  free_dev(p->d_op);
+  int st = upload_complex(&p->d_op, h, p->precision == FMMFFT_PREC_C128);
+  if (st != FMMFFT_OK) return st;
+  p->elements_plain = (int64_t)per * p->n_dir;
+  p->elements_compressed = p->elements_plain;
+  p->bytes_operator = (int64_t)(per * p->n_dir * elem_bytes(p));
+  for (int i = 0; i < 6; ++i) p->rmax[i] = 0;
+  return FMMFFT_OK;
+}
+
+// Tucker-3D store from per-direction factors.
+int upload_tucker3d(fmmfft_plan_s* p, const std::vector<fmm::Tucker3>& tk) {
+  const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  p->desc.assign(p->n_dir, fmm::Tucker3DDesc());
+  int64_t off = 0, offh = 0;
+  for (int i = 0; i < 3; ++i) { p->rmax[i] = 0; p->mean_rank[i] = 0; }
+  int64_t elems = 0;
+  for (int d = 0; d < p->n_dir; ++d) {
+    fmm::Tucker3DDesc& D = p->desc[d];
+    D.r1 = tk[d].r[0];
+    D.r2 = tk[d].r[1];
+    D.r3 = tk[d].r[2];
+    D.pad = 0;
+    D.off_core = off; off += (int64_t)D.r1 * D.r2 * D.r3;
+    D.off_u1 = off; off += (int64_t)n1 * D.r1;
+    D.off_u2 = off; off += (int64_t)n2 * D.r2;
+    D.off_u3 = off; off += (int64_t)n3 * D.r3;
+    D.off_h = offh; offh += (int64_t)n1 * D.r2 * D.r3;
+    for (int i = 0; i < 3; ++i) {
+      p->rmax[i] = std::max(p->rmax[i], tk[d].r[i]);
+      p->mean_rank[i] += tk[d].r[i] / (double)p->n_dir;
+    }
+  }
+  elems = off;
+  std::vector<cdouble> pack((size_t)off);
+  fmm::parallel_for(p->n_dir, [&](int d) {
+    const fmm::Tucker3DDesc& D = p->desc[d];
+    std::copy(tk[d].core.begin(), tk[d].core.end(), pack.begin() + D.off_core);
+    std::copy(tk[d].U[0].begin(), tk[d].U[0].end(), pack.begin() + D.off_u1);
+    std::copy(tk[d].U[1].begin(), tk[d].U[1].end(), pack.begin() + D.off_u2);
+    std::copy(tk[d].U[2].begin(), tk[d].U[2].end(), pack.begin() + D.off_u3);
+  });
+  free_dev(p->d_pack);
+  int st = upload_complex(&p->d_pack, pack, p->precision == FMMFFT_PREC_C128);
+  if (st != FMMFFT_OK) return st;
+  void* dd = p->d_desc;
+  free_dev(dd);
+  p->d_desc = nullptr;
+  if ((st = dev_alloc(&dd, sizeof(fmm::Tucker3DDesc) * p->n_dir)) != FMMFFT_OK) return st;
+  p->d_desc = (fmm::Tucker3DDesc*)dd;
+  if (cudaMemcpy(dd, p->desc.data(), sizeof(fmm::Tucker3DDesc) * p->n_dir, cudaMemcpyHostToDevice) != cudaSuccess)
+    return FMMFFT_ERR_CUDA;
+  free_dev(p->d_h);
+  if ((st = dev_alloc(&p->d_h, (size_t)offh * elem_bytes(p))) != FMMFFT_OK) return st;
+  p->elements_plain = (int64_t)n1 * n2 * n3 * p->n_dir;
+  p->elements_compressed = elems;
+  p->bytes_operator = (int64_t)(elems * elem_bytes(p) + sizeof(fmm::Tucker3DDesc) * p->n_dir);
+  p->bytes_h = (int64_t)(offh * elem_bytes(p));
+  return FMMFFT_OK;
+}
+
+fmm::OperatorSpec spec_of(const fmmfft_plan_s* p) {
+  fmm::OperatorSpec s;
+  for (int i = 0; i < 3; ++i) {
+    s.K[i] = p->K[i];
+    s.n[i] = p->n[i];
+  }
+  s.L = p->L;
+  s.a = p->a;
+  s.k0 = p->k0;
+  s.near_rule = p->near_rule;
+  s.kappa = p->kappa;
+  s.prefactor = p->prefactor;
+  return s;
+}
+
+bool precision_supported(const fmmfft_plan_s* p) {
+  return p->precision == FMMFFT_PREC_C128 || p->precision == FMMFFT_PREC_C64;
+}
+
+bool check_supported(fmmfft_plan_s* p) {
+  fmm::TranslateArgs a = base_args(p);
+  return fmm::translate_supported(a);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fmmfft_status_string(int s) {
+  switch (s) {
+    case FMMFFT_OK: return "ok";
+    case FMMFFT_ERR_INVALID_ARG: return "invalid argument";
+    case FMMFFT_ERR_NOT_COMPRESSED: return "plan has no operator yet (call fmmfft_compress or an import)";
+    case FMMFFT_ERR_OOM: return "out of memory";
+    case FMMFFT_ERR_CUDA: return "CUDA runtime error";
+    case FMMFFT_ERR_UNSUPPORTED: return "sizes or format not supported by this build";
+    case FMMFFT_ERR_DEVICE: return "a kernel reported a failure";
+    case FMMFFT_ERR_IO: return "file input/output failed";
+    default: return "unknown status";
+  }
+}
+
+int fmmfft_plan_create(fmmfft_plan* out, int Nx, int Ny, int Nz, double a, double k0, int L,
+                       int format, int decomp, double tol) {
+  if (!out) return FMMFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int K[3] = {Nx, Ny, Nz};
+  for (int i = 0; i < 3; ++i)
+    if (K[i] < 2 || K[i] > 128) return FMMFFT_ERR_INVALID_ARG;
+  if (!(a > 0) || !(k0 > 0) || !std::isfinite(a) || !std::isfinite(k0)) return FMMFFT_ERR_INVALID_ARG;
+  if (L < 0 || L > 64) return FMMFFT_ERR_INVALID_ARG;
+  if (format != FMMFFT_FORMAT_NONE && format != FMMFFT_FORMAT_3D && format != FMMFFT_FORMAT_4D)
+    return FMMFFT_ERR_INVALID_ARG;
+  if (decomp < FMMFFT_DECOMP_NONE || decomp > FMMFFT_DECOMP_HTUCKER) return FMMFFT_ERR_INVALID_ARG;
+  if ((format == FMMFFT_FORMAT_NONE) != (decomp == FMMFFT_DECOMP_NONE)) return FMMFFT_ERR_INVALID_ARG;
+  if (decomp == FMMFFT_DECOMP_HTUCKER && format != FMMFFT_FORMAT_4D) return FMMFFT_ERR_INVALID_ARG;
+  if (decomp != FMMFFT_DECOMP_NONE && !(tol > 0 && tol < 1)) return FMMFFT_ERR_INVALID_ARG;
+  fmmfft_plan_s* p = new (std::nothrow) fmmfft_plan_s();
+  if (!p) return FMMFFT_ERR_OOM;
+  for (int i = 0; i < 3; ++i) {
+    p->K[i] = K[i];
+    p->n[i] = embed_extent(K[i]);
+  }
+  p->a = a;
+  p->k0 = k0;
+  p->L = L;
+  p->format = format;
+  p->decomp = decomp;
+  p->tol = tol;
+  p->n_dir = (L + 1) * 2 * (L + 1);
+  fmm::direction_grid(L, 2 * (L + 1), p->khat, p->weights);
+  *out = p;
+  return FMMFFT_OK;
+}
+
+int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
+  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE)) return FMMFFT_ERR_INVALID_ARG;
+  const int iv = (int)v;
+  switch (key) {
+    case FMMFFT_KEY_PRECISION:
+      if (iv < FMMFFT_PREC_C128 || iv > FMMFFT_PREC_C64_BF16X3 || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->precision = iv;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_NPHI_RULE:
+      if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->nphi_rule = iv;
+      {
+        const int nphi = iv == 0 ? 2 * (p->L + 1) : 2 * p->L + 1;
+        p->n_dir = (p->L + 1) * nphi;
+        fmm::direction_grid(p->L, nphi, p->khat, p->weights);
+      }
+      return FMMFFT_OK;
+    case FMMFFT_KEY_NEAR_RULE:
+      if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->near_rule = iv;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_KAPPA:
+      if (!(v >= 0) || !std::isfinite(v)) return FMMFFT_ERR_INVALID_ARG;
+      p->kappa = v;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_PREFACTOR:
+      if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->prefactor = iv;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_TRUNC_RULE:
+      if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->trunc_rule = iv;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_PROFILE:
+      if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->profile = iv == 1;
+      return FMMFFT_OK;
+    default:
+      return FMMFFT_ERR_INVALID_ARG;
+  }
+}
+
+int fmmfft_compress(fmmfft_plan p) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!(p->format == FMMFFT_FORMAT_NONE ||
+        (p->format == FMMFFT_FORMAT_3D && p->decomp == FMMFFT_DECOMP_TUCKER)))
+    return FMMFFT_ERR_UNSUPPORTED;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  if (p->format == FMMFFT_FORMAT_NONE && !check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  release_operator(p);
+  const fmm::OperatorSpec s = spec_of(p);
+  int st;
+  if (p->format == FMMFFT_FORMAT_NONE) {
+    std::vector<std::vector<cdouble>> ops(p->n_dir);
+    fmm::parallel_for(p->n_dir, [&](int d) { fmm::fft_operator(s, &p->khat[3 * d], ops[d]); });
+    st = upload_plain(p, [&](int d) { return ops[d].data(); });
+  } else {
+    std::vector<fmm::Tucker3> tk(p->n_dir);
+    fmm::parallel_for(p->n_dir, [&](int d) {
+      std::vector<cdouble> T;
+      fmm::fft_operator(s, &p->khat[3 * d], T);
+      fmm::hosvd3(T, p->n, p->tol, p->trunc_rule, tk[d]);
+    });
+    for (int i = 0; i < 3; ++i) p->rmax[i] = 0;
+    for (auto& t : tk)
+      for (int i = 0; i < 3; ++i) p->rmax[i] = std::max(p->rmax[i], t.r[i]);
+    if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+    st = upload_tucker3d(p, tk);
+  }
+  if (st != FMMFFT_OK) return st;
+  if ((st = ensure_common(p)) != FMMFFT_OK) return st;
+  p->ready = true;
+  p->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return FMMFFT_OK;
+}
+
+int fmmfft_import_plain(fmmfft_plan p, const double* That) {
+  if (!p || !That || p->format != FMMFFT_FORMAT_NONE) return FMMFFT_ERR_INVALID_ARG;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  release_operator(p);
+  const size_t per = (size_t)p->n[0] * p->n[1] * p->n[2];
+  const cdouble* T = reinterpret_cast<const cdouble*>(That);
+  int st = upload_plain(p, [&](int d) { return T + per * d; });
+  if (st != FMMFFT_OK) return st;
+  if ((st = ensure_common(p)) != FMMFFT_OK) return st;
+  p->ready = true;
+  return FMMFFT_OK;
+}
+
+int fmmfft_import_tucker3d(fmmfft_plan p, const int* ranks, const double* core, const double* U1,
+                           const double* U2, const double* U3) {
+  if (!p || !ranks || !core || !U1 || !U2 || !U3) return FMMFFT_ERR_INVALID_ARG;
+  if (p->format != FMMFFT_FORMAT_3D || p->decomp != FMMFFT_DECOMP_TUCKER) return FMMFFT_ERR_INVALID_ARG;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  std::vector<fmm::Tucker3> tk(p->n_dir);
+  const cdouble* c = reinterpret_cast<const cdouble*>(core);
+  const cdouble* u[3] = {reinterpret_cast<const cdouble*>(U1), reinterpret_cast<const cdouble*>(U2),
+                         reinterpret_cast<const cdouble*>(U3)};
+  for (int d = 0; d < p->n_dir; ++d) {
+    for (int i = 0; i < 3; ++i) {
+      const int r = ranks[3 * d + i];
+      if (r < 1 || r > p->n[i]) return FMMFFT_ERR_INVALID_ARG;
+      tk[d].r[i] = r;
+    }
+    const size_t nc = (size_t)tk[d].r[0] * tk[d].r[1] * tk[d].r[2];
+    tk[d].core.assign(c, c + nc);
+    c += nc;
+    for (int i = 0; i < 3; ++i) {
+      const size_t nu = (size_t)p->n[i] * tk[d].r[i];
+      tk[d].U[i].assign(u[i], u[i] + nu);
+      u[i] += nu;
+    }
+  }
+  for (int i = 0; i < 3; ++i) p->rmax[i] = 0;
+  for (auto& t : tk)
+    for (int i = 0; i < 3; ++i) p->rmax[i] = std::max(p->rmax[i], t.r[i]);
+  if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  release_operator(p);
+  int st = upload_tucker3d(p, tk);
+  if (st != FMMFFT_OK) return st;
+  if ((st = ensure_common(p)) != FMMFFT_OK) return st;
+  p->ready = true;
+  return FMMFFT_OK;
+}
+
+int fmmfft_translate(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* stream) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
+  if (!S_in || !S_out || nrhs < 1 || nrhs > 4096) return FMMFFT_ERR_INVALID_ARG;
+  const size_t es = elem_bytes(p);
+  const size_t field = (size_t)p->K[0] * p->K[1] * p->K[2];
+  const size_t bytes = (size_t)p->n_dir * 2 * nrhs * field * es;
+  const char* i0 = (const char*)S_in;
+  const char* o0 = (const char*)S_out;
+  if (i0 < o0 + bytes && o0 < i0 + bytes) return FMMFFT_ERR_INVALID_ARG;
+  if (((uintptr_t)S_in | (uintptr_t)S_out) % es) return FMMFFT_ERR_INVALID_ARG;
+  const size_t inter = (size_t)p->n_dir * 2 * nrhs * p->n[0] * p->K[1] * p->K[2] * es;
+  if (inter > p->inter_bytes) {
+    if (p->d_inter) {
+      cudaStreamSynchronize((cudaStream_t)stream);
+      free_dev(p->d_inter);
+    }
+    p->inter_bytes = 0;
+    int st = dev_alloc(&p->d_inter, inter);
+    if (st != FMMFFT_OK) return st;
+    p->inter_bytes = inter;
+  }
+  fmm::TranslateArgs a = base_args(p);
+  a.nrhs = nrhs;
+  a.s_in = S_in;
+  a.s_out = S_out;
+  a.inter = p->d_inter;
+  a.stream = (cudaStream_t)stream;
+  p->last_stream = a.stream;
+  if (p->profile) {
+    if (!p->events[0])
+      for (auto& ev : p->events)
+        if (cudaEventCreate(&ev) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    a.events = p->events;
+    p->profiled_run = true;
+  }
+  cudaError_t e = fmm::launch_translate(a);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
+int fmmfft_translate_host(fmmfft_plan p, const void* S_in_host, void* S_out_host, int nrhs,
+                          void* stream) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
+  if (!S_in_host || !S_out_host || nrhs < 1 || nrhs > 4096) return FMMFFT_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)p->n_dir * 2 * nrhs * p->K[0] * p->K[1] * p->K[2] * elem_bytes(p);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (2 * bytes > p->io_bytes) {
+    if (p->d_io) {
+      cudaStreamSynchronize(s);
+      free_dev(p->d_io);
+    }
+    p->io_bytes = 0;
+    int st = dev_alloc(&p->d_io, 2 * bytes);
+    if (st != FMMFFT_OK) return st;
+    p->io_bytes = 2 * bytes;
+  }
+  char* din = (char*)p->d_io;
+  char* dout = din + bytes;
+  if (cudaMemcpyAsync(din, S_in_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  int st = fmmfft_translate(p, din, dout, nrhs, stream);
+  if (st != FMMFFT_OK) return st;
+  if (cudaMemcpyAsync(S_out_host, dout, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  return FMMFFT_OK;
+}
+
+int fmmfft_operator_host(fmmfft_plan p, int d, double* out) {
+  if (!p || !out || d < 0 || d >= p->n_dir) return FMMFFT_ERR_INVALID_ARG;
+  std::vector<cdouble> T;
+  fmm::fft_operator(spec_of(p), &p->khat[3 * d], T);
+  std::memcpy(out, T.data(), T.size() * sizeof(cdouble));
+  return FMMFFT_OK;
+}
+
+int fmmfft_compress_direction_host(fmmfft_plan p, int d, int* ranks, double* restored) {
+  if (!p || !ranks || d < 0 || d >= p->n_dir) return FMMFFT_ERR_INVALID_ARG;
+  if (p->format != FMMFFT_FORMAT_3D || p->decomp != FMMFFT_DECOMP_TUCKER) return FMMFFT_ERR_INVALID_ARG;
+  std::vector<cdouble> T;
+  fmm::fft_operator(spec_of(p), &p->khat[3 * d], T);
+  fmm::Tucker3 tk;
+  fmm::hosvd3(T, p->n, p->tol, p->trunc_rule, tk);
+  for (int i = 0; i < 3; ++i) ranks[i] = tk.r[i];
+  if (restored) {
+    const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+    const int r1 = tk.r[0], r2 = tk.r[1], r3 = tk.r[2];
+    cdouble* o = reinterpret_cast<cdouble*>(restored);
+    for (int x = 0; x < n1; ++x)
+      for (int y = 0; y < n2; ++y)
+        for (int z = 0; z < n3; ++z) {
+          cdouble acc(0.0, 0.0);
+          for (int a = 0; a < r1; ++a)
+            for (int b = 0; b < r2; ++b) {
+              const cdouble ab = tk.U[0][(size_t)x * r1 + a] * tk.U[1][(size_t)y * r2 + b];
+              const cdouble* c = &tk.core[((size_t)a * r2 + b) * r3];
+              cdouble s(0.0, 0.0);
+              for (int k = 0; k < r3; ++k) s += c[k] * tk.U[2][(size_t)z * r3 + k];
+              acc += ab * s;
+            }
+          o[((size_t)x * n2 + y) * n3 + z] = acc;
+        }
+  }
+  return FMMFFT_OK;
+}
+
+int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
+  if (!p || !o) return FMMFFT_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->n_dir = p->n_dir;
+  o->L = p->L;
+  for (int i = 0; i < 3; ++i) {
+    o->K[i] = p->K[i];
+    o->n[i] = p->n[i];
+    o->mean_rank[i] = p->mean_rank[i];
+  }
+  o->format = p->format;
+  o->decomp = p->decomp;
+  o->precision = p->precision;
+  for (int i = 0; i < 6; ++i) o->max_rank[i] = p->rmax[i];
+  o->elements_plain = p->elements_plain;
+  o->elements_compressed = p->elements_compressed;
+  o->saving = p->elements_plain ? 1.0 - (double)p->elements_compressed / (double)p->elements_plain : 0.0;
+  o->device_bytes_operator = p->bytes_operator;
+  o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes) + p->bytes_h;
+  o->setup_seconds = p->setup_seconds;
+  return FMMFFT_OK;
+}
+
+int fmmfft_plan_ranks(fmmfft_plan p, int* ranks) {
+  if (!p || !ranks || !p->ready || p->format != FMMFFT_FORMAT_3D) return FMMFFT_ERR_INVALID_ARG;
+  for (int d = 0; d < p->n_dir; ++d) {
+    ranks[3 * d] = p->desc[d].r1;
+    ranks[3 * d + 1] = p->desc[d].r2;
+    ranks[3 * d + 2] = p->desc[d].r3;
+  }
+  return FMMFFT_OK;
+}
+
+int fmmfft_plan_directions(fmmfft_plan p, double* khat, double* weights) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  if (khat) std::memcpy(khat, p->khat.data(), sizeof(double) * 3 * p->n_dir);
+  if (weights) std::memcpy(weights, p->weights.data(), sizeof(double) * p->n_dir);
+  return FMMFFT_OK;
+}
+
+int fmmfft_stage_times(fmmfft_plan p, float* ms) {
+  if (!p || !ms || !p->profiled_run) return FMMFFT_ERR_INVALID_ARG;
+  if (cudaEventSynchronize(p->events[FMMFFT_NUM_STAGES]) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  for (int i = 0; i < FMMFFT_NUM_STAGES; ++i)
+    if (cudaEventElapsedTime(&ms[i], p->events[i], p->events[i + 1]) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  return FMMFFT_OK;
+}
+
+int fmmfft_poll_status(fmmfft_plan p, int* device_status) {
+  if (!p || !device_status) return FMMFFT_ERR_INVALID_ARG;
+  *device_status = 0;
+  if (!p->d_status) return FMMFFT_OK;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  if (cudaMemcpy(device_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FMMFFT_ERR_CUDA;
+  if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  return FMMFFT_OK;
+}
+
+int fmmfft_plan_destroy(fmmfft_plan p) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  if (p->last_stream || p->d_status) cudaDeviceSynchronize();
+  release_operator(p);
+  free_dev(p->d_inter);
+  free_dev(p->d_io);
+  for (auto& ev : p->events)
+    if (ev) cudaEventDestroy(ev);
+  void* s = p->d_status;
+  free_dev(s);
+  delete p;
+  return FMMFFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// FP64 host set-up of the translation operators: directions, operator
+// samples (Eq. 7), circulant embedding and FFT (Sec. II.B), and the tensor
+// decompositions used to compress them (Algs. 1-3).  Independent of the CUDA
+// kernels; runs on the host cores.
+#pragma once
+
+#include <complex>
+#include <functional>
+#include <vector>
+
+namespace fmm {
+
+using cdouble = std::complex<double>;
+
+// Run fn(i) for i in [0, n) on the host cores.
+void parallel_for(int n, const std::function<void(int)>& fn);
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1], by Newton's method
+// on P_n from the asymptotic initial guesses.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Directions k_p (3 per direction) and weights, theta-major (Sec. II.A).
+void direction_grid(int L, int nphi, std::vector<double>& khat, std::vector<double>& w);
+
+struct OperatorSpec {
+  int K[3];
+  int n[3];
+  int L;
+  double a, k0;
+  int near_rule;      // 0 Chebyshev shell max|d_i| <= 1, 1 a|d| < kappa a sqrt(3)/2
+  double kappa;
+  int prefactor;      // 0 unit, 1 -k^2 eta / (16 pi^2)
+};
+
+// T~_p = FFT3(embed(T_p)) for direction khat, layout [x][y][z] (z fastest).
+void fft_operator(const OperatorSpec& s, const double* khat, std::vector<cdouble>& out);
+
+// In-place unnormalised DFT (sign -1 forward, +1 inverse) of a 3D array
+// [n0][n1][n2] (last index fastest), all powers of two.
+void fft3(std::vector<cdouble>& a, const int n[3], int sign);
+
+// Eigen-decomposition of a Hermitian n x n matrix (row-major, overwritten) by
+// cyclic Jacobi rotations.  Eigenvalues descending in `lam`, eigenvectors as
+// the columns of V (row-major n x n).
+void hermitian_eig(int n, std::vector<cdouble>& A, std::vector<double>& lam, std::vector<cdouble>& V);
+
+// Rank kept at per-step budget delta (rule 0: discarded energy; rule 1:
+// first normalised singular value below delta).  lam = squared singular values.
+int truncation_rank(const std::vector<double>& lam, double delta, int rule);
+
+struct Tucker3 {
+  int r[3];
+  std::vector<cdouble> core;   // r1 x r2 x r3
+  std::vector<cdouble> U[3];   // n_i x r_i
+};
+
+// HOSVD (Alg. 1) of a 3D tensor [n0][n1][n2] at tolerance gamma.
+void hosvd3(const std::vector<cdouble>& T, const int n[3], double gamma, int rule, Tucker3& out);
+
+}  // namespace fmm

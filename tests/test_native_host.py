@@ -1,0 +1,117 @@
+"""Host-side checks of the native library (no GPU needed).
+
+* the shared library loads and exports every function include/fmmfft.h declares;
+* argument validation of the plan life cycle;
+* the library's own FP64 set-up (directions, operator of Eq. 7 embedded and
+  FFT'ed as in Sec. II.B, HOSVD of Alg. 1) against the oracle.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import decomp as D
+from oracle import directions as dr
+from oracle import pipeline as pl
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fmmfft.h")
+
+
+def test_library_exports_every_declared_symbol(native):
+    names = set(re.findall(r"^\s*(?:int|const char\*)\s+(fmmfft_\w+)\s*\(", open(HEADER).read(), re.M))
+    assert len(names) >= 12
+    assert names == set(native.EXPORTED)
+    for n in names:
+        assert hasattr(native.lib(), n), n
+
+
+def test_status_strings(native):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert native.fmmfft_status_string(s)
+    assert native.fmmfft_status_string(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("args", [
+    (1, 4, 4, 0.5, 6.28, 3, 0, 0, 0.0),        # K < 2
+    (4, 4, 200, 0.5, 6.28, 3, 0, 0, 0.0),      # K > 128
+    (4, 4, 4, -0.5, 6.28, 3, 0, 0, 0.0),       # a <= 0
+    (4, 4, 4, 0.5, 0.0, 3, 0, 0, 0.0),         # k0 <= 0
+    (4, 4, 4, 0.5, 6.28, -1, 0, 0, 0.0),       # L < 0
+    (4, 4, 4, 0.5, 6.28, 3, 3, 0, 1e-3),       # 3D format without a decomposition
+    (4, 4, 4, 0.5, 6.28, 3, 0, 1, 1e-3),       # decomposition without a format
+    (4, 4, 4, 0.5, 6.28, 3, 3, 3, 1e-3),       # H-Tucker in the 3D format
+    (4, 4, 4, 0.5, 6.28, 3, 3, 1, 0.0),        # tol 0 with a decomposition
+    (4, 4, 4, 0.5, 6.28, 3, 7, 1, 1e-3),       # unknown format
+])
+def test_plan_create_rejects(native, args):
+    with pytest.raises(native.FmmfftError) as e:
+        native.fmmfft_plan_create(*args)
+    assert e.value.status == native.FMMFFT_ERR_INVALID_ARG
+
+
+def test_plan_set_and_translate_before_compress(native):
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, 3, 0, 0, 0.0)
+    try:
+        with pytest.raises(native.FmmfftError) as e:
+            native.fmmfft_plan_set(h, 99, 1)
+        assert e.value.status == native.FMMFFT_ERR_INVALID_ARG
+        with pytest.raises(native.FmmfftError):
+            native.fmmfft_plan_set(h, native.FMMFFT_KEY_PRECISION, 7)
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_NPHI_RULE, 1)
+        assert native.fmmfft_plan_stats(h)["n_dir"] == 4 * 7
+        with pytest.raises(native.FmmfftError) as e:
+            native.fmmfft_translate(h, 16, 4096, 1, 0)
+        assert e.value.status == native.FMMFFT_ERR_NOT_COMPRESSED
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("L,rule", [(3, 0), (5, 0), (8, 0), (6, 1)])
+def test_directions_match_oracle(native, L, rule):
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, L, 0, 0, 0.0)
+    try:
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_NPHI_RULE, rule)
+        kh, w = native.fmmfft_plan_directions(h)
+        kh2, w2 = dr.direction_grid(L, "baseline" if rule == 0 else "paper")
+        np.testing.assert_allclose(kh, kh2, atol=1e-14)
+        np.testing.assert_allclose(w, w2, atol=1e-14)
+        assert abs(w.sum() - 4 * np.pi) < 1e-12
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("K,L,near", [((4, 3, 5), 3, 0), ((8, 8, 8), 5, 0), ((6, 5, 4), 4, 1)])
+def test_operator_generator_matches_oracle(native, K, L, near):
+    h = native.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 0, 0, 0.0)
+    try:
+        if near:
+            native.fmmfft_plan_set(h, native.FMMFFT_KEY_NEAR_RULE, 1)
+        plan = pl.Plan(K=K, L=L, near_rule="kappa" if near else "chebyshev")
+        dirs = [0, plan.n_dir // 2, plan.n_dir - 1]
+        ref = pl.operators(plan, dirs)
+        for i, p in enumerate(dirs):
+            T = native.fmmfft_operator_host(h, p)
+            assert T.shape == plan.n
+            assert np.linalg.norm(T - ref[i]) <= 1e-11 * np.linalg.norm(ref[i])
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-4, 1e-6])
+def test_hosvd_setup_matches_oracle(native, tol):
+    K, L = (8, 8, 8), 5
+    h = native.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 3, 1, tol)
+    try:
+        plan = pl.Plan(K=K, L=L)
+        for p in (1, 40):
+            ranks, R = native.fmmfft_compress_direction_host(h, p)
+            T = pl.operators(plan, [p])[0]
+            tk = D.tucker_hosvd(T, tol)
+            assert ranks == tk.ranks
+            err = np.linalg.norm(R - T) / np.linalg.norm(T)
+            assert err <= tol
+            ref = np.linalg.norm(D.tucker_restore(tk) - T) / np.linalg.norm(T)
+            assert abs(err - ref) <= 1e-9 + 1e-6 * ref
+    finally:
+        native.fmmfft_plan_destroy(h)
