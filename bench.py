@@ -168,30 +168,62 @@ def run_cpu_baseline(ndirs: int):
 # ---------------------------------------------------------------------------
 # reference arm: the oracle as the reference implementation
 # ---------------------------------------------------------------------------
+def reference_child(steps: int, warmup: int):
+    """One BLAS thread.  A step translates one field of the workload with the
+    oracle (Eq. 5, FP64), its direction's Tucker-3D operator restored (Fig.
+    3(a)) whenever the direction changes; fields are taken in workload order
+    starting at direction 0.  Prints the per-step seconds."""
+    import numpy as np
+    from oracle import decomp as D
+    from oracle import pipeline as pl
+    from oracle import translate as tr
+    from seeded_inputs import field_spectra_rows
+
+    K, L, nrhs, seed = WL["K"], WL["L"], WL["nrhs"], WL["seed"]
+    plan = pl.Plan(K=K, L=L)
+    nf = 2 * nrhs
+    total = steps + warmup
+    dirs = sorted({f // nf for f in range(total)})
+    tks = {p: D.tucker_hosvd(pl.operators(plan, [p])[0], WL["tol"]) for p in dirs}
+    A = field_spectra_rows(seed, plan.n_dir, nrhs, K, np.arange(total))
+    secs = []
+    cur, That = None, None
+    for f in range(total):
+        t0 = time.perf_counter()
+        p = f // nf
+        if p != cur:
+            tk = tks[p]
+            That = D.tucker3d_restore_steps(tk.core, *tk.factors)
+            cur = p
+        tr.translate_field_fft(That, A[f])
+        secs.append(time.perf_counter() - t0)
+    print(json.dumps({"seconds": secs[warmup:]}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    steps = []
-    cpu = None
-    for i in range(args.warmup + args.steps):
-        cpu = run_cpu_baseline(1)
-        if i >= args.warmup:
-            steps.append(cpu)
-    if any(s["value"] is None for s in steps):
-        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + steps[0].get("error", "")}))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--reference-child",
+                        str(args.steps), str(args.warmup)],
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + r.stderr[-300:]}))
         return
-    secs = [s["seconds"] for s in steps]
-    val = sum(8 * 64 ** 3 for _ in steps) / sum(secs) / 1e9
+    secs = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    units = 64 ** 3
+    val = units * len(secs) / sum(secs) / 1e9
+    sample = (f"{len(secs)} fields (one per step) of the 32^3-box L=8 Tucker-3D workload, taken in "
+              f"workload order; FP64 NumPy oracle (restore + FFT translation), 1 thread")
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
            "config": {"workload": WL["name"], "K": list(WL["K"]), "L": WL["L"], "n_dir": 162,
-                      "nrhs": WL["nrhs"], "tol": WL["tol"],
-                      "step": "1 of 162 directions (8 fields) per step: the full workload takes ~3 min of CPU"},
-           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": steps[0]["sample"].replace("1 of 162", "1 of 162")},
+                      "nrhs": WL["nrhs"], "tol": WL["tol"], "step": "one field of the workload per step"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -225,14 +257,21 @@ def step_flops(K, n, n_dir, nrhs, ranks=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nrhs", type=int, default=0, help="override the RHS count (profiling cases)")
+    ap.add_argument("--only", default="both", choices=["both", "compressed", "plain"])
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-baseline-child", type=int, default=0)
+    ap.add_argument("--reference-child", type=int, nargs=2, default=None)
     args = ap.parse_args()
     if args.cpu_baseline_child:
         cpu_baseline_child(args.cpu_baseline_child)
+        return
+    if args.reference_child:
+        reference_child(*args.reference_child)
         return
     if args.impl == "reference":
         run_reference(args)
@@ -257,16 +296,20 @@ def main():
         from paper_2010_00520_gb300 import build as _b
         _b.build()
 
-    K, L, nrhs = WL["K"], WL["L"], WL["nrhs"]
+    K, L, nrhs = WL["K"], WL["L"], (args.nrhs or WL["nrhs"])
     plans = {}
-    for name, fmt, dec, tol in (("compressed", 3, 1, WL["tol"]), ("plain", 0, 0, 0.0)):
+    arms = [a for a in (("compressed", 3, 1, WL["tol"]), ("plain", 0, 0, 0.0))
+            if args.only in ("both", a[0])]
+    for name, fmt, dec, tol in arms:
         h = F.fmmfft_plan_create(K[0], K[1], K[2], WL["a"], WL["k0"], L, fmt, dec, tol)
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64)
         F.fmmfft_compress(h)
         plans[name] = h
-    st = F.fmmfft_plan_stats(plans["compressed"])
+    main_arm = "compressed" if "compressed" in plans else "plain"
+    st = F.fmmfft_plan_stats(plans[main_arm])
     n, n_dir = tuple(st["n"]), st["n_dir"]
-    ranks = [tuple(int(v) for v in r) for r in F.fmmfft_plan_ranks(plans["compressed"])]
+    ranks = ([tuple(int(v) for v in r) for r in F.fmmfft_plan_ranks(plans["compressed"])]
+             if "compressed" in plans else None)
     S_host = field_spectra(WL["seed"], n_dir, nrhs, K).astype(np.complex64)
     x = torch.from_numpy(S_host).to("cuda")
     y = torch.empty_like(x)
@@ -297,86 +340,93 @@ def main():
             ms = float(t.item())
         return ms
 
+    units = _units(n, n_dir, nrhs)
     clocks = ClockSampler(local)
     clocks.start()
-    ms_comp = timed(plans["compressed"], args.steps)
-    ms_plain = timed(plans["plain"], args.steps)
+    ms = {name: timed(h, args.steps) for name, h in plans.items()}
     clk = clocks.stop()
-    units = _units(n, n_dir, nrhs)
-    value = world * units / (ms_comp * 1e-3) / 1e9
-    value_plain = world * units / (ms_plain * 1e-3) / 1e9
     for h in plans.values():
         assert F.fmmfft_poll_status(h) == 0
+    value = {name: world * units / (t * 1e-3) / 1e9 for name, t in ms.items()}
 
-    # per-stage device times of the compressed step (events on the launch stream)
+    # per-stage device times (CUDA events on the launch stream, between kernels)
     stage = {}
     for name, h in plans.items():
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PROFILE, 1)
         acc = [0.0] * F.FMMFFT_NUM_STAGES
-        for _ in range(args.steps):
+        nst = min(args.steps, 50)
+        for _ in range(nst):
             F.fmmfft_translate(h, x, y, nrhs, stream)
             t = F.fmmfft_stage_times(h)
             acc = [a + b for a, b in zip(acc, t)]
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PROFILE, 0)
-        stage[name] = {k: v / args.steps for k, v in zip(("restore", "xfwd", "yz", "xinv"), acc)}
+        stage[name] = {k: v / nst for k, v in zip(("restore", "xfwd", "yz", "xinv"), acc)}
 
-    # end to end through the host-buffer entry point (pinned memory)
-    hin = torch.from_numpy(S_host).pin_memory()
-    hout = torch.empty_like(hin).pin_memory()
-    for _ in range(2):
-        F.fmmfft_translate_host(plans["compressed"], hin, hout, nrhs, stream)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        F.fmmfft_translate_host(plans["compressed"], hin, hout, nrhs, stream)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
     io_bytes = S_host.nbytes
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the host-buffer entry point (pinned memory)
+        hin = torch.from_numpy(S_host).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for _ in range(2):
+            F.fmmfft_translate_host(plans[main_arm], hin, hout, nrhs, stream)
+        barrier()
+        ne = min(args.steps, 50)
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            F.fmmfft_translate_host(plans[main_arm], hin, hout, nrhs, stream)
+        e2e_s = (time.perf_counter() - t0) / ne
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * units / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+               "d2h_bytes_per_step": io_bytes}
 
     peaks, peak_src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s, FMA = 2 flops
-    yz_ms = stage["compressed"]["yz"]
+    yz_ms = stage[main_arm]["yz"]
     yz_fl = yz_flops(K, n, n_dir, nrhs, ranks)
     achieved = yz_fl / (yz_ms * 1e-3) / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "yz_kernel_tucker3d_32cube_L8.traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and main_arm == "compressed":
         with open(prof) as f:
             traffic = json.load(f).get("dram_bytes_per_launch")
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_comp, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value[main_arm], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms[main_arm], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
-        "config": {"workload": WL["name"], "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
-                   "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d", "tol": WL["tol"],
-                   "precision": "FP32 FFTs and FP32 restores",
-                   "l2": "inputs (340 MB) and outputs (340 MB) each larger than the 129 MB L2; no flush"},
-        "plain": {"value": value_plain, "ms_per_step": ms_plain},
-        "ratio_compressed_over_plain_time": ms_comp / ms_plain,
-        "memory": {"operator_bytes_compressed": st["device_bytes_operator"],
-                   "operator_bytes_plain": F.fmmfft_plan_stats(plans["plain"])["device_bytes_operator"],
-                   "saving": st["saving"], "max_rank": st["max_rank"][:3],
-                   "mean_rank": [round(v, 2) for v in st["mean_rank"]]},
+        "config": {"workload": WL["name"] if nrhs == WL["nrhs"] else WL["name"].replace("4rhs", f"{nrhs}rhs"),
+                   "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
+                   "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d" if main_arm == "compressed" else "none",
+                   "tol": WL["tol"], "precision": "FP32 FFTs and FP32 restores",
+                   "l2": "inputs and outputs each larger than the 129 MB L2; no flush"},
         "stages_ms": stage,
-        "roofline": {"kernel": "yz_kernel (Tucker-3D slab restore + y/z FFTs + Hadamard)", "bound": "alu",
+        "roofline": {"kernel": "yz_kernel (slab restore + y/z FFTs + Hadamard)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic,
                      "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({peak_src} clock)",
                      "flops_model": "nominal 5 N log2 N per complex DFT line + 6 per Hadamard point + 8 per complex MAC of the restore"},
         "hbm": {"algorithmic_bytes_per_step": step_bytes,
-                "achieved_gbs": step_bytes / (ms_comp * 1e-3) / 1e9,
-                "peak_gbs": peaks.get("hbm_gbs"), "frac": step_bytes / (ms_comp * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
-        "step_tflops_nominal": step_flops(K, n, n_dir, nrhs, ranks) / (ms_comp * 1e-3) / 1e12,
+                "achieved_gbs": step_bytes / (ms[main_arm] * 1e-3) / 1e9,
+                "peak_gbs": peaks.get("hbm_gbs"),
+                "frac": step_bytes / (ms[main_arm] * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+        "step_tflops_nominal": step_flops(K, n, n_dir, nrhs, ranks) / (ms[main_arm] * 1e-3) / 1e12,
         "clocks": clk,
-        "e2e": {"value": world * units / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
-                "d2h_bytes_per_step": io_bytes},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (4 if main_arm == "compressed" else 3) * args.steps,
     }
+    if "plain" in plans and "compressed" in plans:
+        out["plain"] = {"value": value["plain"], "ms_per_step": ms["plain"]}
+        out["ratio_compressed_over_plain_time"] = ms["compressed"] / ms["plain"]
+        out["memory"] = {"operator_bytes_compressed": st["device_bytes_operator"],
+                         "operator_bytes_plain": F.fmmfft_plan_stats(plans["plain"])["device_bytes_operator"],
+                         "saving": st["saving"], "max_rank": st["max_rank"][:3],
+                         "mean_rank": [round(v, 2) for v in st["mean_rank"]]}
+    if e2e is not None:
+        out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = run_cpu_baseline(CPU_SAMPLE_DIRS)
     for h in plans.values():
