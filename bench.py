@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=0, help="override the RHS count (profiling cases)")
     ap.add_argument("--only", default="both", choices=["both", "compressed", "plain"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--yz-variant", type=int, default=2, choices=[0, 1, 2],
+                    help="y/z kernel variant (2: shared-memory lines; 0: register lines, 256 threads; 1: 128 threads)")
     ap.add_argument("--cpu-baseline-child", type=int, default=0)
     ap.add_argument("--reference-child", type=int, nargs=2, default=None)
     args = ap.parse_args()
@@ -304,6 +306,7 @@ def main():
         h = F.fmmfft_plan_create(K[0], K[1], K[2], WL["a"], WL["k0"], L, fmt, dec, tol)
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64)
         F.fmmfft_compress(h)
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_YZ_VARIANT, args.yz_variant)
         plans[name] = h
     main_arm = "compressed" if "compressed" in plans else "plain"
     st = F.fmmfft_plan_stats(plans[main_arm])
@@ -393,7 +396,10 @@ def main():
     prof = os.path.join(ROOT, "profiles", "yz_kernel_tucker3d_32cube_L8.traffic.json")
     if os.path.exists(prof) and main_arm == "compressed":
         with open(prof) as f:
-            traffic = json.load(f).get("dram_bytes_per_launch")
+            tj = json.load(f)
+        # counters only count for the kernel they were taken on
+        if tj.get("yz_variant") == args.yz_variant and nrhs == WL["nrhs"]:
+            traffic = tj.get("dram_bytes_per_launch")
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
         "metric": METRIC, "value": value[main_arm], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -402,10 +408,13 @@ def main():
         "config": {"workload": WL["name"] if nrhs == WL["nrhs"] else WL["name"].replace("4rhs", f"{nrhs}rhs"),
                    "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
                    "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d" if main_arm == "compressed" else "none",
-                   "tol": WL["tol"], "precision": "FP32 FFTs and FP32 restores",
+                   "tol": WL["tol"], "precision": "FP32 FFTs and FP32 restores", "yz_variant": args.yz_variant,
                    "l2": "inputs and outputs each larger than the 129 MB L2; no flush"},
         "stages_ms": stage,
-        "roofline": {"kernel": "yz_kernel (slab restore + y/z FFTs + Hadamard)", "bound": "alu",
+        "roofline": {"kernel": ("yz2_kernel (slab restore + register-line y/z FFTs + Hadamard)"
+                                if args.yz_variant in (0, 1) else
+                                "yz_kernel (slab restore + shared-memory-line y/z FFTs + Hadamard)"),
+                     "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic,
                      "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({peak_src} clock)",

@@ -98,9 +98,16 @@ enum {
   FMMFFT_KEY_PREFACTOR = 5,      /* 0: c = 1 (default); 1: c = -k^2 eta/(16 pi^2) (Eq. 7) */
   FMMFFT_KEY_TRUNC_RULE = 6,     /* 0: discarded-energy rule (default);
                                     1: normalised singular value < gamma/sqrt(d) */
-  FMMFFT_KEY_PROFILE = 7         /* 1: record CUDA events between the kernels of
+  FMMFFT_KEY_PROFILE = 7,        /* 1: record CUDA events between the kernels of
                                     each translation (fmmfft_stage_times); may
                                     be changed at any time                      */
+  FMMFFT_KEY_YZ_VARIANT = 8      /* kernel of the y/z pass: 2 = line transforms
+                                    through shared memory (default); 0 = line
+                                    transforms in registers, 256-thread blocks;
+                                    1 = the same with 128-thread blocks.  Variants
+                                    0 and 1 cover complex64 with n2, n3 <= 64;
+                                    elsewhere 2 runs.  May be changed at any time;
+                                    the results agree to rounding.               */
 };
 
 /* Stages of one translation, in launch order (fmmfft_stage_times). */

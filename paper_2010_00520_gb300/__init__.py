@@ -40,6 +40,7 @@ FMMFFT_KEY_KAPPA = 4
 FMMFFT_KEY_PREFACTOR = 5
 FMMFFT_KEY_TRUNC_RULE = 6
 FMMFFT_KEY_PROFILE = 7
+FMMFFT_KEY_YZ_VARIANT = 8
 FMMFFT_STAGE_RESTORE, FMMFFT_STAGE_XFWD, FMMFFT_STAGE_YZ, FMMFFT_STAGE_XINV = 0, 1, 2, 3
 FMMFFT_NUM_STAGES = 4
 
@@ -256,7 +257,7 @@ class Plan:
         keys = {"precision": FMMFFT_KEY_PRECISION, "nphi_rule": FMMFFT_KEY_NPHI_RULE,
                 "near_rule": FMMFFT_KEY_NEAR_RULE, "kappa": FMMFFT_KEY_KAPPA,
                 "prefactor": FMMFFT_KEY_PREFACTOR, "trunc_rule": FMMFFT_KEY_TRUNC_RULE,
-                "profile": FMMFFT_KEY_PROFILE}
+                "profile": FMMFFT_KEY_PROFILE, "yz_variant": FMMFFT_KEY_YZ_VARIANT}
         for k, v in opts.items():
             fmmfft_plan_set(self.handle, keys[k], v)
 

@@ -36,6 +36,7 @@ struct fmmfft_plan_s {
   int* d_status = nullptr;
   cudaStream_t last_stream = nullptr;
   bool profile = false;
+  int yz_variant = 2;
   bool profiled_run = false;
   cudaEvent_t events[FMMFFT_NUM_STAGES + 1] = {};
   // host-side bookkeeping
@@ -144,6 +145,7 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   a.t3_pack = p->d_pack;
   a.t3_h = p->d_h;
   a.status = p->d_status;
+  a.yz_variant = p->yz_variant;
   return a;
 }
 
@@ -298,7 +300,8 @@ int fmmfft_plan_create(fmmfft_plan* out, int Nx, int Ny, int Nz, double a, doubl
 }
 
 int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
-  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE)) return FMMFFT_ERR_INVALID_ARG;
+  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE && key != FMMFFT_KEY_YZ_VARIANT))
+    return FMMFFT_ERR_INVALID_ARG;
   const int iv = (int)v;
   switch (key) {
     case FMMFFT_KEY_PRECISION:
@@ -333,6 +336,17 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
     case FMMFFT_KEY_PROFILE:
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->profile = iv == 1;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_YZ_VARIANT:
+      if (iv < 0 || iv > 2 || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      {
+        const int old = p->yz_variant;
+        p->yz_variant = iv;
+        if (p->ready && !check_supported(p)) {
+          p->yz_variant = old;
+          return FMMFFT_ERR_UNSUPPORTED;
+        }
+      }
       return FMMFFT_OK;
     default:
       return FMMFFT_ERR_INVALID_ARG;

@@ -45,6 +45,7 @@ struct TranslateArgs {
   int t3_rmax[3];                // largest r1, r2, r3
   int* status;                   // device status word
   cudaEvent_t* events;           // FMMFFT_NUM_STAGES + 1 events, or null
+  int yz_variant;                // FMMFFT_KEY_YZ_VARIANT
   cudaStream_t stream;
 };
 

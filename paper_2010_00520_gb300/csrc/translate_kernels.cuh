@@ -44,6 +44,7 @@ struct YZParams {
   double scale;        // restore scale 1 / (n1 n2 n3)
   int rmax2, rmax3;    // shared-memory capacity of the launch (ranks)
   int* status;
+  int variant;         // yz launch variant (FMMFFT_KEY_YZ_VARIANT)
 };
 
 struct HParams {
@@ -285,6 +286,180 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
     for (int i = tid; i < Kz * Ky; i += kThreads) {
       const int z = i / Ky, y = i - z * Ky;
       io[i] = plane[z * PY + y];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// yz pass, lane-split version (n2, n3 <= 64).  Every line transform runs in
+// registers (one or two lanes per line, see Split<N>); shared memory holds the
+// operator slab Tt[z][y] and G field planes [z][y] (pitch n2 + 1), so the y,
+// z, Hadamard and inverse steps of G fields of direction p run per group of
+// five barriers.  Inputs of a forward line beyond its K entries are never
+// read, so no zero padding is stored.
+// ---------------------------------------------------------------------------
+template <typename R, int N2, int N3, int NT>
+struct YZ2Layout {
+  static constexpr int L2 = Split<N2>::L, L3 = Split<N3>::L;
+  static constexpr int G = (NT / (N2 * L3)) > 0 ? (NT / (N2 * L3)) : 1;  // planes
+  static constexpr int PP = N2 + 1;    // plane pitch
+  // slab pitch: with two lanes per z-line, lanes l = 0, 1 read slab rows 2m
+  // and 2m + 1 of the same column; a pitch of 8 (mod 16) complex elements puts
+  // them in different bank pairs
+  static constexpr int PT = (L3 == 2 && N2 % 16 == 0) ? N2 + 8 : N2;
+  static constexpr size_t slab_elems = (size_t)N3 * PT;
+  static constexpr size_t planes_elems = (size_t)G * N3 * PP;
+  static size_t restore_elems(int r2, int r3) {
+    const size_t r2p = (size_t)(r2 | 1);
+    const size_t a = (size_t)r3 * r2p + (size_t)r2 * (N2 + 1), b = (size_t)N3 * r3;
+    return (size_t)r3 * N2 + (a > b ? a : b);
+  }
+  static size_t smem_bytes(int fmt, int r2, int r3) {
+    size_t work = planes_elems;
+    if (fmt == 1) { const size_t r = restore_elems(r2, r3); if (r > work) work = r; }
+    return sizeof(cx<R>) * (slab_elems + work);
+  }
+};
+
+// Tucker-3D slab restore (Fig. 3(a) steps 2-3) into Tt[z * pt + y], scaled.
+template <typename R, int N2, int N3, int NT>
+__device__ __forceinline__ void restore_slab_tucker3d(const YZParams& P, int p, int x, cx<R>* Tt, int pt,
+                                                      cx<R>* work) {
+  using C = cx<R>;
+  const Tucker3DDesc d = P.desc[p];
+  const int r2 = d.r2, r3 = d.r3, r2p = d.r2 | 1;
+  const int tid = threadIdx.x;
+  const C* pack = reinterpret_cast<const C*>(P.pack);
+  const C* H = reinterpret_cast<const C*>(P.hbuf) + d.off_h + (size_t)x * r2 * r3;
+  C* Gt = work;                              // r3 x N2
+  C* Ht = Gt + r3 * N2;                      // r3 x r2p   (Ht[c][b] = H[b][c])
+  C* U2t = Ht + r3 * r2p;                    // r2 x (N2+1) (U2t[b][y] = U2[y][b])
+  C* U3s = Ht;                               // N3 x r3 once Gt is formed
+  for (int i = tid; i < r2 * r3; i += NT) {
+    const int b = i / r3, c = i - b * r3;
+    Ht[c * r2p + b] = H[i];
+  }
+  for (int i = tid; i < N2 * r2; i += NT) {
+    const int y = i / r2, b = i - y * r2;
+    U2t[b * (N2 + 1) + y] = pack[d.off_u2 + i];
+  }
+  __syncthreads();
+  block_cgemm<8, (N2 >= 64 ? 2 : 1), C, NT / 32>(r3, N2, r2, Ht, r2p, U2t, N2 + 1, Gt, N2, (R)1);
+  __syncthreads();
+  for (int i = tid; i < N3 * r3; i += NT) U3s[i] = pack[d.off_u3 + i];
+  __syncthreads();
+  block_cgemm<8, (N2 >= 64 ? 2 : 1), C, NT / 32>(N3, N2, r3, U3s, r3, Gt, N2, Tt, pt, (R)P.scale);
+}
+
+template <typename R, int N2, int N3, int FMT, int NT>
+__global__ void __launch_bounds__(NT) yz2_kernel(YZParams P) {
+  using C = cx<R>;
+  using LY = YZ2Layout<R, N2, N3, NT>;
+  constexpr int L2 = LY::L2, L3 = LY::L3, G = LY::G, PP = LY::PP, PT = LY::PT;
+  constexpr int M2 = Split<N2>::M, M3 = Split<N3>::M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Tt = reinterpret_cast<C*>(smem_raw);       // N3 x PT
+  C* planes = Tt + LY::slab_elems;              // G x N3 x PP
+  const int x = blockIdx.x, p = blockIdx.y;
+  const int tid = threadIdx.x;
+
+  if constexpr (FMT == 0) {
+    const C* op = reinterpret_cast<const C*>(P.op) + ((size_t)p * P.n1 + x) * (N3 * N2);
+    for (int i = tid; i < N3 * N2; i += NT) {
+      const int z = i / N2, y = i - z * N2;
+      Tt[z * PT + y] = op[i];
+    }
+  } else {
+    const Tucker3DDesc d = P.desc[p];
+    if (d.r2 > P.rmax2 || d.r3 > P.rmax3) {
+      if (tid == 0) atomicOr(P.status, kStatusRankOverflow);
+      return;
+    }
+    restore_slab_tucker3d<R, N2, N3, NT>(P, p, x, Tt, PT, planes);
+  }
+
+  const int Ky = P.Ky, Kz = P.Kz;
+  const int fsz = Kz * Ky;
+  C* inter = reinterpret_cast<C*>(P.inter);
+#pragma unroll 1
+  for (int g0 = 0; g0 < P.nf; g0 += G) {
+    const int ng = min(G, P.nf - g0);
+    __syncthreads();
+    // fields g0 .. g0 + ng - 1 into planes rows z < Kz, columns y < Ky
+    for (int i = tid; i < ng * fsz; i += NT) {
+      const int j = i / fsz, r = i - j * fsz;
+      const int z = r / Ky, y = r - z * Ky;
+      const size_t f = (size_t)p * P.nf + g0 + j;
+      planes[(j * N3 + z) * PP + y] = inter[(f * P.n1 + x) * fsz + r];
+    }
+    __syncthreads();
+    // forward y: rows (j, z < Kz); inputs y < Ky, all n2 outputs
+    {
+      const int l = tid % L2;
+#pragma unroll 1
+      for (int base = 0; base < ng * Kz; base += NT / L2) {
+        const int li = base + tid / L2;
+        const bool act = li < ng * Kz;
+        const int j = act ? li / Kz : 0, z = act ? li - (li / Kz) * Kz : 0;
+        C* row = planes + (j * N3 + z) * PP;
+        C v[M2];
+        if (act) split_load_head<N2>(v, row, 1, Ky);
+        __syncwarp();
+        if (act) {
+          split_fwd<N2>(v, l);
+#pragma unroll
+          for (int m = 0; m < M2; ++m) row[L2 * m + l] = v[m];
+        }
+      }
+    }
+    __syncthreads();
+    // z: forward, Hadamard with the slab, inverse; columns (j, y < n2)
+    {
+      const int l = tid % L3;
+#pragma unroll 1
+      for (int base = 0; base < ng * N2; base += NT / L3) {
+        const int li = base + tid / L3;
+        const bool act = li < ng * N2;
+        const int j = act ? li / N2 : 0, col = act ? li % N2 : 0;
+        C* cl = planes + j * N3 * PP + col;
+        C v[M3];
+        if (act) split_load_head<N3>(v, cl, PP, Kz);
+        __syncwarp();
+        if (act) {
+          split_fwd<N3>(v, l);
+#pragma unroll
+          for (int m = 0; m < M3; ++m) v[m] = cmul(v[m], Tt[(L3 * m + l) * PT + col]);
+          split_inv<N3>(v, l);
+        }
+        split_inv_store<N3>(v, cl, PP, Kz, l, act);
+      }
+    }
+    __syncthreads();
+    // inverse y: rows (j, z < Kz), outputs y < Ky
+    {
+      const int l = tid % L2;
+#pragma unroll 1
+      for (int base = 0; base < ng * Kz; base += NT / L2) {
+        const int li = base + tid / L2;
+        const bool act = li < ng * Kz;
+        const int j = act ? li / Kz : 0, z = act ? li - (li / Kz) * Kz : 0;
+        C* row = planes + (j * N3 + z) * PP;
+        C v[M2];
+        if (act) {
+#pragma unroll
+          for (int m = 0; m < M2; ++m) v[m] = row[L2 * m + l];
+        }
+        __syncwarp();
+        if (act) split_inv<N2>(v, l);
+        split_inv_store<N2>(v, row, 1, Ky, l, act);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < ng * fsz; i += NT) {
+      const int j = i / fsz, r = i - j * fsz;
+      const int z = r / Ky, y = r - z * Ky;
+      const size_t f = (size_t)p * P.nf + g0 + j;
+      inter[(f * P.n1 + x) * fsz + r] = planes[(j * N3 + z) * PP + y];
     }
   }
 }

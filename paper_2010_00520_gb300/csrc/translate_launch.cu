@@ -5,10 +5,10 @@ namespace fmm {
 
 cudaError_t launch_yz_f32(const YZParams& P, int n2, int n3, int fmt, dim3 grid, size_t smem,
                           cudaStream_t s);
-size_t yz_smem_f32(int n2, int n3, int fmt, int r2, int r3);
+size_t yz_smem_f32(int n2, int n3, int fmt, int r2, int r3, int variant);
 cudaError_t launch_yz_f64(const YZParams& P, int n2, int n3, int fmt, dim3 grid, size_t smem,
                           cudaStream_t s);
-size_t yz_smem_f64(int n2, int n3, int fmt, int r2, int r3);
+size_t yz_smem_f64(int n2, int n3, int fmt, int r2, int r3, int variant);
 
 static const size_t kMaxSmem = 227 * 1024;
 static const int kHCols = 128;
@@ -63,8 +63,8 @@ static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (
 size_t yz_smem_bytes(const TranslateArgs& a) {
   const int fmt = (a.format == FMMFFT_FORMAT_NONE) ? 0 : 1;
   const int r2 = a.t3_rmax[1], r3 = a.t3_rmax[2];
-  return a.precision == FMMFFT_PREC_C128 ? yz_smem_f64(a.n[1], a.n[2], fmt, r2, r3)
-                                         : yz_smem_f32(a.n[1], a.n[2], fmt, r2, r3);
+  return a.precision == FMMFFT_PREC_C128 ? yz_smem_f64(a.n[1], a.n[2], fmt, r2, r3, a.yz_variant)
+                                         : yz_smem_f32(a.n[1], a.n[2], fmt, r2, r3, a.yz_variant);
 }
 
 static size_t h_smem_bytes(const TranslateArgs& a) {
@@ -143,6 +143,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   Y.rmax2 = a.t3_rmax[1];
   Y.rmax3 = a.t3_rmax[2];
   Y.status = a.status;
+  Y.variant = a.yz_variant;
   const int fmt = tucker ? 1 : 0;
   const size_t smem = yz_smem_bytes(a);
   dim3 grid(a.n[0], a.n_dir);
