@@ -62,7 +62,9 @@ enum {
   FMMFFT_ERR_CUDA = -4,          /* a CUDA runtime call or launch failed    */
   FMMFFT_ERR_UNSUPPORTED = -5,   /* valid request outside this build's limits */
   FMMFFT_ERR_DEVICE = -6,        /* a kernel reported a failure (status word) */
-  FMMFFT_ERR_IO = -7             /* file could not be read or written       */
+  FMMFFT_ERR_IO = -7,            /* file could not be read or written       */
+  FMMFFT_ERR_TOO_LARGE = -8      /* needs more scratch than the fixed buffer of
+                                    fmmfft_translate_noalloc holds           */
 };
 
 /* ---- storage format and decomposition (Sec. II.B) ---------------------- */
@@ -199,6 +201,35 @@ int fmmfft_import_tucker3d(fmmfft_plan plan, const int* ranks, const double* cor
  * (a failure a kernel of an earlier call reported through the status word).
  */
 int fmmfft_translate(fmmfft_plan plan, const void* S_in, void* S_out, int nrhs, void* stream);
+
+/*
+ * Allocation-free variant of fmmfft_translate (the paper has no counterpart;
+ * this is an interface for callers).  Some callers cannot call cudaMalloc
+ * while they translate: an iterative solver that runs inside a framework
+ * whose memory pool owns the device memory, or a time-critical loop where
+ * cudaMalloc / cudaFree would synchronise the device and stall other streams.
+ * fmmfft_translate allocates its intermediate buffer on its first call (and
+ * again when nrhs grows); this entry point never does.  Its intermediate
+ * (the x-transformed fields, n_dir * 2 * nrhs * n1 * Ky * Kz complex) lives in
+ * one file-scope device array of FMMFFT_NOALLOC_SCRATCH_BYTES (32 MiB), which
+ * every GPU that loads this library holds until the process exits.  The plan's
+ * own operator storage, set up by fmmfft_compress or an import, is used as is.
+ *
+ * Arguments, layouts, ownership and results are those of fmmfft_translate;
+ * FMMFFT_KEY_PROFILE is ignored (no stage times are recorded).
+ * Set-up: the first call on a device, with that device current, looks up the
+ * device address of the array (cudaGetSymbolAddress); make that first call
+ * before any stream capture begins.
+ * Sharing: every call, from any plan or thread, uses the same array.  Calls
+ * whose kernels overlap on the GPU (different streams, or host threads
+ * without ordering between them) race on it and give wrong results; order
+ * them on one stream.  Nothing needs clearing between calls: the first kernel
+ * of a call writes every scratch element that the later ones read.
+ * Errors: those of fmmfft_translate except OOM; FMMFFT_ERR_TOO_LARGE (checked
+ * before anything is launched) when the intermediate exceeds the array.
+ */
+#define FMMFFT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int fmmfft_translate_noalloc(fmmfft_plan plan, const void* S_in, void* S_out, int nrhs, void* stream);
 
 /*
  * As fmmfft_translate with HOST field buffers: copies S_in to the device,

@@ -29,6 +29,8 @@ FMMFFT_ERR_CUDA = -4
 FMMFFT_ERR_UNSUPPORTED = -5
 FMMFFT_ERR_DEVICE = -6
 FMMFFT_ERR_IO = -7
+FMMFFT_ERR_TOO_LARGE = -8
+FMMFFT_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 FMMFFT_FORMAT_NONE, FMMFFT_FORMAT_3D, FMMFFT_FORMAT_4D = 0, 3, 4
 FMMFFT_DECOMP_NONE, FMMFFT_DECOMP_TUCKER, FMMFFT_DECOMP_TT, FMMFFT_DECOMP_HTUCKER = 0, 1, 2, 3
@@ -50,7 +52,7 @@ EXPORTED = (
     "fmmfft_import_tucker3d", "fmmfft_translate", "fmmfft_translate_host", "fmmfft_plan_stats",
     "fmmfft_plan_directions", "fmmfft_poll_status", "fmmfft_plan_destroy", "fmmfft_status_string",
     "fmmfft_operator_host", "fmmfft_compress_direction_host", "fmmfft_stage_times",
-    "fmmfft_plan_ranks",
+    "fmmfft_plan_ranks", "fmmfft_translate_noalloc",
 )
 
 
@@ -92,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "fmmfft_import_tucker3d": [vp, ip, dp, dp, dp, dp],
         "fmmfft_translate": [vp, vp, vp, i, vp],
         "fmmfft_translate_host": [vp, vp, vp, i, vp],
+        "fmmfft_translate_noalloc": [vp, vp, vp, i, vp],
         "fmmfft_plan_stats": [vp, ctypes.POINTER(_Stats)],
         "fmmfft_plan_directions": [vp, dp, dp],
         "fmmfft_poll_status": [vp, ip],
@@ -184,6 +187,15 @@ def fmmfft_import_tucker3d(plan, ranks, core, U1, U2, U3):
 def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):
     _check(lib().fmmfft_translate(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
            "fmmfft_translate")
+
+
+def fmmfft_translate_noalloc(plan, S_in, S_out, nrhs, stream=None):
+    """fmmfft_translate without any device allocation: the intermediate lives
+    in the library's fixed 32 MiB device array (shared by every call; order
+    calls on one stream).  Raises FmmfftError(FMMFFT_ERR_TOO_LARGE) when the
+    workload's intermediate does not fit."""
+    _check(lib().fmmfft_translate_noalloc(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
+           "fmmfft_translate_noalloc")
 
 
 def fmmfft_translate_host(plan, S_in, S_out, nrhs, stream=None):

@@ -262,6 +262,8 @@ const char* fmmfft_status_string(int s) {
     case FMMFFT_ERR_UNSUPPORTED: return "sizes or format not supported by this build";
     case FMMFFT_ERR_DEVICE: return "a kernel reported a failure";
     case FMMFFT_ERR_IO: return "file input/output failed";
+    case FMMFFT_ERR_TOO_LARGE:
+      return "the translation needs more scratch than fmmfft_translate_noalloc's fixed 32 MiB buffer";
     default: return "unknown status";
   }
 }
@@ -481,6 +483,50 @@ int fmmfft_translate(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, voi
   }
   return FMMFFT_OK;
 }
+
+}  // extern "C"
+
+namespace fmm {
+
+int translate_scratch_bytes(fmmfft_plan p, int nrhs, size_t* bytes) {
+  if (!p || !bytes) return FMMFFT_ERR_INVALID_ARG;
+  if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
+  if (nrhs < 1 || nrhs > 4096) return FMMFFT_ERR_INVALID_ARG;
+  *bytes = (size_t)p->n_dir * 2 * nrhs * p->n[0] * p->K[1] * p->K[2] * elem_bytes(p);
+  return FMMFFT_OK;
+}
+
+int translate_into(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* stream,
+                   void* scratch, size_t scratch_bytes) {
+  size_t need = 0;
+  int st = translate_scratch_bytes(p, nrhs, &need);
+  if (st != FMMFFT_OK) return st;
+  if (!S_in || !S_out || !scratch) return FMMFFT_ERR_INVALID_ARG;
+  const size_t es = elem_bytes(p);
+  const size_t bytes = (size_t)p->n_dir * 2 * nrhs * p->K[0] * p->K[1] * p->K[2] * es;
+  const char* i0 = (const char*)S_in;
+  const char* o0 = (const char*)S_out;
+  if (i0 < o0 + bytes && o0 < i0 + bytes) return FMMFFT_ERR_INVALID_ARG;
+  if (((uintptr_t)S_in | (uintptr_t)S_out | (uintptr_t)scratch) % es) return FMMFFT_ERR_INVALID_ARG;
+  if (need > scratch_bytes) return FMMFFT_ERR_TOO_LARGE;
+  fmm::TranslateArgs a = base_args(p);
+  a.nrhs = nrhs;
+  a.s_in = S_in;
+  a.s_out = S_out;
+  a.inter = scratch;
+  a.stream = (cudaStream_t)stream;
+  a.events = nullptr;
+  p->last_stream = a.stream;
+  if (fmm::launch_translate(a) != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
+}  // namespace fmm
+
+extern "C" {
 
 int fmmfft_translate_host(fmmfft_plan p, const void* S_in_host, void* S_out_host, int nrhs,
                           void* stream) {

@@ -56,4 +56,13 @@ cudaError_t launch_translate(const TranslateArgs& a);
 size_t yz_smem_bytes(const TranslateArgs& a);
 bool translate_supported(const TranslateArgs& a);
 
+// Translation of a compressed plan with a caller-provided intermediate buffer
+// (fmmfft_api.cpp), used by the allocation-free entry point.
+// translate_scratch_bytes validates the plan and nrhs and returns the bytes of
+// intermediate one call needs; translate_into validates the field buffers and
+// launches the translation with `scratch` (scratch_bytes long) as intermediate.
+int translate_scratch_bytes(fmmfft_plan p, int nrhs, size_t* bytes);
+int translate_into(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* stream,
+                   void* scratch, size_t scratch_bytes);
+
 }  // namespace fmm
