@@ -42,6 +42,8 @@ UNIT = "Gvoxel·dir/s"
 WL = dict(name="tucker3d_32cube_L8_tol1e-4_2pol_4rhs", K=(32, 32, 32), L=8, a=0.5, k0=2 * math.pi,
           tol=1e-4, nrhs=4, seed=1002)
 CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
+# version of the yz kernel the committed DRAM-traffic figure was taken on
+YZ_KERNEL_VERSION = 1
 
 
 def _units(n, n_dir, nrhs):
@@ -264,8 +266,6 @@ def main():
     ap.add_argument("--nrhs", type=int, default=0, help="override the RHS count (profiling cases)")
     ap.add_argument("--only", default="both", choices=["both", "compressed", "plain"])
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--yz-variant", type=int, default=2, choices=[0, 1, 2],
-                    help="y/z kernel variant (2: shared-memory lines; 0: register lines, 256 threads; 1: 128 threads)")
     ap.add_argument("--cpu-baseline-child", type=int, default=0)
     ap.add_argument("--reference-child", type=int, nargs=2, default=None)
     args = ap.parse_args()
@@ -306,7 +306,6 @@ def main():
         h = F.fmmfft_plan_create(K[0], K[1], K[2], WL["a"], WL["k0"], L, fmt, dec, tol)
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64)
         F.fmmfft_compress(h)
-        F.fmmfft_plan_set(h, F.FMMFFT_KEY_YZ_VARIANT, args.yz_variant)
         plans[name] = h
     main_arm = "compressed" if "compressed" in plans else "plain"
     st = F.fmmfft_plan_stats(plans[main_arm])
@@ -398,7 +397,7 @@ def main():
         with open(prof) as f:
             tj = json.load(f)
         # counters only count for the kernel they were taken on
-        if tj.get("yz_variant") == args.yz_variant and nrhs == WL["nrhs"]:
+        if tj.get("kernel_version") == YZ_KERNEL_VERSION and nrhs == WL["nrhs"]:
             traffic = tj.get("dram_bytes_per_launch")
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
@@ -408,12 +407,10 @@ def main():
         "config": {"workload": WL["name"] if nrhs == WL["nrhs"] else WL["name"].replace("4rhs", f"{nrhs}rhs"),
                    "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
                    "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d" if main_arm == "compressed" else "none",
-                   "tol": WL["tol"], "precision": "FP32 FFTs and FP32 restores", "yz_variant": args.yz_variant,
+                   "tol": WL["tol"], "precision": "FP32 FFTs and FP32 restores",
                    "l2": "inputs and outputs each larger than the 129 MB L2; no flush"},
         "stages_ms": stage,
-        "roofline": {"kernel": ("yz2_kernel (slab restore + register-line y/z FFTs + Hadamard)"
-                                if args.yz_variant in (0, 1) else
-                                "yz_kernel (slab restore + shared-memory-line y/z FFTs + Hadamard)"),
+        "roofline": {"kernel": "yz_kernel (slab restore + y/z FFTs + Hadamard)",
                      "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic,

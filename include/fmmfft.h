@@ -100,16 +100,9 @@ enum {
   FMMFFT_KEY_PREFACTOR = 5,      /* 0: c = 1 (default); 1: c = -k^2 eta/(16 pi^2) (Eq. 7) */
   FMMFFT_KEY_TRUNC_RULE = 6,     /* 0: discarded-energy rule (default);
                                     1: normalised singular value < gamma/sqrt(d) */
-  FMMFFT_KEY_PROFILE = 7,        /* 1: record CUDA events between the kernels of
+  FMMFFT_KEY_PROFILE = 7         /* 1: record CUDA events between the kernels of
                                     each translation (fmmfft_stage_times); may
                                     be changed at any time                      */
-  FMMFFT_KEY_YZ_VARIANT = 8      /* kernel of the y/z pass: 2 = line transforms
-                                    through shared memory (default); 0 = line
-                                    transforms in registers, 256-thread blocks;
-                                    1 = the same with 128-thread blocks.  Variants
-                                    0 and 1 cover complex64 with n2, n3 <= 64;
-                                    elsewhere 2 runs.  May be changed at any time;
-                                    the results agree to rounding.               */
 };
 
 /* Stages of one translation, in launch order (fmmfft_stage_times). */
@@ -189,6 +182,50 @@ int fmmfft_import_tucker3d(fmmfft_plan plan, const int* ranks, const double* cor
                            const double* U1, const double* U2, const double* U3);
 
 /*
+ * Load externally computed per-direction TT factors (format 3D, decomp TT),
+ * Eq. 13 for each direction p:
+ *   T~_p[x][y][z] = sum_{a,b} U1_p[x][a] C1_p[a][y][b] U3_p[z][b].
+ * ranks: n_dir * 2 ints (r1, r2 of each direction).  U1 (n1 x r1), C1
+ * (r1 x n2 x r2, last index fastest) and U3 (n3 x r2): complex doubles, the
+ * directions' arrays concatenated in direction order.  Copied.
+ */
+int fmmfft_import_tt3d(fmmfft_plan plan, const int* ranks, const double* U1, const double* C1,
+                       const double* U3);
+
+/*
+ * Load an externally computed Tucker decomposition of T_4D (format 4D, decomp
+ * TUCKER), T_4D[x][y][z][p] = T~_p[x][y][z] (Sec. II.B, Eq. 9):
+ *   T_4D[x][y][z][p] = sum C[a][b][c][d] U1[x][a] U2[y][b] U3[z][c] U4[p][d].
+ * ranks: 4 ints.  core: r1 x r2 x r3 x r4 (d fastest); U_i: n_i x r_i, U4:
+ * n_dir x r4; complex doubles.  Copied.
+ */
+int fmmfft_import_tucker4d(fmmfft_plan plan, const int* ranks, const double* core, const double* U1,
+                           const double* U2, const double* U3, const double* U4);
+
+/*
+ * Load an externally computed H-Tucker decomposition of T_4D (format 4D,
+ * decomp HTUCKER), balanced tree {1,2},{3,4} (Eq. 11, Alg. 2):
+ *   T_4D[x][y][z][p] = sum U1[x][a] U2[y][b] U3[z][c] U4[p][d]
+ *                          C12[a][b][s] B[s][t] C34[c][d][t].
+ * ranks: 6 ints (r1 r2 r3 r4 r12 r34).  U_i: n_i x r_i (U4: n_dir x r4);
+ * C12: r1 x r2 x r12; C34: r3 x r4 x r34; B: r12 x r34; complex doubles,
+ * last index fastest.  Copied.
+ */
+int fmmfft_import_htucker(fmmfft_plan plan, const int* ranks, const double* U1, const double* U2,
+                          const double* U3, const double* U4, const double* C12, const double* C34,
+                          const double* B);
+
+/*
+ * Load an externally computed TT decomposition of T_4D (format 4D, decomp
+ * TT), Eq. 14:
+ *   T_4D[x][y][z][p] = sum U1[x][a] C1[a][y][b] C2[b][z][c] U3[p][c].
+ * ranks: 3 ints (r1 r2 r3).  U1: n1 x r1; C1: r1 x n2 x r2; C2: r2 x n3 x r3;
+ * U3: n_dir x r3; complex doubles, last index fastest.  Copied.
+ */
+int fmmfft_import_tt4d(fmmfft_plan plan, const int* ranks, const double* U1, const double* C1,
+                       const double* C2, const double* U3);
+
+/*
  * The translation (Eq. 5) of every field, asynchronous on `stream`
  * (a cudaStream_t; NULL = legacy default stream):
  *   S_out[p][pol][rhs] = crop( IFFT( T~_p . FFT( pad(S_in[p][pol][rhs]) ) ) )
@@ -255,6 +292,18 @@ int fmmfft_operator_host(fmmfft_plan plan, int p, double* That_out);
  * INVALID_ARG for plans of another format; touches no GPU.
  */
 int fmmfft_compress_direction_host(fmmfft_plan plan, int p, int* ranks_out, double* restored_out);
+
+/*
+ * Host-only FP64 compression of the whole operator exactly as fmmfft_compress
+ * does it for the plan's compressed format (Algs. 1-3), restored through the
+ * same restore schedule the kernels run (pre-pass products, then the slab
+ * formula of each direction), without touching a GPU.  ranks_out: n_dir * 3
+ * ints for 3D formats (r1 r2 r3; TT: r1 r2 0), 6 ints for 4D formats (Tucker:
+ * r1 r2 r3 r4 0 0; H-Tucker: r1 r2 r3 r4 r12 r34; TT: r1 r2 r3 0 0 0).
+ * restored_out (optional): n_dir * n1 * n2 * n3 complex doubles, index
+ * ((p * n1 + x) * n2 + y) * n3 + z.  INVALID_ARG for format NONE.
+ */
+int fmmfft_compress_host(fmmfft_plan plan, int* ranks_out, double* restored_out);
 
 /* Fill *out (see fmmfft_stats). */
 int fmmfft_plan_stats(fmmfft_plan plan, fmmfft_stats* out);

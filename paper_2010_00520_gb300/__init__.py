@@ -42,7 +42,6 @@ FMMFFT_KEY_KAPPA = 4
 FMMFFT_KEY_PREFACTOR = 5
 FMMFFT_KEY_TRUNC_RULE = 6
 FMMFFT_KEY_PROFILE = 7
-FMMFFT_KEY_YZ_VARIANT = 8
 FMMFFT_STAGE_RESTORE, FMMFFT_STAGE_XFWD, FMMFFT_STAGE_YZ, FMMFFT_STAGE_XINV = 0, 1, 2, 3
 FMMFFT_NUM_STAGES = 4
 
@@ -52,7 +51,8 @@ EXPORTED = (
     "fmmfft_import_tucker3d", "fmmfft_translate", "fmmfft_translate_host", "fmmfft_plan_stats",
     "fmmfft_plan_directions", "fmmfft_poll_status", "fmmfft_plan_destroy", "fmmfft_status_string",
     "fmmfft_operator_host", "fmmfft_compress_direction_host", "fmmfft_stage_times",
-    "fmmfft_plan_ranks", "fmmfft_translate_noalloc",
+    "fmmfft_plan_ranks", "fmmfft_translate_noalloc", "fmmfft_import_tt3d", "fmmfft_import_tucker4d",
+    "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
 )
 
 
@@ -92,6 +92,11 @@ def lib() -> ctypes.CDLL:
         "fmmfft_compress": [vp],
         "fmmfft_import_plain": [vp, dp],
         "fmmfft_import_tucker3d": [vp, ip, dp, dp, dp, dp],
+        "fmmfft_import_tt3d": [vp, ip, dp, dp, dp],
+        "fmmfft_import_tucker4d": [vp, ip, dp, dp, dp, dp, dp],
+        "fmmfft_import_htucker": [vp, ip, dp, dp, dp, dp, dp, dp, dp],
+        "fmmfft_import_tt4d": [vp, ip, dp, dp, dp, dp],
+        "fmmfft_compress_host": [vp, ip, dp],
         "fmmfft_translate": [vp, vp, vp, i, vp],
         "fmmfft_translate_host": [vp, vp, vp, i, vp],
         "fmmfft_translate_noalloc": [vp, vp, vp, i, vp],
@@ -184,6 +189,49 @@ def fmmfft_import_tucker3d(plan, ranks, core, U1, U2, U3):
                                         *[_dptr(x) for x in arrs]), "fmmfft_import_tucker3d")
 
 
+def _ints(x):
+    r = np.ascontiguousarray(x, dtype=np.int32)
+    return r, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def fmmfft_import_tt3d(plan, ranks, U1, C1, U3):
+    r, rp = _ints(ranks)
+    arrs = [_cplx(x) for x in (U1, C1, U3)]
+    _check(lib().fmmfft_import_tt3d(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_tt3d")
+
+
+def fmmfft_import_tucker4d(plan, ranks, core, U1, U2, U3, U4):
+    r, rp = _ints(ranks)
+    arrs = [_cplx(x) for x in (core, U1, U2, U3, U4)]
+    _check(lib().fmmfft_import_tucker4d(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_tucker4d")
+
+
+def fmmfft_import_htucker(plan, ranks, U1, U2, U3, U4, C12, C34, B):
+    r, rp = _ints(ranks)
+    arrs = [_cplx(x) for x in (U1, U2, U3, U4, C12, C34, B)]
+    _check(lib().fmmfft_import_htucker(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_htucker")
+
+
+def fmmfft_import_tt4d(plan, ranks, U1, C1, C2, U3):
+    r, rp = _ints(ranks)
+    arrs = [_cplx(x) for x in (U1, C1, C2, U3)]
+    _check(lib().fmmfft_import_tt4d(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_tt4d")
+
+
+def fmmfft_compress_host(plan, restored=True):
+    """Host FP64 compression of the whole operator in the plan's format:
+    returns (ranks, restored) with ranks an (n_dir, 3) array for 3D formats or
+    6 ints for 4D formats, restored (n_dir, n1, n2, n3) or None."""
+    st = fmmfft_plan_stats(plan)
+    nd, n = st["n_dir"], tuple(st["n"])
+    is3d = st["format"] == FMMFFT_FORMAT_3D
+    r = np.zeros(nd * 3 if is3d else 6, dtype=np.int32)
+    out = np.zeros((nd,) + n, dtype=np.complex128) if restored else None
+    _check(lib().fmmfft_compress_host(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      _dptr(out) if restored else None), "fmmfft_compress_host")
+    return (r.reshape(nd, 3) if is3d else r), out
+
+
 def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):
     _check(lib().fmmfft_translate(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
            "fmmfft_translate")
@@ -269,7 +317,7 @@ class Plan:
         keys = {"precision": FMMFFT_KEY_PRECISION, "nphi_rule": FMMFFT_KEY_NPHI_RULE,
                 "near_rule": FMMFFT_KEY_NEAR_RULE, "kappa": FMMFFT_KEY_KAPPA,
                 "prefactor": FMMFFT_KEY_PREFACTOR, "trunc_rule": FMMFFT_KEY_TRUNC_RULE,
-                "profile": FMMFFT_KEY_PROFILE, "yz_variant": FMMFFT_KEY_YZ_VARIANT}
+                "profile": FMMFFT_KEY_PROFILE}
         for k, v in opts.items():
             fmmfft_plan_set(self.handle, keys[k], v)
 

@@ -318,102 +318,16 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
 }
 
 // ---------------------------------------------------------------------------
-// Lane-split register lines (N <= 64).  A line is held by L lanes, M = N / L
-// values each: L = 1 for N <= 32 and L = 2 for N = 64 (two adjacent lanes of a
-// warp).  For a forward transform whose inputs vanish beyond N/2, lane l
-// computes the outputs k = L m + l directly from the same inputs:
-//   X[L m + l] = sum_{n < N/2} (x[n] W_N^{n l}) W_M^{n m},
-// and the inverse transform, of which only outputs n < N/2 are used, is
-//   x[n] = sum_l W_N^{-n l} [IDFT_M(X[L . + l])](n),
-// the two lanes' parts being summed with one shuffle exchange.
-// ---------------------------------------------------------------------------
-template <int N> struct Split {
-  static constexpr int L = (N >= 64) ? 2 : 1;
-  static constexpr int M = N / L;
-  static_assert(N <= 64, "lane-split lines cover N <= 64");
-};
-
-// v[I] *= exp(S 2 pi i I / N) for I in [I0, END)
-template <int N, int S, int I, int END, typename C>
-__device__ __forceinline__ void apply_tw(C* v) {
-  if constexpr (I < END) {
-    v[I] = twiddle_ct<N, I, S>(v[I]);
-    apply_tw<N, S, I + 1, END>(v);
-  }
-}
-
-// Load the non-zero head (n < nz <= N/2) of a line; the rest of v is zeroed.
-template <int N, typename C>
-__device__ __forceinline__ void split_load_head(C* v, const C* ln, int es, int nz) {
-  constexpr int M = Split<N>::M;
-#pragma unroll
-  for (int n = 0; n < M; ++n) v[n] = (n < N / 2 && n < nz) ? ln[n * es] : czero<C>();
-}
-
-// Forward DFT of the loaded head: afterwards v[m] = X[L m + l].
-template <int N, typename C>
-__device__ __forceinline__ void split_fwd(C* v, int l) {
-  constexpr int L = Split<N>::L, M = Split<N>::M;
-  if constexpr (L == 1) {
-    dft<N, N / 2, -1>(v);
-  } else {
-    if (l) apply_tw<N, -1, 1, M>(v);
-    dft<M, M, -1>(v);
-  }
-}
-
-// Inverse DFT from v[m] = Y[L m + l]; leaves this lane's additive part.
-template <int N, typename C>
-__device__ __forceinline__ void split_inv(C* v, int l) {
-  constexpr int L = Split<N>::L, M = Split<N>::M;
-  dft<M, M, +1>(v);
-  if constexpr (L == 2) {
-    if (l) apply_tw<N, +1, 1, M>(v);
-  }
-}
-
-template <typename C> __device__ __forceinline__ C shfl_xor1(C v) {
-  C r;
-  r.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
-  r.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
-  return r;
-}
-
-// Store outputs n < keep (<= N/2) of the inverse; with L = 2 lane 0 writes
-// n < N/4 and lane 1 n in [N/4, N/2).  All lanes of the warp must call it.
-template <int N, typename C>
-__device__ __forceinline__ void split_inv_store(const C* v, C* ln, int es, int keep, int l, bool active) {
-  constexpr int L = Split<N>::L, M = Split<N>::M;
-  if constexpr (L == 1) {
-    if (active) {
-#pragma unroll
-      for (int n = 0; n < N / 2; ++n)
-        if (n < keep) ln[n * es] = v[n];
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < M / 2; ++i) {
-      const C send = l ? v[i] : v[M / 2 + i];
-      const C recv = shfl_xor1(send);
-      const C own = l ? v[M / 2 + i] : v[i];
-      const int n = l ? M / 2 + i : i;
-      if (active && n < keep) ln[n * es] = cadd(own, recv);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Small complex GEMM on shared-memory operands, all threads of the block:
 //   Cm[m * ldc + n] = scale * sum_k A[m * lda + k] * B[k * ldb + n]
 // Each warp computes TM rows x (32 TN) columns at a time; lane l owns columns
 // n0 + l + 32 j, so B reads are conflict-free and A reads are broadcasts.
 // Cm may point to shared or global memory.
 // ---------------------------------------------------------------------------
-template <int TM, int TN, typename C, int NW = kWarps>
+template <int TM, int TN, typename C>
 __device__ __forceinline__ void block_cgemm(int M, int N, int K, const C* A, int lda, const C* B,
                                             int ldb, C* Cm, int ldc,
                                             typename real_of<C>::type scale) {
-  constexpr int kWarps = NW;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nrb = (M + TM - 1) / TM, ncb = (N + 32 * TN - 1) / (32 * TN);
   for (int item = w; item < nrb * ncb; item += kWarps) {

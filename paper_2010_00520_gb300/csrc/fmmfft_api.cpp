@@ -6,8 +6,10 @@
 #include <vector>
 
 #include "../../include/fmmfft.h"
+#include "host_decomp.h"
 #include "host_setup.h"
 #include "plan_internal.h"
+#include "plan_layout.h"
 
 using fmm::cdouble;
 
@@ -25,10 +27,15 @@ struct fmmfft_plan_s {
   bool ready = false;
   // device state
   void* d_tw[3] = {nullptr, nullptr, nullptr};
-  void* d_op = nullptr;
-  void* d_pack = nullptr;
-  fmm::Tucker3DDesc* d_desc = nullptr;
-  void* d_h = nullptr;
+  void* d_op = nullptr;         // format NONE: T~_p / (n1 n2 n3), [p][x][z][y]
+  void* d_pack = nullptr;       // compressed formats: stored factors
+  void* d_scratch = nullptr;    // compressed formats: restore pre-pass outputs
+  fmm::SlabDesc* d_slab = nullptr;
+  fmm::GemmDesc* d_gemm = nullptr;
+  fmm::GemmStage stages[fmm::kMaxGemmStages] = {};
+  int n_stages = 0;
+  int yz_fmt = 0;
+  int rmax_a = 0, rmax_b = 0;
   void* d_inter = nullptr;
   size_t inter_bytes = 0;
   void* d_io = nullptr;       // device copies for fmmfft_translate_host
@@ -36,15 +43,14 @@ struct fmmfft_plan_s {
   int* d_status = nullptr;
   cudaStream_t last_stream = nullptr;
   bool profile = false;
-  int yz_variant = 2;
   bool profiled_run = false;
   cudaEvent_t events[FMMFFT_NUM_STAGES + 1] = {};
   // host-side bookkeeping
-  std::vector<fmm::Tucker3DDesc> desc;
+  std::vector<int> ranks3;      // 3D formats: n_dir x 3
   int rmax[6] = {0, 0, 0, 0, 0, 0};
   double mean_rank[3] = {0, 0, 0};
   int64_t elements_plain = 0, elements_compressed = 0;
-  int64_t bytes_operator = 0, bytes_h = 0;
+  int64_t bytes_operator = 0, bytes_restore = 0;
   double setup_seconds = 0;
 };
 
@@ -67,10 +73,14 @@ void release_operator(fmmfft_plan_s* p) {
   for (auto& t : p->d_tw) free_dev(t);
   free_dev(p->d_op);
   free_dev(p->d_pack);
-  void* d = p->d_desc;
+  free_dev(p->d_scratch);
+  void* d = p->d_slab;
   free_dev(d);
-  p->d_desc = nullptr;
-  free_dev(p->d_h);
+  p->d_slab = nullptr;
+  d = p->d_gemm;
+  free_dev(d);
+  p->d_gemm = nullptr;
+  p->n_stages = 0;
   p->ready = false;
 }
 
@@ -134,18 +144,17 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
     a.K[i] = p->K[i];
     a.n[i] = p->n[i];
     a.tw[i] = p->d_tw[i];
-    a.t3_rmax[i] = p->rmax[i];
   }
   a.n_dir = p->n_dir;
   a.precision = p->precision;
-  a.format = p->format;
-  a.decomp = p->decomp;
+  a.yz_fmt = p->format == FMMFFT_FORMAT_NONE ? 0 : p->yz_fmt;
   a.op_plain = p->d_op;
-  a.t3_desc = p->d_desc;
-  a.t3_pack = p->d_pack;
-  a.t3_h = p->d_h;
+  a.slab = p->d_slab;
+  a.rmax_a = p->rmax_a;
+  a.rmax_b = p->rmax_b;
+  a.n_stages = p->n_stages;
+  for (int i = 0; i < p->n_stages; ++i) a.stages[i] = p->stages[i];
   a.status = p->d_status;
-  a.yz_variant = p->yz_variant;
   return a;
 }
 
@@ -173,55 +182,65 @@ int upload_plain(fmmfft_plan_s* p, const std::function<const cdouble*(int)>& sla
   return FMMFFT_OK;
 }
 
-// Tucker-3D store from per-direction factors.
-int upload_tucker3d(fmmfft_plan_s* p, const std::vector<fmm::Tucker3>& tk) {
-  const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
-  p->desc.assign(p->n_dir, fmm::Tucker3DDesc());
-  int64_t off = 0, offh = 0;
-  for (int i = 0; i < 3; ++i) { p->rmax[i] = 0; p->mean_rank[i] = 0; }
-  int64_t elems = 0;
-  for (int d = 0; d < p->n_dir; ++d) {
-    fmm::Tucker3DDesc& D = p->desc[d];
-    D.r1 = tk[d].r[0];
-    D.r2 = tk[d].r[1];
-    D.r3 = tk[d].r[2];
-    D.pad = 0;
-    D.off_core = off; off += (int64_t)D.r1 * D.r2 * D.r3;
-    D.off_u1 = off; off += (int64_t)n1 * D.r1;
-    D.off_u2 = off; off += (int64_t)n2 * D.r2;
-    D.off_u3 = off; off += (int64_t)n3 * D.r3;
-    D.off_h = offh; offh += (int64_t)n1 * D.r2 * D.r3;
-    for (int i = 0; i < 3; ++i) {
-      p->rmax[i] = std::max(p->rmax[i], tk[d].r[i]);
-      p->mean_rank[i] += tk[d].r[i] / (double)p->n_dir;
-    }
-  }
-  elems = off;
-  std::vector<cdouble> pack((size_t)off);
-  fmm::parallel_for(p->n_dir, [&](int d) {
-    const fmm::Tucker3DDesc& D = p->desc[d];
-    std::copy(tk[d].core.begin(), tk[d].core.end(), pack.begin() + D.off_core);
-    std::copy(tk[d].U[0].begin(), tk[d].U[0].end(), pack.begin() + D.off_u1);
-    std::copy(tk[d].U[1].begin(), tk[d].U[1].end(), pack.begin() + D.off_u2);
-    std::copy(tk[d].U[2].begin(), tk[d].U[2].end(), pack.begin() + D.off_u3);
-  });
+// Compressed store: factors, restore scratch and the descriptors of the
+// restore schedule (pre-pass products and per-direction slab restores).
+int upload_layout(fmmfft_plan_s* p, const fmm::Layout& L) {
+  const bool dbl = p->precision == FMMFFT_PREC_C128;
+  const size_t es = elem_bytes(p);
+  if ((int)L.stages.size() > fmm::kMaxGemmStages) return FMMFFT_ERR_UNSUPPORTED;
   free_dev(p->d_pack);
-  int st = upload_complex(&p->d_pack, pack, p->precision == FMMFFT_PREC_C128);
+  int st = upload_complex(&p->d_pack, L.pack, dbl);
   if (st != FMMFFT_OK) return st;
-  void* dd = p->d_desc;
-  free_dev(dd);
-  p->d_desc = nullptr;
-  if ((st = dev_alloc(&dd, sizeof(fmm::Tucker3DDesc) * p->n_dir)) != FMMFFT_OK) return st;
-  p->d_desc = (fmm::Tucker3DDesc*)dd;
-  if (cudaMemcpy(dd, p->desc.data(), sizeof(fmm::Tucker3DDesc) * p->n_dir, cudaMemcpyHostToDevice) != cudaSuccess)
+  free_dev(p->d_scratch);
+  if ((st = dev_alloc(&p->d_scratch, (size_t)L.scratch * es)) != FMMFFT_OK) return st;
+  std::vector<std::vector<fmm::GemmDesc>> g;
+  fmm::bind_gemms(L, p->d_pack, p->d_scratch, es, g);
+  std::vector<fmm::GemmDesc> flat;
+  for (auto& stage : g) flat.insert(flat.end(), stage.begin(), stage.end());
+  void* dg = nullptr;
+  if ((st = dev_alloc(&dg, sizeof(fmm::GemmDesc) * std::max<size_t>(flat.size(), 1))) != FMMFFT_OK) return st;
+  p->d_gemm = (fmm::GemmDesc*)dg;
+  if (!flat.empty() &&
+      cudaMemcpy(dg, flat.data(), sizeof(fmm::GemmDesc) * flat.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return FMMFFT_ERR_CUDA;
-  free_dev(p->d_h);
-  if ((st = dev_alloc(&p->d_h, (size_t)offh * elem_bytes(p))) != FMMFFT_OK) return st;
-  p->elements_plain = (int64_t)n1 * n2 * n3 * p->n_dir;
-  p->elements_compressed = elems;
-  p->bytes_operator = (int64_t)(elems * elem_bytes(p) + sizeof(fmm::Tucker3DDesc) * p->n_dir);
-  p->bytes_h = (int64_t)(offh * elem_bytes(p));
+  p->n_stages = (int)g.size();
+  size_t at = 0;
+  for (int i = 0; i < p->n_stages; ++i) {
+    fmm::GemmStage& S = p->stages[i];
+    S.desc = p->d_gemm + at;
+    S.batch = (int)g[i].size();
+    S.max_m = 0;
+    S.max_n = 0;
+    for (auto& d : g[i]) {
+      S.max_m = std::max(S.max_m, d.M);
+      S.max_n = std::max(S.max_n, d.N);
+    }
+    at += g[i].size();
+  }
+  std::vector<fmm::SlabDesc> sl;
+  fmm::bind_slabs(L, p->d_pack, p->d_scratch, es, sl);
+  void* ds = nullptr;
+  if ((st = dev_alloc(&ds, sizeof(fmm::SlabDesc) * sl.size())) != FMMFFT_OK) return st;
+  p->d_slab = (fmm::SlabDesc*)ds;
+  if (cudaMemcpy(ds, sl.data(), sizeof(fmm::SlabDesc) * sl.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FMMFFT_ERR_CUDA;
+  p->elements_plain = (int64_t)p->n[0] * p->n[1] * p->n[2] * p->n_dir;
+  p->elements_compressed = L.elements;
+  p->bytes_operator = (int64_t)(L.pack.size() * es + sizeof(fmm::SlabDesc) * sl.size() +
+                                sizeof(fmm::GemmDesc) * flat.size());
+  p->bytes_restore = (int64_t)(L.scratch * es);
   return FMMFFT_OK;
+}
+
+// Plan fields that describe a layout (ranks, restore shape), set before the
+// support check so that it sees the layout's shared-memory needs.
+void adopt_layout_shape(fmmfft_plan_s* p, const fmm::Layout& L) {
+  p->yz_fmt = L.yz_fmt;
+  p->rmax_a = L.rmax_a;
+  p->rmax_b = L.rmax_b;
+  for (int i = 0; i < 6; ++i) p->rmax[i] = L.rank[i];
+  for (int i = 0; i < 3; ++i) p->mean_rank[i] = L.mean_rank[i];
+  p->ranks3 = L.ranks3;
 }
 
 fmm::OperatorSpec spec_of(const fmmfft_plan_s* p) {
@@ -246,6 +265,77 @@ bool precision_supported(const fmmfft_plan_s* p) {
 bool check_supported(fmmfft_plan_s* p) {
   fmm::TranslateArgs a = base_args(p);
   return fmm::translate_supported(a);
+}
+
+bool format_known(const fmmfft_plan_s* p) {
+  if (p->format == FMMFFT_FORMAT_NONE) return true;
+  if (p->format == FMMFFT_FORMAT_3D) return p->decomp == FMMFFT_DECOMP_TUCKER || p->decomp == FMMFFT_DECOMP_TT;
+  return p->decomp == FMMFFT_DECOMP_TUCKER || p->decomp == FMMFFT_DECOMP_TT || p->decomp == FMMFFT_DECOMP_HTUCKER;
+}
+
+// FP64 host set-up of a compressed plan: operators (Eq. 7, Sec. II.B) and
+// their decomposition in the plan's format (Algs. 1-3), as a layout.
+void build_layout(const fmmfft_plan_s* p, fmm::Layout& L) {
+  const fmm::OperatorSpec s = spec_of(p);
+  const int nd = p->n_dir;
+  if (p->format == FMMFFT_FORMAT_3D && p->decomp == FMMFFT_DECOMP_TUCKER) {
+    std::vector<fmm::Tucker3> tk(nd);
+    fmm::parallel_for(nd, [&](int d) {
+      std::vector<cdouble> T;
+      fmm::fft_operator(s, &p->khat[3 * d], T);
+      fmm::hosvd3(T, p->n, p->tol, p->trunc_rule, tk[d]);
+    });
+    fmm::layout_tucker3d(tk, p->n, L);
+    return;
+  }
+  if (p->format == FMMFFT_FORMAT_3D) {
+    std::vector<fmm::TT3> tt(nd);
+    fmm::parallel_for(nd, [&](int d) {
+      std::vector<cdouble> T;
+      fmm::fft_operator(s, &p->khat[3 * d], T);
+      fmm::ttsvd3(T, p->n, p->tol, p->trunc_rule, tt[d]);
+    });
+    fmm::layout_tt3d(tt, p->n, L);
+    return;
+  }
+  std::vector<std::vector<cdouble>> Tp(nd);
+  fmm::parallel_for(nd, [&](int d) { fmm::fft_operator(s, &p->khat[3 * d], Tp[d]); });
+  if (p->decomp == FMMFFT_DECOMP_TUCKER) {
+    double n2 = 0.0;
+    for (auto& T : Tp)
+      for (auto& z : T) n2 += std::norm(z);
+    fmm::Tucker4 tk;
+    fmm::hosvd4(Tp, p->n, fmm::step_budget(std::sqrt(n2), p->tol, 4.0, p->trunc_rule), p->trunc_rule, tk);
+    fmm::layout_tucker4d(tk, p->n, nd, L);
+  } else if (p->decomp == FMMFFT_DECOMP_HTUCKER) {
+    fmm::HTucker4 ht;
+    fmm::htucker4(Tp, p->n, p->tol, p->trunc_rule, ht);
+    fmm::layout_htucker(ht, p->n, nd, L);
+  } else {
+    fmm::TT4 tt;
+    fmm::tt4_via_tucker(Tp, p->n, p->tol, p->trunc_rule, tt);
+    fmm::layout_tt4d(tt, p->n, nd, L);
+  }
+}
+
+// Adopt a compressed layout: support check, upload, common buffers.
+int install_layout(fmmfft_plan_s* p, const fmm::Layout& L) {
+  release_operator(p);
+  adopt_layout_shape(p, L);
+  if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  int st = upload_layout(p, L);
+  if (st != FMMFFT_OK) return st;
+  if ((st = ensure_common(p)) != FMMFFT_OK) return st;
+  p->ready = true;
+  return FMMFFT_OK;
+}
+
+const cdouble* as_cd(const double* x) { return reinterpret_cast<const cdouble*>(x); }
+
+std::vector<cdouble> take(const cdouble*& src, size_t count) {
+  std::vector<cdouble> v(src, src + count);
+  src += count;
+  return v;
 }
 
 }  // namespace
@@ -302,8 +392,7 @@ int fmmfft_plan_create(fmmfft_plan* out, int Nx, int Ny, int Nz, double a, doubl
 }
 
 int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
-  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE && key != FMMFFT_KEY_YZ_VARIANT))
-    return FMMFFT_ERR_INVALID_ARG;
+  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE)) return FMMFFT_ERR_INVALID_ARG;
   const int iv = (int)v;
   switch (key) {
     case FMMFFT_KEY_PRECISION:
@@ -339,17 +428,6 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->profile = iv == 1;
       return FMMFFT_OK;
-    case FMMFFT_KEY_YZ_VARIANT:
-      if (iv < 0 || iv > 2 || iv != v) return FMMFFT_ERR_INVALID_ARG;
-      {
-        const int old = p->yz_variant;
-        p->yz_variant = iv;
-        if (p->ready && !check_supported(p)) {
-          p->yz_variant = old;
-          return FMMFFT_ERR_UNSUPPORTED;
-        }
-      }
-      return FMMFFT_OK;
     default:
       return FMMFFT_ERR_INVALID_ARG;
   }
@@ -358,34 +436,23 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
 int fmmfft_compress(fmmfft_plan p) {
   if (!p) return FMMFFT_ERR_INVALID_ARG;
   const auto t0 = std::chrono::steady_clock::now();
-  if (!(p->format == FMMFFT_FORMAT_NONE ||
-        (p->format == FMMFFT_FORMAT_3D && p->decomp == FMMFFT_DECOMP_TUCKER)))
-    return FMMFFT_ERR_UNSUPPORTED;
-  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
-  if (p->format == FMMFFT_FORMAT_NONE && !check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
-  release_operator(p);
-  const fmm::OperatorSpec s = spec_of(p);
+  if (!format_known(p) || !precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   int st;
   if (p->format == FMMFFT_FORMAT_NONE) {
+    if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+    release_operator(p);
+    const fmm::OperatorSpec s = spec_of(p);
     std::vector<std::vector<cdouble>> ops(p->n_dir);
     fmm::parallel_for(p->n_dir, [&](int d) { fmm::fft_operator(s, &p->khat[3 * d], ops[d]); });
     st = upload_plain(p, [&](int d) { return ops[d].data(); });
+    if (st != FMMFFT_OK) return st;
+    if ((st = ensure_common(p)) != FMMFFT_OK) return st;
+    p->ready = true;
   } else {
-    std::vector<fmm::Tucker3> tk(p->n_dir);
-    fmm::parallel_for(p->n_dir, [&](int d) {
-      std::vector<cdouble> T;
-      fmm::fft_operator(s, &p->khat[3 * d], T);
-      fmm::hosvd3(T, p->n, p->tol, p->trunc_rule, tk[d]);
-    });
-    for (int i = 0; i < 3; ++i) p->rmax[i] = 0;
-    for (auto& t : tk)
-      for (int i = 0; i < 3; ++i) p->rmax[i] = std::max(p->rmax[i], t.r[i]);
-    if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
-    st = upload_tucker3d(p, tk);
+    fmm::Layout L;
+    build_layout(p, L);
+    if ((st = install_layout(p, L)) != FMMFFT_OK) return st;
   }
-  if (st != FMMFFT_OK) return st;
-  if ((st = ensure_common(p)) != FMMFFT_OK) return st;
-  p->ready = true;
   p->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return FMMFFT_OK;
 }
@@ -410,33 +477,140 @@ int fmmfft_import_tucker3d(fmmfft_plan p, const int* ranks, const double* core, 
   if (p->format != FMMFFT_FORMAT_3D || p->decomp != FMMFFT_DECOMP_TUCKER) return FMMFFT_ERR_INVALID_ARG;
   if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   std::vector<fmm::Tucker3> tk(p->n_dir);
-  const cdouble* c = reinterpret_cast<const cdouble*>(core);
-  const cdouble* u[3] = {reinterpret_cast<const cdouble*>(U1), reinterpret_cast<const cdouble*>(U2),
-                         reinterpret_cast<const cdouble*>(U3)};
+  const cdouble* c = as_cd(core);
+  const cdouble* u[3] = {as_cd(U1), as_cd(U2), as_cd(U3)};
   for (int d = 0; d < p->n_dir; ++d) {
     for (int i = 0; i < 3; ++i) {
       const int r = ranks[3 * d + i];
       if (r < 1 || r > p->n[i]) return FMMFFT_ERR_INVALID_ARG;
       tk[d].r[i] = r;
     }
-    const size_t nc = (size_t)tk[d].r[0] * tk[d].r[1] * tk[d].r[2];
-    tk[d].core.assign(c, c + nc);
-    c += nc;
-    for (int i = 0; i < 3; ++i) {
-      const size_t nu = (size_t)p->n[i] * tk[d].r[i];
-      tk[d].U[i].assign(u[i], u[i] + nu);
-      u[i] += nu;
-    }
+    tk[d].core = take(c, (size_t)tk[d].r[0] * tk[d].r[1] * tk[d].r[2]);
+    for (int i = 0; i < 3; ++i) tk[d].U[i] = take(u[i], (size_t)p->n[i] * tk[d].r[i]);
   }
-  for (int i = 0; i < 3; ++i) p->rmax[i] = 0;
-  for (auto& t : tk)
-    for (int i = 0; i < 3; ++i) p->rmax[i] = std::max(p->rmax[i], t.r[i]);
-  if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
-  release_operator(p);
-  int st = upload_tucker3d(p, tk);
-  if (st != FMMFFT_OK) return st;
-  if ((st = ensure_common(p)) != FMMFFT_OK) return st;
-  p->ready = true;
+  fmm::Layout L;
+  fmm::layout_tucker3d(tk, p->n, L);
+  return install_layout(p, L);
+}
+
+int fmmfft_import_tt3d(fmmfft_plan p, const int* ranks, const double* U1, const double* C1, const double* U3) {
+  if (!p || !ranks || !U1 || !C1 || !U3) return FMMFFT_ERR_INVALID_ARG;
+  if (p->format != FMMFFT_FORMAT_3D || p->decomp != FMMFFT_DECOMP_TT) return FMMFFT_ERR_INVALID_ARG;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  std::vector<fmm::TT3> tt(p->n_dir);
+  const cdouble* u1 = as_cd(U1);
+  const cdouble* c1 = as_cd(C1);
+  const cdouble* u3 = as_cd(U3);
+  const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  for (int d = 0; d < p->n_dir; ++d) {
+    const int r1 = ranks[2 * d], r2 = ranks[2 * d + 1];
+    if (r1 < 1 || r1 > n1 || r2 < 1 || r2 > (int64_t)r1 * n2) return FMMFFT_ERR_INVALID_ARG;
+    tt[d].r1 = r1;
+    tt[d].r2 = r2;
+    tt[d].U1 = take(u1, (size_t)n1 * r1);
+    tt[d].C1 = take(c1, (size_t)r1 * n2 * r2);
+    tt[d].U3 = take(u3, (size_t)n3 * r2);
+  }
+  fmm::Layout L;
+  fmm::layout_tt3d(tt, p->n, L);
+  return install_layout(p, L);
+}
+
+int fmmfft_import_tucker4d(fmmfft_plan p, const int* ranks, const double* core, const double* U1,
+                           const double* U2, const double* U3, const double* U4) {
+  if (!p || !ranks || !core || !U1 || !U2 || !U3 || !U4) return FMMFFT_ERR_INVALID_ARG;
+  if (p->format != FMMFFT_FORMAT_4D || p->decomp != FMMFFT_DECOMP_TUCKER) return FMMFFT_ERR_INVALID_ARG;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  const int dims[4] = {p->n[0], p->n[1], p->n[2], p->n_dir};
+  fmm::Tucker4 tk;
+  size_t nc = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (ranks[i] < 1 || ranks[i] > dims[i]) return FMMFFT_ERR_INVALID_ARG;
+    tk.r[i] = ranks[i];
+    nc *= (size_t)ranks[i];
+  }
+  const cdouble* c = as_cd(core);
+  tk.core = take(c, nc);
+  const double* U[4] = {U1, U2, U3, U4};
+  for (int i = 0; i < 4; ++i) {
+    const cdouble* u = as_cd(U[i]);
+    tk.U[i] = take(u, (size_t)dims[i] * tk.r[i]);
+  }
+  fmm::Layout L;
+  fmm::layout_tucker4d(tk, p->n, p->n_dir, L);
+  return install_layout(p, L);
+}
+
+int fmmfft_import_htucker(fmmfft_plan p, const int* ranks, const double* U1, const double* U2,
+                          const double* U3, const double* U4, const double* C12, const double* C34,
+                          const double* B) {
+  if (!p || !ranks || !U1 || !U2 || !U3 || !U4 || !C12 || !C34 || !B) return FMMFFT_ERR_INVALID_ARG;
+  if (p->format != FMMFFT_FORMAT_4D || p->decomp != FMMFFT_DECOMP_HTUCKER) return FMMFFT_ERR_INVALID_ARG;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  const int dims[4] = {p->n[0], p->n[1], p->n[2], p->n_dir};
+  fmm::HTucker4 ht;
+  for (int i = 0; i < 6; ++i) {
+    if (ranks[i] < 1) return FMMFFT_ERR_INVALID_ARG;
+    ht.r[i] = ranks[i];
+  }
+  for (int i = 0; i < 4; ++i)
+    if (ranks[i] > dims[i]) return FMMFFT_ERR_INVALID_ARG;
+  if (ranks[4] > ranks[0] * ranks[1] || ranks[5] > ranks[2] * ranks[3]) return FMMFFT_ERR_INVALID_ARG;
+  const double* U[4] = {U1, U2, U3, U4};
+  for (int i = 0; i < 4; ++i) {
+    const cdouble* u = as_cd(U[i]);
+    ht.U[i] = take(u, (size_t)dims[i] * ht.r[i]);
+  }
+  const cdouble* c12 = as_cd(C12);
+  const cdouble* c34 = as_cd(C34);
+  const cdouble* b = as_cd(B);
+  ht.C12 = take(c12, (size_t)ht.r[0] * ht.r[1] * ht.r[4]);
+  ht.C34 = take(c34, (size_t)ht.r[2] * ht.r[3] * ht.r[5]);
+  ht.B = take(b, (size_t)ht.r[4] * ht.r[5]);
+  fmm::Layout L;
+  fmm::layout_htucker(ht, p->n, p->n_dir, L);
+  return install_layout(p, L);
+}
+
+int fmmfft_import_tt4d(fmmfft_plan p, const int* ranks, const double* U1, const double* C1, const double* C2,
+                       const double* U3) {
+  if (!p || !ranks || !U1 || !C1 || !C2 || !U3) return FMMFFT_ERR_INVALID_ARG;
+  if (p->format != FMMFFT_FORMAT_4D || p->decomp != FMMFFT_DECOMP_TT) return FMMFFT_ERR_INVALID_ARG;
+  if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  fmm::TT4 tt;
+  for (int i = 0; i < 3; ++i) {
+    if (ranks[i] < 1) return FMMFFT_ERR_INVALID_ARG;
+    tt.r[i] = ranks[i];
+  }
+  if (tt.r[0] > n1 || tt.r[2] > p->n_dir) return FMMFFT_ERR_INVALID_ARG;
+  const cdouble* u1 = as_cd(U1);
+  const cdouble* c1 = as_cd(C1);
+  const cdouble* c2 = as_cd(C2);
+  const cdouble* u3 = as_cd(U3);
+  tt.U1 = take(u1, (size_t)n1 * tt.r[0]);
+  tt.C1 = take(c1, (size_t)tt.r[0] * n2 * tt.r[1]);
+  tt.C2 = take(c2, (size_t)tt.r[1] * n3 * tt.r[2]);
+  tt.U3 = take(u3, (size_t)p->n_dir * tt.r[2]);
+  fmm::Layout L;
+  fmm::layout_tt4d(tt, p->n, p->n_dir, L);
+  return install_layout(p, L);
+}
+
+int fmmfft_compress_host(fmmfft_plan p, int* ranks, double* restored) {
+  if (!p || !ranks || p->format == FMMFFT_FORMAT_NONE || !format_known(p)) return FMMFFT_ERR_INVALID_ARG;
+  fmm::Layout L;
+  build_layout(p, L);
+  if (p->format == FMMFFT_FORMAT_3D) {
+    std::memcpy(ranks, L.ranks3.data(), sizeof(int) * L.ranks3.size());
+  } else {
+    for (int i = 0; i < 6; ++i) ranks[i] = L.rank[i];
+  }
+  if (restored) {
+    std::vector<cdouble> T;
+    fmm::restore_host(L, T);
+    std::memcpy(restored, T.data(), T.size() * sizeof(cdouble));
+  }
   return FMMFFT_OK;
 }
 
@@ -611,18 +785,14 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   o->elements_compressed = p->elements_compressed;
   o->saving = p->elements_plain ? 1.0 - (double)p->elements_compressed / (double)p->elements_plain : 0.0;
   o->device_bytes_operator = p->bytes_operator;
-  o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes) + p->bytes_h;
+  o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes) + p->bytes_restore;
   o->setup_seconds = p->setup_seconds;
   return FMMFFT_OK;
 }
 
 int fmmfft_plan_ranks(fmmfft_plan p, int* ranks) {
   if (!p || !ranks || !p->ready || p->format != FMMFFT_FORMAT_3D) return FMMFFT_ERR_INVALID_ARG;
-  for (int d = 0; d < p->n_dir; ++d) {
-    ranks[3 * d] = p->desc[d].r1;
-    ranks[3 * d + 1] = p->desc[d].r2;
-    ranks[3 * d + 2] = p->desc[d].r3;
-  }
+  std::memcpy(ranks, p->ranks3.data(), sizeof(int) * p->ranks3.size());
   return FMMFFT_OK;
 }
 

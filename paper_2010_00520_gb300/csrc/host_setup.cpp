@@ -10,11 +10,15 @@ namespace fmm {
 
 static const double kPiD = 3.14159265358979323846264338327950288;
 
+// Set inside the worker threads: a parallel_for nested in another runs
+// serially on the calling worker instead of spawning more threads.
+static thread_local bool t_in_worker = false;
+
 void parallel_for(int n, const std::function<void(int)>& fn) {
   if (n <= 0) return;
   unsigned hw = std::thread::hardware_concurrency();
   int nt = (int)std::min<unsigned>(hw ? hw : 1, (unsigned)n);
-  if (nt <= 1) {
+  if (nt <= 1 || t_in_worker) {
     for (int i = 0; i < n; ++i) fn(i);
     return;
   }
@@ -23,6 +27,7 @@ void parallel_for(int n, const std::function<void(int)>& fn) {
   th.reserve(nt);
   for (int t = 0; t < nt; ++t)
     th.emplace_back([&]() {
+      t_in_worker = true;
       for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
     });
   for (auto& t : th) t.join();

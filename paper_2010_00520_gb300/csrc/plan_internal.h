@@ -13,16 +13,36 @@ namespace fmm {
 
 using cdouble = std::complex<double>;
 
-// Per-direction Tucker-3D descriptor (device and host copies).  Offsets count
-// complex elements in the packed factor buffer / the restore scratch buffer.
-struct Tucker3DDesc {
-  int r1, r2, r3, pad;
-  int64_t off_core;   // C_p, r1 x r2 x r3, c fastest
-  int64_t off_u1;     // U1_p, n1 x r1
-  int64_t off_u2;     // U2_p, n2 x r2
-  int64_t off_u3;     // U3_p, n3 x r3
-  int64_t off_h;      // H_p = C_p x_1 U1_p, n1 x r2 x r3, in the restore scratch
+// Per-direction restore descriptor of the yz kernel (device pointers).
+//   Tucker-like (yz format 1): h = H_p, row x at h + x * hx (ra x rb, [b][c]);
+//                              u2 = U2 (n2 x ra); u3 = U3 (n3 x rb)
+//   TT-like (yz format 2):     h = T1 of the direction, row x at h + x * hx
+//                              (n2 x rb, [y][b]); u3 = R_p (n3 x rb); ra = 0
+struct SlabDesc {
+  const void* h;
+  const void* u2;
+  const void* u3;
+  long long hx;
+  int ra, rb;
 };
+
+// One product of the restore pre-pass: C = A B, complex, row-major and
+// contiguous (A: M x K, B: K x N, C: M x N).
+struct GemmDesc {
+  const void* A;
+  const void* B;
+  void* C;
+  int M, N, K, pad;
+};
+
+// One launch of the pre-pass: `batch` products described at `desc` (device).
+struct GemmStage {
+  const GemmDesc* desc;
+  int batch;
+  int max_m, max_n;
+};
+
+constexpr int kMaxGemmStages = 4;
 
 // Arguments of one translation, prepared by the host for the launchers.
 struct TranslateArgs {
@@ -31,25 +51,24 @@ struct TranslateArgs {
   int n_dir;
   int nrhs;
   int precision;      // FMMFFT_PREC_*
-  int format, decomp;
+  int yz_fmt;         // 0 plain operator, 1 Tucker-like restore, 2 TT-like restore
   const void* s_in;
   void* s_out;
   void* inter;        // x-transformed fields, [F][n1][Kz][Ky]
   const void* tw[3];  // twiddle tables W_{n_i}^m, m < n_i
   // format NONE: T~_p / (n1 n2 n3), layout [p][x][z][y]
   const void* op_plain;
-  // Tucker-3D
-  const Tucker3DDesc* t3_desc;   // device, n_dir entries
-  const void* t3_pack;           // device, packed cores and factors
-  void* t3_h;                    // device, restore scratch (H_p)
-  int t3_rmax[3];                // largest r1, r2, r3
-  int* status;                   // device status word
-  cudaEvent_t* events;           // FMMFFT_NUM_STAGES + 1 events, or null
-  int yz_variant;                // FMMFFT_KEY_YZ_VARIANT
+  // compressed formats
+  const SlabDesc* slab;              // device, n_dir entries
+  int rmax_a, rmax_b;                // largest ra, rb over directions
+  int n_stages;                      // pre-pass launches, in order
+  GemmStage stages[kMaxGemmStages];
+  int* status;                       // device status word
+  cudaEvent_t* events;               // FMMFFT_NUM_STAGES + 1 events, or null
   cudaStream_t stream;
 };
 
-// Kernel launchers (translate_kernels.cu).  Return a cudaError_t.
+// Kernel launchers (translate_launch.cu).  Return a cudaError_t.
 cudaError_t launch_translate(const TranslateArgs& a);
 // Largest shared-memory request of the yz kernel for the given args (bytes);
 // 0 if the sizes are not supported by the compiled kernels.

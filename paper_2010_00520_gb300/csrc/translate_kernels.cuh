@@ -1,17 +1,28 @@
-// Kernels of the translation stage (Eq. 5) and of the Tucker-3D restoration
-// (Sec. II.C, Fig. 3(a)).
+// Kernels of the translation stage (Eq. 5) and of the operator restorations
+// (Sec. II.C, Figs. 3 and 4).
 //
 // A field A (Kz x Ky x Kx, x fastest) is translated in three passes:
 //   xfwd  : rows r = z Ky + y: zero-pad x to n1, forward DFT along x, write
 //           the x-spectrum transposed to the intermediate I[f][x][r]
 //   yz    : one block per (x, direction p): the operator slab T~_p[x][:][:]
-//           is loaded (format NONE) or restored (Tucker-3D) into shared
-//           memory once, then for every field of direction p: forward DFT
-//           along y (rows z < Kz), along z (columns) fused with the Hadamard
-//           product and the inverse DFT along z, inverse DFT along y, and the
-//           Kz x Ky corner is written back in place
+//           is loaded (format NONE) or restored (compressed formats) into
+//           shared memory once, then for every field of direction p: forward
+//           DFT along y (rows z < Kz), along z (columns) fused with the
+//           Hadamard product and the inverse DFT along z, inverse DFT along y,
+//           and the Kz x Ky corner is written back in place
 //   xinv  : inverse DFT along x of every row, first Kx entries written out
 // The 1 / (n1 n2 n3) of the inverse transform is folded into the operator.
+//
+// Restoration is split between a pre-pass and the yz kernel.  The pre-pass
+// (batched complex GEMMs, `cgemm_batched_kernel`) forms per call what does not
+// depend on x: the core of each direction for the 4D formats (Figs. 3(b),
+// 3(c), 4(b)) and H = U1 . mat(core), an n1 x (...) matrix whose row x is all
+// the yz block (x, p) needs besides two small factor matrices:
+//   Tucker-like (Tucker-3D, Tucker-4D, H-Tucker):
+//       slab[z][y] = sum_c U3[z][c] sum_b U2[y][b] H_p[x][b][c]
+//   TT-like (TT-3D, TT-4D):
+//       slab[z][y] = sum_b R_p[z][b] T1[x][y][b]
+// with R_p = U3 of the direction (TT-3D) or the generated slice S_p^T (TT-4D).
 #pragma once
 
 #include "fft_core.cuh"
@@ -38,22 +49,9 @@ struct YZParams {
   const void* tw2, *tw3;
   int Ky, Kz, n1, nf;  // nf = fields per direction (2 nrhs)
   const void* op;      // plain: [p][x][z][y], scaled
-  const Tucker3DDesc* desc;
-  const void* pack;
-  const void* hbuf;
+  const SlabDesc* desc;
   double scale;        // restore scale 1 / (n1 n2 n3)
-  int rmax2, rmax3;    // shared-memory capacity of the launch (ranks)
-  int* status;
-  int variant;         // yz launch variant (FMMFFT_KEY_YZ_VARIANT)
-};
-
-struct HParams {
-  const Tucker3DDesc* desc;
-  const void* pack;
-  void* hbuf;
-  int n1;
-  int cols_per_block;
-  int rmax1;
+  int rmax_a, rmax_b;  // shared-memory capacity of the launch (ranks)
   int* status;
 };
 
@@ -139,39 +137,73 @@ constexpr size_t xpass_smem(int rows_per_block) {
 }
 
 // ---------------------------------------------------------------------------
-// Tucker-3D restore, step 1 (Fig. 3(a)): H_p = U1_p . mat(C_p), an
-// n1 x (r2 r3) matrix per direction; one block per (column chunk, p).
+// Batched complex GEMM of the restore pre-pass: block (bx, by, g) computes the
+// 64 x 64 tile (by, bx) of product g.  256 threads, 4 x 4 outputs each; A and
+// B are staged through shared memory in chunks of kGemmKC along K.
 // ---------------------------------------------------------------------------
+constexpr int kGemmT = 64, kGemmKC = 16;
+
 template <typename R>
-__global__ void __launch_bounds__(kThreads) tucker3d_h_kernel(HParams P) {
+__global__ void __launch_bounds__(kThreads) cgemm_batched_kernel(const GemmDesc* __restrict__ descs) {
   using C = cx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Tucker3DDesc d = P.desc[blockIdx.y];
-  const int ncol = d.r2 * d.r3;
-  const int c0 = blockIdx.x * P.cols_per_block;
-  if (c0 >= ncol) return;
-  if (d.r1 > P.rmax1) {
-    if (threadIdx.x == 0) atomicOr(P.status, kStatusRankOverflow);
-    return;
+  __shared__ C sA[kGemmT][kGemmKC + 1];
+  __shared__ C sB[kGemmKC][kGemmT];
+  const GemmDesc d = descs[blockIdx.z];
+  const int m0 = blockIdx.y * kGemmT, n0 = blockIdx.x * kGemmT;
+  if (m0 >= d.M || n0 >= d.N) return;
+  const C* A = reinterpret_cast<const C*>(d.A);
+  const C* B = reinterpret_cast<const C*>(d.B);
+  C* Cm = reinterpret_cast<C*>(d.C);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+  for (int k0 = 0; k0 < d.K; k0 += kGemmKC) {
+    for (int i = tid; i < kGemmT * kGemmKC; i += kThreads) {
+      const int r = i / kGemmKC, k = i - r * kGemmKC;
+      const int gm = m0 + r, gk = k0 + k;
+      sA[r][k] = (gm < d.M && gk < d.K) ? A[(size_t)gm * d.K + gk] : czero<C>();
+    }
+    for (int i = tid; i < kGemmKC * kGemmT; i += kThreads) {
+      const int k = i / kGemmT, c = i - k * kGemmT;
+      const int gk = k0 + k, gn = n0 + c;
+      sB[k][c] = (gk < d.K && gn < d.N) ? B[(size_t)gk * d.N + gn] : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kGemmKC; ++k) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[ty + 16 * i][k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
   }
-  const int nc = min(P.cols_per_block, ncol - c0);
-  C* sU1 = reinterpret_cast<C*>(smem_raw);          // n1 x r1
-  C* sC = sU1 + P.n1 * d.r1;                         // r1 x cols_per_block
-  const C* pack = reinterpret_cast<const C*>(P.pack);
-  for (int i = threadIdx.x; i < P.n1 * d.r1; i += kThreads) sU1[i] = pack[d.off_u1 + i];
-  for (int i = threadIdx.x; i < d.r1 * nc; i += kThreads) {
-    const int a = i / nc, c = i - a * nc;
-    sC[a * P.cols_per_block + c] = pack[d.off_core + (int64_t)a * ncol + c0 + c];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= d.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn < d.N) Cm[(size_t)gm * d.N + gn] = acc[i][j];
+    }
   }
-  __syncthreads();
-  C* H = reinterpret_cast<C*>(P.hbuf) + d.off_h + c0;
-  block_cgemm<8, 2>(P.n1, nc, d.r1, sU1, d.r1, sC, P.cols_per_block, H, ncol, (R)1);
 }
 
 // ---------------------------------------------------------------------------
-// yz pass.  FMT 0: plain operator from global memory.  FMT 1: Tucker-3D
-// restore of the slab from H_p[x] (r2 x r3), U2_p and U3_p (Fig. 3(a),
-// steps 2-3):  T~_p[x][y][z] = sum_{b,c} U2_p[y][b] H_p[x][b][c] U3_p[z][c].
+// yz pass.  FMT 0: plain operator from global memory.  FMT 1: Tucker-like
+// restore of the slab (Fig. 3(a) steps 2-3, with the factors of the format):
+//   T~_p[x][y][z] = sum_{b,c} U2[y][b] H_p[x][b][c] U3[z][c]
+// FMT 2: TT-like restore (Fig. 4(a) step 2, Fig. 4(b) step 3):
+//   T~_p[x][y][z] = sum_b T1[x][y][b] R_p[z][b]
 // ---------------------------------------------------------------------------
 template <typename R, int N2, int N3>
 struct YZLayout {
@@ -179,13 +211,15 @@ struct YZLayout {
   static constexpr int XW = (Line<N2>::XW > Line<N3>::XW) ? Line<N2>::XW : Line<N3>::XW;
   static constexpr size_t fixed_elems = (size_t)N3 * PY + N2 + N3;   // Tt + twiddles
   static constexpr size_t plane_elems = (size_t)N3 * PY + kWarps * XW;
-  static size_t restore_elems(int r2, int r3) {
-    const size_t a = (size_t)r3 * r2 + (size_t)r2 * N2, b = (size_t)N3 * r3;
-    return (size_t)r3 * N2 + (a > b ? a : b);
+  // restore work space: Gt (rb x N2) plus, before stage B, Ht (rb x ra) and
+  // U2t (ra x N2) [FMT 1] or nothing [FMT 2]; then U3 (N3 x rb)
+  static size_t restore_elems(int fmt, int ra, int rb) {
+    const size_t a = (fmt == 1) ? (size_t)rb * ra + (size_t)ra * N2 : 0, b = (size_t)N3 * rb;
+    return (size_t)rb * N2 + (a > b ? a : b);
   }
-  static size_t smem_bytes(int fmt, int r2, int r3) {
+  static size_t smem_bytes(int fmt, int ra, int rb) {
     size_t work = plane_elems;
-    if (fmt == 1) { const size_t r = restore_elems(r2, r3); if (r > work) work = r; }
+    if (fmt != 0) { const size_t r = restore_elems(fmt, ra, rb); if (r > work) work = r; }
     return sizeof(cx<R>) * (fixed_elems + work);
   }
 };
@@ -214,32 +248,40 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       Tt[z * PY + y] = op[i];
     }
   } else {
-    const Tucker3DDesc d = P.desc[p];
-    const int r2 = d.r2, r3 = d.r3;
-    if (r2 > P.rmax2 || r3 > P.rmax3) {
+    const SlabDesc d = P.desc[p];
+    const int ra = d.ra, rb = d.rb;
+    if (ra > P.rmax_a || rb > P.rmax_b) {
       if (tid == 0) atomicOr(P.status, kStatusRankOverflow);
       return;
     }
-    const C* pack = reinterpret_cast<const C*>(P.pack);
-    const C* H = reinterpret_cast<const C*>(P.hbuf) + d.off_h + (size_t)x * r2 * r3;
-    C* Gt = work;                              // r3 x N2
-    C* Ht = Gt + r3 * N2;                      // r3 x r2
-    C* U2t = Ht + r3 * r2;                     // r2 x N2
-    C* U3s = Ht;                               // N3 x r3 (after Gt is formed)
-    for (int i = tid; i < r2 * r3; i += kThreads) {
-      const int b = i / r3, c = i - b * r3;
-      Ht[c * r2 + b] = H[i];
+    const C* H = reinterpret_cast<const C*>(d.h) + (size_t)x * d.hx;
+    C* Gt = work;                              // rb x N2
+    C* U3s = Gt + rb * N2;                     // N3 x rb (stage B)
+    if constexpr (FMT == 1) {
+      C* Ht = Gt + rb * N2;                    // rb x ra
+      C* U2t = Ht + rb * ra;                   // ra x N2
+      const C* U2 = reinterpret_cast<const C*>(d.u2);
+      for (int i = tid; i < ra * rb; i += kThreads) {
+        const int b = i / rb, c = i - b * rb;
+        Ht[c * ra + b] = H[i];
+      }
+      for (int i = tid; i < N2 * ra; i += kThreads) {
+        const int y = i / ra, b = i - y * ra;
+        U2t[b * N2 + y] = U2[i];
+      }
+      __syncthreads();
+      block_cgemm<8, (N2 >= 64 ? 2 : 1)>(rb, N2, ra, Ht, ra, U2t, N2, Gt, N2, (R)1);
+    } else {
+      for (int i = tid; i < N2 * rb; i += kThreads) {
+        const int y = i / rb, b = i - y * rb;
+        Gt[b * N2 + y] = H[i];
+      }
     }
-    for (int i = tid; i < N2 * r2; i += kThreads) {
-      const int y = i / r2, b = i - y * r2;
-      U2t[b * N2 + y] = pack[d.off_u2 + i];
-    }
     __syncthreads();
-    block_cgemm<8, (N2 >= 64 ? 2 : 1)>(r3, N2, r2, Ht, r2, U2t, N2, Gt, N2, (R)1);
+    const C* U3 = reinterpret_cast<const C*>(d.u3);
+    for (int i = tid; i < N3 * rb; i += kThreads) U3s[i] = U3[i];
     __syncthreads();
-    for (int i = tid; i < N3 * r3; i += kThreads) U3s[i] = pack[d.off_u3 + i];
-    __syncthreads();
-    block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, r3, U3s, r3, Gt, N2, Tt, PY, (R)P.scale);
+    block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
   }
   __syncthreads();
 
@@ -286,180 +328,6 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
     for (int i = tid; i < Kz * Ky; i += kThreads) {
       const int z = i / Ky, y = i - z * Ky;
       io[i] = plane[z * PY + y];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// yz pass, lane-split version (n2, n3 <= 64).  Every line transform runs in
-// registers (one or two lanes per line, see Split<N>); shared memory holds the
-// operator slab Tt[z][y] and G field planes [z][y] (pitch n2 + 1), so the y,
-// z, Hadamard and inverse steps of G fields of direction p run per group of
-// five barriers.  Inputs of a forward line beyond its K entries are never
-// read, so no zero padding is stored.
-// ---------------------------------------------------------------------------
-template <typename R, int N2, int N3, int NT>
-struct YZ2Layout {
-  static constexpr int L2 = Split<N2>::L, L3 = Split<N3>::L;
-  static constexpr int G = (NT / (N2 * L3)) > 0 ? (NT / (N2 * L3)) : 1;  // planes
-  static constexpr int PP = N2 + 1;    // plane pitch
-  // slab pitch: with two lanes per z-line, lanes l = 0, 1 read slab rows 2m
-  // and 2m + 1 of the same column; a pitch of 8 (mod 16) complex elements puts
-  // them in different bank pairs
-  static constexpr int PT = (L3 == 2 && N2 % 16 == 0) ? N2 + 8 : N2;
-  static constexpr size_t slab_elems = (size_t)N3 * PT;
-  static constexpr size_t planes_elems = (size_t)G * N3 * PP;
-  static size_t restore_elems(int r2, int r3) {
-    const size_t r2p = (size_t)(r2 | 1);
-    const size_t a = (size_t)r3 * r2p + (size_t)r2 * (N2 + 1), b = (size_t)N3 * r3;
-    return (size_t)r3 * N2 + (a > b ? a : b);
-  }
-  static size_t smem_bytes(int fmt, int r2, int r3) {
-    size_t work = planes_elems;
-    if (fmt == 1) { const size_t r = restore_elems(r2, r3); if (r > work) work = r; }
-    return sizeof(cx<R>) * (slab_elems + work);
-  }
-};
-
-// Tucker-3D slab restore (Fig. 3(a) steps 2-3) into Tt[z * pt + y], scaled.
-template <typename R, int N2, int N3, int NT>
-__device__ __forceinline__ void restore_slab_tucker3d(const YZParams& P, int p, int x, cx<R>* Tt, int pt,
-                                                      cx<R>* work) {
-  using C = cx<R>;
-  const Tucker3DDesc d = P.desc[p];
-  const int r2 = d.r2, r3 = d.r3, r2p = d.r2 | 1;
-  const int tid = threadIdx.x;
-  const C* pack = reinterpret_cast<const C*>(P.pack);
-  const C* H = reinterpret_cast<const C*>(P.hbuf) + d.off_h + (size_t)x * r2 * r3;
-  C* Gt = work;                              // r3 x N2
-  C* Ht = Gt + r3 * N2;                      // r3 x r2p   (Ht[c][b] = H[b][c])
-  C* U2t = Ht + r3 * r2p;                    // r2 x (N2+1) (U2t[b][y] = U2[y][b])
-  C* U3s = Ht;                               // N3 x r3 once Gt is formed
-  for (int i = tid; i < r2 * r3; i += NT) {
-    const int b = i / r3, c = i - b * r3;
-    Ht[c * r2p + b] = H[i];
-  }
-  for (int i = tid; i < N2 * r2; i += NT) {
-    const int y = i / r2, b = i - y * r2;
-    U2t[b * (N2 + 1) + y] = pack[d.off_u2 + i];
-  }
-  __syncthreads();
-  block_cgemm<8, (N2 >= 64 ? 2 : 1), C, NT / 32>(r3, N2, r2, Ht, r2p, U2t, N2 + 1, Gt, N2, (R)1);
-  __syncthreads();
-  for (int i = tid; i < N3 * r3; i += NT) U3s[i] = pack[d.off_u3 + i];
-  __syncthreads();
-  block_cgemm<8, (N2 >= 64 ? 2 : 1), C, NT / 32>(N3, N2, r3, U3s, r3, Gt, N2, Tt, pt, (R)P.scale);
-}
-
-template <typename R, int N2, int N3, int FMT, int NT>
-__global__ void __launch_bounds__(NT) yz2_kernel(YZParams P) {
-  using C = cx<R>;
-  using LY = YZ2Layout<R, N2, N3, NT>;
-  constexpr int L2 = LY::L2, L3 = LY::L3, G = LY::G, PP = LY::PP, PT = LY::PT;
-  constexpr int M2 = Split<N2>::M, M3 = Split<N3>::M;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* Tt = reinterpret_cast<C*>(smem_raw);       // N3 x PT
-  C* planes = Tt + LY::slab_elems;              // G x N3 x PP
-  const int x = blockIdx.x, p = blockIdx.y;
-  const int tid = threadIdx.x;
-
-  if constexpr (FMT == 0) {
-    const C* op = reinterpret_cast<const C*>(P.op) + ((size_t)p * P.n1 + x) * (N3 * N2);
-    for (int i = tid; i < N3 * N2; i += NT) {
-      const int z = i / N2, y = i - z * N2;
-      Tt[z * PT + y] = op[i];
-    }
-  } else {
-    const Tucker3DDesc d = P.desc[p];
-    if (d.r2 > P.rmax2 || d.r3 > P.rmax3) {
-      if (tid == 0) atomicOr(P.status, kStatusRankOverflow);
-      return;
-    }
-    restore_slab_tucker3d<R, N2, N3, NT>(P, p, x, Tt, PT, planes);
-  }
-
-  const int Ky = P.Ky, Kz = P.Kz;
-  const int fsz = Kz * Ky;
-  C* inter = reinterpret_cast<C*>(P.inter);
-#pragma unroll 1
-  for (int g0 = 0; g0 < P.nf; g0 += G) {
-    const int ng = min(G, P.nf - g0);
-    __syncthreads();
-    // fields g0 .. g0 + ng - 1 into planes rows z < Kz, columns y < Ky
-    for (int i = tid; i < ng * fsz; i += NT) {
-      const int j = i / fsz, r = i - j * fsz;
-      const int z = r / Ky, y = r - z * Ky;
-      const size_t f = (size_t)p * P.nf + g0 + j;
-      planes[(j * N3 + z) * PP + y] = inter[(f * P.n1 + x) * fsz + r];
-    }
-    __syncthreads();
-    // forward y: rows (j, z < Kz); inputs y < Ky, all n2 outputs
-    {
-      const int l = tid % L2;
-#pragma unroll 1
-      for (int base = 0; base < ng * Kz; base += NT / L2) {
-        const int li = base + tid / L2;
-        const bool act = li < ng * Kz;
-        const int j = act ? li / Kz : 0, z = act ? li - (li / Kz) * Kz : 0;
-        C* row = planes + (j * N3 + z) * PP;
-        C v[M2];
-        if (act) split_load_head<N2>(v, row, 1, Ky);
-        __syncwarp();
-        if (act) {
-          split_fwd<N2>(v, l);
-#pragma unroll
-          for (int m = 0; m < M2; ++m) row[L2 * m + l] = v[m];
-        }
-      }
-    }
-    __syncthreads();
-    // z: forward, Hadamard with the slab, inverse; columns (j, y < n2)
-    {
-      const int l = tid % L3;
-#pragma unroll 1
-      for (int base = 0; base < ng * N2; base += NT / L3) {
-        const int li = base + tid / L3;
-        const bool act = li < ng * N2;
-        const int j = act ? li / N2 : 0, col = act ? li % N2 : 0;
-        C* cl = planes + j * N3 * PP + col;
-        C v[M3];
-        if (act) split_load_head<N3>(v, cl, PP, Kz);
-        __syncwarp();
-        if (act) {
-          split_fwd<N3>(v, l);
-#pragma unroll
-          for (int m = 0; m < M3; ++m) v[m] = cmul(v[m], Tt[(L3 * m + l) * PT + col]);
-          split_inv<N3>(v, l);
-        }
-        split_inv_store<N3>(v, cl, PP, Kz, l, act);
-      }
-    }
-    __syncthreads();
-    // inverse y: rows (j, z < Kz), outputs y < Ky
-    {
-      const int l = tid % L2;
-#pragma unroll 1
-      for (int base = 0; base < ng * Kz; base += NT / L2) {
-        const int li = base + tid / L2;
-        const bool act = li < ng * Kz;
-        const int j = act ? li / Kz : 0, z = act ? li - (li / Kz) * Kz : 0;
-        C* row = planes + (j * N3 + z) * PP;
-        C v[M2];
-        if (act) {
-#pragma unroll
-          for (int m = 0; m < M2; ++m) v[m] = row[L2 * m + l];
-        }
-        __syncwarp();
-        if (act) split_inv<N2>(v, l);
-        split_inv_store<N2>(v, row, 1, Ky, l, act);
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < ng * fsz; i += NT) {
-      const int j = i / fsz, r = i - j * fsz;
-      const int z = r / Ky, y = r - z * Ky;
-      const size_t f = (size_t)p * P.nf + g0 + j;
-      inter[(f * P.n1 + x) * fsz + r] = planes[(j * N3 + z) * PP + y];
     }
   }
 }

@@ -1,17 +1,20 @@
-// Launch sequence of one translation: [restore step 1] -> xfwd -> yz -> xinv.
+// Launch sequence of one translation: [restore pre-pass] -> xfwd -> yz -> xinv.
 #include "translate_kernels.cuh"
 
 namespace fmm {
 
-cudaError_t launch_yz_f32(const YZParams& P, int n2, int n3, int fmt, dim3 grid, size_t smem,
-                          cudaStream_t s);
-size_t yz_smem_f32(int n2, int n3, int fmt, int r2, int r3, int variant);
-cudaError_t launch_yz_f64(const YZParams& P, int n2, int n3, int fmt, dim3 grid, size_t smem,
-                          cudaStream_t s);
-size_t yz_smem_f64(int n2, int n3, int fmt, int r2, int r3, int variant);
+#define FMM_YZ_DECL(TAG, F)                                                                  \
+  cudaError_t launch_yz_##TAG##_##F(const YZParams& P, int n2, int n3, dim3 grid, size_t smem, \
+                                    cudaStream_t s);
+FMM_YZ_DECL(f32, 0)
+FMM_YZ_DECL(f32, 1)
+FMM_YZ_DECL(f32, 2)
+FMM_YZ_DECL(f64, 0)
+FMM_YZ_DECL(f64, 1)
+FMM_YZ_DECL(f64, 2)
+#undef FMM_YZ_DECL
 
 static const size_t kMaxSmem = 227 * 1024;
-static const int kHCols = 128;
 
 template <typename R, int N1>
 static int xpass_rows_per_block(int rows) {
@@ -60,29 +63,63 @@ static cudaError_t launch_x(bool fwd, int n1, const XPassParams& P, int F, cudaS
 
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
-size_t yz_smem_bytes(const TranslateArgs& a) {
-  const int fmt = (a.format == FMMFFT_FORMAT_NONE) ? 0 : 1;
-  const int r2 = a.t3_rmax[1], r3 = a.t3_rmax[2];
-  return a.precision == FMMFFT_PREC_C128 ? yz_smem_f64(a.n[1], a.n[2], fmt, r2, r3, a.yz_variant)
-                                         : yz_smem_f32(a.n[1], a.n[2], fmt, r2, r3, a.yz_variant);
+template <typename R, int N2>
+static size_t yz_smem_n3(int n3, int fmt, int ra, int rb) {
+  switch (n3) {
+    case 4: return YZLayout<R, N2, 4>::smem_bytes(fmt, ra, rb);
+    case 8: return YZLayout<R, N2, 8>::smem_bytes(fmt, ra, rb);
+    case 16: return YZLayout<R, N2, 16>::smem_bytes(fmt, ra, rb);
+    case 32: return YZLayout<R, N2, 32>::smem_bytes(fmt, ra, rb);
+    case 64: return YZLayout<R, N2, 64>::smem_bytes(fmt, ra, rb);
+    case 128: return YZLayout<R, N2, 128>::smem_bytes(fmt, ra, rb);
+    default: return 0;
+  }
 }
 
-static size_t h_smem_bytes(const TranslateArgs& a) {
-  const size_t es = a.precision == FMMFFT_PREC_C128 ? 16 : 8;
-  return es * ((size_t)a.n[0] * a.t3_rmax[0] + (size_t)a.t3_rmax[0] * kHCols);
+template <typename R>
+static size_t yz_smem_any(int n2, int n3, int fmt, int ra, int rb) {
+  switch (n2) {
+    case 4: return yz_smem_n3<R, 4>(n3, fmt, ra, rb);
+    case 8: return yz_smem_n3<R, 8>(n3, fmt, ra, rb);
+    case 16: return yz_smem_n3<R, 16>(n3, fmt, ra, rb);
+    case 32: return yz_smem_n3<R, 32>(n3, fmt, ra, rb);
+    case 64: return yz_smem_n3<R, 64>(n3, fmt, ra, rb);
+    case 128: return yz_smem_n3<R, 128>(n3, fmt, ra, rb);
+    default: return 0;
+  }
+}
+
+size_t yz_smem_bytes(const TranslateArgs& a) {
+  return a.precision == FMMFFT_PREC_C128 ? yz_smem_any<double>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b)
+                                         : yz_smem_any<float>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b);
 }
 
 bool translate_supported(const TranslateArgs& a) {
   if (!pow2_in(a.n[0], 4, 256) || !pow2_in(a.n[1], 4, 128) || !pow2_in(a.n[2], 4, 128)) return false;
-  if (a.format != FMMFFT_FORMAT_NONE &&
-      !(a.format == FMMFFT_FORMAT_3D && a.decomp == FMMFFT_DECOMP_TUCKER))
-    return false;
+  if (a.yz_fmt < 0 || a.yz_fmt > 2) return false;
   const size_t s = yz_smem_bytes(a);
   if (s == 0 || s > kMaxSmem) return false;
-  if (a.format != FMMFFT_FORMAT_NONE && h_smem_bytes(a) > kMaxSmem) return false;
   // x-pass shared memory at the largest rows-per-block candidate is bounded
   // by construction (<= 96 KB)
   return true;
+}
+
+static cudaError_t launch_yz(const TranslateArgs& a, const YZParams& Y, dim3 grid, size_t smem) {
+  const int n2 = a.n[1], n3 = a.n[2];
+  if (a.precision == FMMFFT_PREC_C128) {
+    switch (a.yz_fmt) {
+      case 0: return launch_yz_f64_0(Y, n2, n3, grid, smem, a.stream);
+      case 1: return launch_yz_f64_1(Y, n2, n3, grid, smem, a.stream);
+      case 2: return launch_yz_f64_2(Y, n2, n3, grid, smem, a.stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (a.yz_fmt) {
+    case 0: return launch_yz_f32_0(Y, n2, n3, grid, smem, a.stream);
+    case 1: return launch_yz_f32_1(Y, n2, n3, grid, smem, a.stream);
+    case 2: return launch_yz_f32_2(Y, n2, n3, grid, smem, a.stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename R>
@@ -90,30 +127,14 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   const int F = a.n_dir * 2 * a.nrhs;
   const int rows = a.K[1] * a.K[2];
   cudaError_t e;
-  const bool tucker = a.format == FMMFFT_FORMAT_3D && a.decomp == FMMFFT_DECOMP_TUCKER;
   auto mark = [&](int i) {
     if (a.events) cudaEventRecord(a.events[i], a.stream);
   };
   mark(0);
-  if (tucker) {
-    HParams H;
-    H.desc = a.t3_desc;
-    H.pack = a.t3_pack;
-    H.hbuf = a.t3_h;
-    H.n1 = a.n[0];
-    H.cols_per_block = kHCols;
-    H.rmax1 = a.t3_rmax[0];
-    H.status = a.status;
-    const size_t smem = h_smem_bytes(a);
-    static size_t configured = 0;
-    if (smem > configured) {
-      e = cudaFuncSetAttribute(tucker3d_h_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      configured = smem;
-    }
-    const int maxcols = a.t3_rmax[1] * a.t3_rmax[2];
-    dim3 grid((maxcols + kHCols - 1) / kHCols, a.n_dir);
-    tucker3d_h_kernel<R><<<grid, kThreads, smem, a.stream>>>(H);
+  for (int i = 0; i < a.n_stages; ++i) {
+    const GemmStage& g = a.stages[i];
+    dim3 grid((g.max_n + kGemmT - 1) / kGemmT, (g.max_m + kGemmT - 1) / kGemmT, g.batch);
+    cgemm_batched_kernel<R><<<grid, kThreads, 0, a.stream>>>(g.desc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   mark(1);
@@ -136,21 +157,14 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   Y.n1 = a.n[0];
   Y.nf = 2 * a.nrhs;
   Y.op = a.op_plain;
-  Y.desc = a.t3_desc;
-  Y.pack = a.t3_pack;
-  Y.hbuf = a.t3_h;
+  Y.desc = a.slab;
   Y.scale = 1.0 / ((double)a.n[0] * a.n[1] * a.n[2]);
-  Y.rmax2 = a.t3_rmax[1];
-  Y.rmax3 = a.t3_rmax[2];
+  Y.rmax_a = a.rmax_a;
+  Y.rmax_b = a.rmax_b;
   Y.status = a.status;
-  Y.variant = a.yz_variant;
-  const int fmt = tucker ? 1 : 0;
   const size_t smem = yz_smem_bytes(a);
   dim3 grid(a.n[0], a.n_dir);
-  e = (a.precision == FMMFFT_PREC_C128)
-          ? launch_yz_f64(Y, a.n[1], a.n[2], fmt, grid, smem, a.stream)
-          : launch_yz_f32(Y, a.n[1], a.n[2], fmt, grid, smem, a.stream);
-  if (e != cudaSuccess) return e;
+  if ((e = launch_yz(a, Y, grid, smem)) != cudaSuccess) return e;
   mark(3);
 
   X.src = a.inter;

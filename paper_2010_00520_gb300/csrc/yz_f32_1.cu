@@ -1,0 +1,4 @@
+// yz-pass kernels, float arithmetic, operator format 1 (0 plain, 1 Tucker-like, 2 TT-like).
+#include "yz_dispatch.cuh"
+
+FMM_YZ_UNIT(float, f32, 1)

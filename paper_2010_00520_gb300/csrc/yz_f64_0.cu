@@ -1,0 +1,4 @@
+// yz-pass kernels, double arithmetic, operator format 0 (0 plain, 1 Tucker-like, 2 TT-like).
+#include "yz_dispatch.cuh"
+
+FMM_YZ_UNIT(double, f64, 0)

@@ -250,25 +250,20 @@ def test_unsupported_precision_is_reported(native, cuda):
         F.fmmfft_plan_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("K,L,nrhs", [((9, 17, 30), 2, 1), ((9, 12, 30), 2, 3)])
-def test_yz_variants_match_oracle(native, cuda, variant, K, L, nrhs):
-    """Each y/z kernel variant (register lines with 256- or 128-thread blocks,
-    shared-memory team lines) on ragged box counts whose FFT planes are 64 x 64
-    and 32 x 64; nrhs = 3 leaves a partial group of field planes in a block.
+def test_ragged_planes_match_oracle(native, cuda, K, L, nrhs):
+    """Ragged box counts whose FFT planes are 64 x 64 and 32 x 64, several RHS.
     Plain operator and Tucker-3D cores, both imported from the oracle."""
     F, torch = native, cuda
     plan = pl.Plan(K=K, L=L)
     ops = pl.operators(plan)
     comp = pl.compress(ops, "3d", "tucker", 1e-4)
-    S = field_spectra(31 + variant, plan.n_dir, nrhs, K)
+    S = field_spectra(31 + nrhs, plan.n_dir, nrhs, K)
     hp = _plan(F, K, L)
     ht = _plan(F, K, L, 3, 1, 1e-4)
     try:
         _import_plain(F, hp, ops)
         _import_tucker(F, ht, comp)
-        F.fmmfft_plan_set(hp, F.FMMFFT_KEY_YZ_VARIANT, variant)
-        F.fmmfft_plan_set(ht, F.FMMFFT_KEY_YZ_VARIANT, variant)
         out_p = _gpu_translate(F, torch, hp, S, nrhs)
         out_t = _gpu_translate(F, torch, ht, S, nrhs)
         assert _rel(out_p, pl.translate_with(lambda p: ops[p], S)) <= 2e-6
