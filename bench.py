@@ -265,6 +265,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=0, help="override the RHS count (profiling cases)")
     ap.add_argument("--only", default="both", choices=["both", "compressed", "plain"])
+    ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "fp32"],
+                    help="restore arithmetic of the compressed arm: tensor cores (3xTF32) or FP32 CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-baseline-child", type=int, default=0)
     ap.add_argument("--reference-child", type=int, nargs=2, default=None)
@@ -304,7 +306,8 @@ def main():
             if args.only in ("both", a[0])]
     for name, fmt, dec, tol in arms:
         h = F.fmmfft_plan_create(K[0], K[1], K[2], WL["a"], WL["k0"], L, fmt, dec, tol)
-        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64)
+        prec = F.FMMFFT_PREC_C64_3XTF32 if (name == "compressed" and args.restore == "3xtf32") else F.FMMFFT_PREC_C64
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, prec)
         F.fmmfft_compress(h)
         plans[name] = h
     main_arm = "compressed" if "compressed" in plans else "plain"
@@ -407,7 +410,9 @@ def main():
         "config": {"workload": WL["name"] if nrhs == WL["nrhs"] else WL["name"].replace("4rhs", f"{nrhs}rhs"),
                    "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
                    "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d" if main_arm == "compressed" else "none",
-                   "tol": WL["tol"], "precision": "FP32 FFTs and FP32 restores",
+                   "tol": WL["tol"],
+                   "precision": ("FP32 FFTs, 3xTF32 restores on the tensor cores (tcgen05, FP32 accumulate)"
+                                 if st.get("restore_on_tensor_cores") else "FP32 FFTs and FP32 restores"),
                    "l2": "inputs and outputs each larger than the 129 MB L2; no flush"},
         "stages_ms": stage,
         "roofline": {"kernel": "yz_kernel (slab restore + y/z FFTs + Hadamard)",

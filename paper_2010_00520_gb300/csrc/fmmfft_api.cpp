@@ -155,6 +155,7 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   a.n_stages = p->n_stages;
   for (int i = 0; i < p->n_stages; ++i) a.stages[i] = p->stages[i];
   a.status = p->d_status;
+  a.tc = fmm::tc_restore_applies(a) ? 1 : 0;
   return a;
 }
 
@@ -259,7 +260,8 @@ fmm::OperatorSpec spec_of(const fmmfft_plan_s* p) {
 }
 
 bool precision_supported(const fmmfft_plan_s* p) {
-  return p->precision == FMMFFT_PREC_C128 || p->precision == FMMFFT_PREC_C64;
+  return p->precision == FMMFFT_PREC_C128 || p->precision == FMMFFT_PREC_C64 ||
+         p->precision == FMMFFT_PREC_C64_3XTF32;
 }
 
 bool check_supported(fmmfft_plan_s* p) {
@@ -787,6 +789,7 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   o->device_bytes_operator = p->bytes_operator;
   o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes) + p->bytes_restore;
   o->setup_seconds = p->setup_seconds;
+  o->restore_on_tensor_cores = p->ready ? base_args(p).tc : 0;
   return FMMFFT_OK;
 }
 

@@ -61,6 +61,7 @@ struct TranslateArgs {
   // compressed formats
   const SlabDesc* slab;              // device, n_dir entries
   int rmax_a, rmax_b;                // largest ra, rb over directions
+  int tc;                            // 1: slab restores on the tensor cores (3xTF32)
   int n_stages;                      // pre-pass launches, in order
   GemmStage stages[kMaxGemmStages];
   int* status;                       // device status word
@@ -74,6 +75,8 @@ cudaError_t launch_translate(const TranslateArgs& a);
 // 0 if the sizes are not supported by the compiled kernels.
 size_t yz_smem_bytes(const TranslateArgs& a);
 bool translate_supported(const TranslateArgs& a);
+// Whether the slab restores of these args run on the tensor cores (3xTF32).
+bool tc_restore_applies(const TranslateArgs& a);
 
 // Translation of a compressed plan with a caller-provided intermediate buffer
 // (fmmfft_api.cpp), used by the allocation-free entry point.

@@ -1,0 +1,305 @@
+// Complex 64 x 64 GEMM tile on the 5th-generation tensor cores (tcgen05) in
+// 3xTF32 split precision with FP32 accumulation in tensor memory (TMEM), for
+// the operator restores (Sec. II.C): all threads of a 256-thread block call
+// tc_cgemm64.
+//
+// Complex product C = A B (A: M x K, B: K x N, M, N <= 64) as one real MMA of
+// shape 128 x 128 x K per K step:
+//   A' = [Re A ; Im A]   (rows 0..63 real parts, 64..127 imaginary parts)
+//   B' = [Re B , Im B]   (columns 0..63 real parts, 64..127 imaginary parts)
+//   D  = A' B' = [[ReA ReB, ReA ImB], [ImA ReB, ImA ImB]]
+//   Re C = D[m][n] - D[64+m][64+n],   Im C = D[m][64+n] + D[64+m][n]
+// Each FP32 operand x is split into tf32 parts x = big + small (big = x rounded
+// to tf32, small = the rounded remainder) and D accumulates big*big +
+// small*big + big*small: the dropped small*small term and the rounding of
+// `small` leave a relative error near 2^-21, the FP32 level.
+//
+// Operands are staged through shared memory in chunks of kTcKC along K, in
+// the no-swizzle K-major canonical layout of tcgen05: 8-row x 16-byte core
+// matrices, the 4 core matrices of a chunk's K extent adjacent (LBO = 128 B),
+// 8-row groups 512 B apart (SBO).  B' is stored transposed (N' x K, K-major).
+// One elected thread issues the MMAs and commits them to an mbarrier; warp 0
+// waits on it (bounded) while the other warps sleep in a block barrier, so the
+// wait takes no shared-memory bandwidth from a co-resident block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fmm {
+
+constexpr int kTcKC = 16;                              // complex K per chunk
+constexpr int kTcTileFloats = 128 * kTcKC;             // one 128 x KC operand split
+constexpr size_t kTcSmemBytes = 4 * kTcTileFloats * sizeof(float) + 16;  // A big/small, B big/small, mbarrier
+constexpr int kTcCols = 128;                           // TMEM columns of D
+constexpr unsigned kTcWaitLimit = 1u << 24;            // mbarrier poll limit
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm volatile("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// float offset of element (row, k) of a 128 x kTcKC tile in the canonical
+// K-major layout (core matrix = 8 rows x 4 floats)
+__device__ __forceinline__ int tc_off(int row, int k) {
+  return (((row >> 3) * (kTcKC / 4) + (k >> 2)) << 5) + ((row & 7) << 2) + (k & 3);
+}
+
+// shared-memory matrix descriptor: no swizzle, LBO 128 B (K direction), SBO
+// between 8-row groups, descriptor version 1
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  const uint64_t lbo = 128, sbo = (kTcKC / 4) * 128;
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor of kind::tf32, D in F32, A and B K-major, M = N = 128
+__host__ __device__ constexpr uint32_t tc_idesc_tf32_128x128() {
+  return (1u << 4)                 // D format F32
+         | (2u << 7)               // A format TF32
+         | (2u << 10)              // B format TF32
+         | ((128u >> 3) << 17)     // N >> 3
+         | ((128u >> 4) << 24);    // M >> 4
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier to complete; false after the poll
+// limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// TMEM allocation by one full warp; the address lands in *slot (shared).
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Per-block state of the tensor-core GEMMs: TMEM address, mbarrier and its
+// phase, staged in shared memory by tc_setup.
+struct TcState {
+  float* buf;          // 4 x kTcTileFloats floats: A big, A small, B big, B small
+  uint32_t mbar;       // shared address of the mbarrier
+  uint32_t tmem;       // TMEM base address of D
+  uint32_t phase;      // parity of the next mbarrier phase
+  bool ok;             // false once a wait ran out (results invalid)
+};
+
+// Block-wide set-up: `buf` (kTcSmemBytes, 16-byte aligned) holds the operand
+// chunks and the mbarrier; `slot` receives the TMEM address.  Warp 0
+// allocates kTcCols columns.  All threads call it.
+__device__ __forceinline__ TcState tc_setup(void* buf, uint32_t* slot) {
+  TcState s;
+  s.buf = reinterpret_cast<float*>(buf);
+  s.mbar = smem_u32(s.buf + 4 * kTcTileFloats);
+  if (threadIdx.x == 0) {
+    mbar_init(s.mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, kTcCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  s.tmem = *slot;
+  s.phase = 0;
+  s.ok = true;
+  return s;
+}
+
+// Block-wide tear-down: warp 0 frees the TMEM columns.  All threads call it,
+// after their last TMEM access.
+__device__ __forceinline__ void tc_teardown(const TcState& s) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    tc_fence_after();
+    tmem_dealloc(s.tmem, kTcCols);
+  }
+}
+
+// C[m * ldc + n] = scale * sum_k A(m, k) B(k, n) for m < M, n < N (M, N <= 64)
+// with A(m, k), B(k, n) complex (float2) supplied by the functors.  Every
+// thread of the 256-thread block calls it; C is in shared memory.
+template <typename FA, typename FB>
+__device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a_of, FB b_of, float2* C,
+                                           int ldc, float scale) {
+  const int tid = threadIdx.x;
+  uint32_t* Ab = reinterpret_cast<uint32_t*>(s.buf);
+  uint32_t* As = Ab + kTcTileFloats;
+  uint32_t* Bb = As + kTcTileFloats;
+  uint32_t* Bs = Bb + kTcTileFloats;
+  constexpr uint32_t idesc = tc_idesc_tf32_128x128();
+  const int nchunks = (K + kTcKC - 1) / kTcKC;
+  // Element i of the first 64 rows of a chunk sits at float i of the tile:
+  // core matrix i / 32 (row group, K group), row (i % 32) / 4, column i % 4;
+  // the second 64 rows follow 1024 floats later.  Each thread owns i = tid +
+  // 256 j (j < 4); consecutive threads write consecutive words.
+  constexpr int kPer = 64 * kTcKC / 256;
+  float2 va[kPer], vb[kPer];
+  auto gather = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + 256 * j;
+      const int cm = i >> 5, w = i & 31;
+      const int m = (cm / (kTcKC / 4)) * 8 + (w >> 2);
+      const int gk = k0 + (cm % (kTcKC / 4)) * 4 + (w & 3);
+      va[j] = (gk < K && m < M) ? a_of(m, gk) : make_float2(0.f, 0.f);
+      vb[j] = (gk < K && m < N) ? b_of(gk, m) : make_float2(0.f, 0.f);
+    }
+  };
+  gather(0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    // stage chunk: A' rows m (real) and 64 + m (imaginary); B'^T rows n
+    // (real) and 64 + n (imaginary), K contiguous
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int o0 = tid + 256 * j, o1 = o0 + 64 * kTcKC;
+      const float2 a = va[j], b = vb[j];
+      const uint32_t arb = to_tf32(a.x), aib = to_tf32(a.y);
+      const uint32_t brb = to_tf32(b.x), bib = to_tf32(b.y);
+      Ab[o0] = arb;
+      Ab[o1] = aib;
+      As[o0] = to_tf32(a.x - __uint_as_float(arb));
+      As[o1] = to_tf32(a.y - __uint_as_float(aib));
+      Bb[o0] = brb;
+      Bb[o1] = bib;
+      Bs[o0] = to_tf32(b.x - __uint_as_float(brb));
+      Bs[o1] = to_tf32(b.y - __uint_as_float(bib));
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ab = smem_u32(Ab), as = smem_u32(As), bb = smem_u32(Bb), bs = smem_u32(Bs);
+#pragma unroll
+      for (int ks = 0; ks < kTcKC / 8; ++ks) {
+        const uint32_t step = ks * 2 * 128;        // two core matrices along K
+        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bb + step), idesc, acc0);
+        tc_mma(s.tmem, tc_desc(as + step), tc_desc(bb + step), idesc, 1u);
+        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bs + step), idesc, 1u);
+      }
+      tc_commit(s.mbar);
+    }
+    // the next chunk's loads overlap the MMAs of this one
+    if (ch + 1 < nchunks) gather((ch + 1) * kTcKC);
+    // warp 0 polls the mbarrier (each poll is a shared-memory operation);
+    // the other warps sleep in the barrier, which also shares the outcome
+    bool timeout = false;
+    if (tid < 32) timeout = !mbar_wait(s.mbar, s.phase);
+    if (__syncthreads_or(timeout)) s.ok = false;
+    s.phase ^= 1u;
+    tc_fence_after();
+  }
+  // epilogue: lanes m (warps 0, 1 and 4, 5) hold the ReA rows, lanes 64 + m
+  // (warps 2, 3 and 6, 7) the ImA rows; warps w and w + 4 split the columns
+  const int w = tid >> 5, q = w & 3, half = w >> 2;
+  const int row = q * 32 + (tid & 31);
+  const uint32_t lane_addr = s.tmem + ((uint32_t)(q * 32) << 16);
+  float v[16];
+  if (q < 2) {
+    const int m = row;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      tmem_ld16(lane_addr + half * 64 + c * 16, v);
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c * 16 + j;
+          if (n < N) {
+            if (half == 0) C[m * ldc + n].x = v[j];   // ReA ReB
+            else C[m * ldc + n].y = v[j];              // ReA ImB
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (q >= 2) {
+    const int m = row - 64;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      tmem_ld16(lane_addr + half * 64 + c * 16, v);
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c * 16 + j;
+          if (n < N) {
+            if (half == 0) C[m * ldc + n].y = (C[m * ldc + n].y + v[j]) * scale;   // + ImA ReB
+            else C[m * ldc + n].x = (C[m * ldc + n].x - v[j]) * scale;             // - ImA ImB
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+}
+
+}  // namespace fmm

@@ -27,6 +27,7 @@
 
 #include "fft_core.cuh"
 #include "plan_internal.h"
+#include "tc_cgemm.cuh"
 
 namespace fmm {
 
@@ -34,6 +35,7 @@ namespace fmm {
 enum : int {
   kStatusRankOverflow = 1,   // a direction's ranks exceed the launch's shared memory
   kStatusBadShape = 2,       // launch shape does not match the problem
+  kStatusTcTimeout = 4,      // a tensor-core wait ran out of polls
 };
 
 struct XPassParams {
@@ -53,6 +55,14 @@ struct YZParams {
   double scale;        // restore scale 1 / (n1 n2 n3)
   int rmax_a, rmax_b;  // shared-memory capacity of the launch (ranks)
   int* status;
+  int tc;              // 1: restore on the tensor cores (TcRestore)
+};
+
+// Plans whose restore runs on the tensor cores (3xTF32): complex64, 64 x 64
+// planes, and for the Tucker-like format at most 64 columns of H_p[x].
+template <typename R, int N2, int N3, int FMT>
+struct TcRestore {
+  static constexpr bool available = sizeof(R) == 4 && N2 == 64 && N3 == 64 && FMT != 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -217,14 +227,21 @@ struct YZLayout {
     const size_t a = (fmt == 1) ? (size_t)rb * ra + (size_t)ra * N2 : 0, b = (size_t)N3 * rb;
     return (size_t)rb * N2 + (a > b ? a : b);
   }
-  static size_t smem_bytes(int fmt, int ra, int rb) {
-    size_t work = plane_elems;
-    if (fmt != 0) { const size_t r = restore_elems(fmt, ra, rb); if (r > work) work = r; }
-    return sizeof(cx<R>) * (fixed_elems + work);
+  // tensor-core restore: operand chunks + mbarrier, then G (rb x (N2 + 1), FMT 1)
+  static size_t restore_bytes_tc(int fmt, int rb) {
+    return kTcSmemBytes + (fmt == 1 ? sizeof(cx<R>) * (size_t)rb * (N2 + 1) : 0);
+  }
+  static size_t smem_bytes(int fmt, int ra, int rb, bool tc = false) {
+    size_t work = sizeof(cx<R>) * plane_elems;
+    if (fmt != 0) {
+      const size_t r = tc ? restore_bytes_tc(fmt, rb) : sizeof(cx<R>) * restore_elems(fmt, ra, rb);
+      if (r > work) work = r;
+    }
+    return sizeof(cx<R>) * fixed_elems + work;
   }
 };
 
-template <typename R, int N2, int N3, int FMT>
+template <typename R, int N2, int N3, int FMT, bool TC>
 __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
   using C = cx<R>;
   using LY = YZLayout<R, N2, N3>;
@@ -255,33 +272,61 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       return;
     }
     const C* H = reinterpret_cast<const C*>(d.h) + (size_t)x * d.hx;
-    C* Gt = work;                              // rb x N2
-    C* U3s = Gt + rb * N2;                     // N3 x rb (stage B)
-    if constexpr (FMT == 1) {
-      C* Ht = Gt + rb * N2;                    // rb x ra
-      C* U2t = Ht + rb * ra;                   // ra x N2
-      const C* U2 = reinterpret_cast<const C*>(d.u2);
-      for (int i = tid; i < ra * rb; i += kThreads) {
-        const int b = i / rb, c = i - b * rb;
-        Ht[c * ra + b] = H[i];
+    if constexpr (TC) {
+      // tensor cores, 3xTF32 (tc_cgemm.cuh); factors read straight from L2
+      __shared__ uint32_t tmem_slot;
+      TcState tc = tc_setup(work, &tmem_slot);
+      const float2* U3 = reinterpret_cast<const float2*>(d.u3);
+      const float2* Hf = reinterpret_cast<const float2*>(H);
+      if constexpr (FMT == 1) {
+        float2* G = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(work) + kTcSmemBytes);
+        const float2* U2 = reinterpret_cast<const float2*>(d.u2);
+        // G[c][y] = sum_b H_p[x][b][c] U2[y][b]; odd pitch PY: the epilogue
+        // writes one row per lane
+        tc_cgemm64(tc, rb, N2, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+                   [&](int b, int y) { return U2[y * ra + b]; }, G, PY, 1.0f);
+        // slab[z][y] = scale sum_c U3[z][c] G[c][y]
+        tc_cgemm64(tc, N3, N2, rb, [&](int z, int c) { return U3[z * rb + c]; },
+                   [&](int c, int y) { return G[c * PY + y]; }, reinterpret_cast<float2*>(Tt), PY,
+                   (float)P.scale);
+      } else {
+        // slab[z][y] = scale sum_b R_p[z][b] T1[x][y][b]
+        tc_cgemm64(tc, N3, N2, rb, [&](int z, int b) { return U3[z * rb + b]; },
+                   [&](int b, int y) { return Hf[y * rb + b]; }, reinterpret_cast<float2*>(Tt), PY,
+                   (float)P.scale);
       }
-      for (int i = tid; i < N2 * ra; i += kThreads) {
-        const int y = i / ra, b = i - y * ra;
-        U2t[b * N2 + y] = U2[i];
+      if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
+      tc_teardown(tc);
+    } else {
+      // CUDA cores
+      C* Gt = work;                              // rb x N2
+      C* U3s = Gt + rb * N2;                     // N3 x rb (stage B)
+      if constexpr (FMT == 1) {
+        C* Ht = Gt + rb * N2;                    // rb x ra
+        C* U2t = Ht + rb * ra;                   // ra x N2
+        const C* U2 = reinterpret_cast<const C*>(d.u2);
+        for (int i = tid; i < ra * rb; i += kThreads) {
+          const int b = i / rb, c = i - b * rb;
+          Ht[c * ra + b] = H[i];
+        }
+        for (int i = tid; i < N2 * ra; i += kThreads) {
+          const int y = i / ra, b = i - y * ra;
+          U2t[b * N2 + y] = U2[i];
+        }
+        __syncthreads();
+        block_cgemm<8, (N2 >= 64 ? 2 : 1)>(rb, N2, ra, Ht, ra, U2t, N2, Gt, N2, (R)1);
+      } else {
+        for (int i = tid; i < N2 * rb; i += kThreads) {
+          const int y = i / rb, b = i - y * rb;
+          Gt[b * N2 + y] = H[i];
+        }
       }
       __syncthreads();
-      block_cgemm<8, (N2 >= 64 ? 2 : 1)>(rb, N2, ra, Ht, ra, U2t, N2, Gt, N2, (R)1);
-    } else {
-      for (int i = tid; i < N2 * rb; i += kThreads) {
-        const int y = i / rb, b = i - y * rb;
-        Gt[b * N2 + y] = H[i];
-      }
+      const C* U3 = reinterpret_cast<const C*>(d.u3);
+      for (int i = tid; i < N3 * rb; i += kThreads) U3s[i] = U3[i];
+      __syncthreads();
+      block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
     }
-    __syncthreads();
-    const C* U3 = reinterpret_cast<const C*>(d.u3);
-    for (int i = tid; i < N3 * rb; i += kThreads) U3s[i] = U3[i];
-    __syncthreads();
-    block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
   }
   __syncthreads();
 

@@ -64,34 +64,41 @@ static cudaError_t launch_x(bool fwd, int n1, const XPassParams& P, int F, cudaS
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
 template <typename R, int N2>
-static size_t yz_smem_n3(int n3, int fmt, int ra, int rb) {
+static size_t yz_smem_n3(int n3, int fmt, int ra, int rb, bool tc) {
   switch (n3) {
-    case 4: return YZLayout<R, N2, 4>::smem_bytes(fmt, ra, rb);
-    case 8: return YZLayout<R, N2, 8>::smem_bytes(fmt, ra, rb);
-    case 16: return YZLayout<R, N2, 16>::smem_bytes(fmt, ra, rb);
-    case 32: return YZLayout<R, N2, 32>::smem_bytes(fmt, ra, rb);
-    case 64: return YZLayout<R, N2, 64>::smem_bytes(fmt, ra, rb);
-    case 128: return YZLayout<R, N2, 128>::smem_bytes(fmt, ra, rb);
+    case 4: return YZLayout<R, N2, 4>::smem_bytes(fmt, ra, rb, tc);
+    case 8: return YZLayout<R, N2, 8>::smem_bytes(fmt, ra, rb, tc);
+    case 16: return YZLayout<R, N2, 16>::smem_bytes(fmt, ra, rb, tc);
+    case 32: return YZLayout<R, N2, 32>::smem_bytes(fmt, ra, rb, tc);
+    case 64: return YZLayout<R, N2, 64>::smem_bytes(fmt, ra, rb, tc);
+    case 128: return YZLayout<R, N2, 128>::smem_bytes(fmt, ra, rb, tc);
     default: return 0;
   }
 }
 
 template <typename R>
-static size_t yz_smem_any(int n2, int n3, int fmt, int ra, int rb) {
+static size_t yz_smem_any(int n2, int n3, int fmt, int ra, int rb, bool tc) {
   switch (n2) {
-    case 4: return yz_smem_n3<R, 4>(n3, fmt, ra, rb);
-    case 8: return yz_smem_n3<R, 8>(n3, fmt, ra, rb);
-    case 16: return yz_smem_n3<R, 16>(n3, fmt, ra, rb);
-    case 32: return yz_smem_n3<R, 32>(n3, fmt, ra, rb);
-    case 64: return yz_smem_n3<R, 64>(n3, fmt, ra, rb);
-    case 128: return yz_smem_n3<R, 128>(n3, fmt, ra, rb);
+    case 4: return yz_smem_n3<R, 4>(n3, fmt, ra, rb, tc);
+    case 8: return yz_smem_n3<R, 8>(n3, fmt, ra, rb, tc);
+    case 16: return yz_smem_n3<R, 16>(n3, fmt, ra, rb, tc);
+    case 32: return yz_smem_n3<R, 32>(n3, fmt, ra, rb, tc);
+    case 64: return yz_smem_n3<R, 64>(n3, fmt, ra, rb, tc);
+    case 128: return yz_smem_n3<R, 128>(n3, fmt, ra, rb, tc);
     default: return 0;
   }
 }
 
+bool tc_restore_applies(const TranslateArgs& a) {
+  return a.precision == FMMFFT_PREC_C64_3XTF32 && a.yz_fmt != 0 && a.n[1] == 64 && a.n[2] == 64 &&
+         (a.yz_fmt == 2 || a.rmax_b <= 64);
+}
+
 size_t yz_smem_bytes(const TranslateArgs& a) {
-  return a.precision == FMMFFT_PREC_C128 ? yz_smem_any<double>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b)
-                                         : yz_smem_any<float>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b);
+  const bool tc = a.tc != 0;
+  return a.precision == FMMFFT_PREC_C128
+             ? yz_smem_any<double>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b, false)
+             : yz_smem_any<float>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b, tc);
 }
 
 bool translate_supported(const TranslateArgs& a) {
@@ -162,6 +169,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   Y.rmax_a = a.rmax_a;
   Y.rmax_b = a.rmax_b;
   Y.status = a.status;
+  Y.tc = a.tc;
   const size_t smem = yz_smem_bytes(a);
   dim3 grid(a.n[0], a.n_dir);
   if ((e = launch_yz(a, Y, grid, smem)) != cudaSuccess) return e;

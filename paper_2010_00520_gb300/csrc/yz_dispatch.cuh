@@ -7,10 +7,10 @@
 
 namespace fmm {
 
-template <typename R, int N2, int N3, int FMT>
-cudaError_t launch_yz_inst(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
+template <typename R, int N2, int N3, int FMT, bool TC>
+cudaError_t launch_yz_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
   static size_t configured = 0;
-  auto kern = yz_kernel<R, N2, N3, FMT>;
+  auto kern = yz_kernel<R, N2, N3, FMT, TC>;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -18,6 +18,14 @@ cudaError_t launch_yz_inst(const YZParams& P, dim3 grid, size_t smem, cudaStream
   }
   kern<<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
+}
+
+template <typename R, int N2, int N3, int FMT>
+cudaError_t launch_yz_inst(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
+  if constexpr (TcRestore<R, N2, N3, FMT>::available) {
+    if (P.tc) return launch_yz_tc<R, N2, N3, FMT, true>(P, grid, smem, s);
+  }
+  return launch_yz_tc<R, N2, N3, FMT, false>(P, grid, smem, s);
 }
 
 template <typename R, int FMT, int N2>

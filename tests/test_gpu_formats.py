@@ -104,3 +104,64 @@ def test_library_compression_acceptance(native, cuda, fmt, dec):
         assert _rel(out, ref) <= tol + 1e-5
     finally:
         F.fmmfft_plan_destroy(h)
+
+
+def _import_any(F, h, fmt, dec, comp):
+    if fmt == "3d" and dec == "tucker":
+        P = comp.parts
+        F.fmmfft_import_tucker3d(h, np.array([t.ranks for t in P], dtype=np.int32),
+                                 np.concatenate([t.core.ravel() for t in P]),
+                                 *[np.concatenate([t.factors[i].ravel() for t in P]) for i in range(3)])
+    else:
+        _import(F, h, fmt, dec, comp.parts)
+
+
+@pytest.mark.parametrize("fmt,dec", [("3d", "tucker")] + CASES)
+def test_tensor_core_restore_matches_oracle(native, cuda, fmt, dec):
+    """FMMFFT_PREC_C64_3XTF32 on 64 x 64 y-z planes: the slab restores run on
+    the tensor cores (tcgen05, 3xTF32).  Same imported factors as the oracle;
+    the 3xTF32 products keep the FP32-level bound of the CUDA-core path."""
+    F, torch = native, cuda
+    K, L, nrhs, tol = (9, 30, 32), 2, 2, 1e-4
+    plan = pl.Plan(K=K, L=L)
+    assert plan.n[1:] == (64, 64)
+    ops = pl.operators(plan)
+    comp = pl.compress(ops, fmt, dec, tol)
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, FMT[fmt], DEC[dec], tol)
+    try:
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64_3XTF32)
+        _import_any(F, h, fmt, dec, comp)
+        assert F.fmmfft_plan_stats(h)["restore_on_tensor_cores"] == 1
+        S = field_spectra(81 + DEC[dec], plan.n_dir, nrhs, K)
+        out = _run(F, torch, h, S, nrhs)
+        assert _rel(out, pl.translate_with(comp.restore, S)) <= 2e-6
+    finally:
+        F.fmmfft_plan_destroy(h)
+
+
+def test_tensor_core_restore_benchmark_workload(native, cuda):
+    """The benchmark's compressed arm (32^3 boxes, L = 8, Tucker-3D tol 1e-4,
+    3xTF32 restores on the tensor cores, 2 x 4 fields per direction), sampled
+    fields against the oracle's uncompressed FP64 translation."""
+    F, torch = native, cuda
+    K, L, tol, nrhs = (32, 32, 32), 8, 1e-4, 4
+    plan = pl.Plan(K=K, L=L)
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, 3, 1, tol)
+    try:
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64_3XTF32)
+        F.fmmfft_compress(h)
+        assert F.fmmfft_plan_stats(h)["restore_on_tensor_cores"] == 1
+        S = field_spectra(1002, plan.n_dir, nrhs, K).astype(np.complex64)
+        out = _run(F, torch, h, S, nrhs)
+        from seeded_inputs import field_spectra_rows
+        from oracle import translate as tr
+        fields = [0, 7, 648 + 3, 1295]
+        A = field_spectra_rows(1002, plan.n_dir, nrhs, K, np.array(fields))
+        for i, f in enumerate(fields):
+            p, rem = divmod(f, 2 * nrhs)
+            pol, r = divmod(rem, nrhs)
+            T = pl.operators(plan, [p])[0]
+            ref = tr.translate_field_fft(T, A[i].astype(np.complex64).astype(np.complex128))
+            assert _rel(out[p, pol, r], ref) <= tol + 1e-5
+    finally:
+        F.fmmfft_plan_destroy(h)
