@@ -43,7 +43,7 @@ WL = dict(name="tucker3d_32cube_L8_tol1e-4_2pol_4rhs", K=(32, 32, 32), L=8, a=0.
           tol=1e-4, nrhs=4, seed=1002)
 CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
 # version of the yz kernel the committed DRAM-traffic figure was taken on
-YZ_KERNEL_VERSION = 1
+YZ_KERNEL_VERSION = 2
 
 
 def _units(n, n_dir, nrhs):
@@ -400,7 +400,7 @@ def main():
         with open(prof) as f:
             tj = json.load(f)
         # counters only count for the kernel they were taken on
-        if tj.get("kernel_version") == YZ_KERNEL_VERSION and nrhs == WL["nrhs"]:
+        if tj.get("kernel_version") == YZ_KERNEL_VERSION and nrhs == WL["nrhs"] and args.restore == "3xtf32":
             traffic = tj.get("dram_bytes_per_launch")
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
