@@ -365,4 +365,35 @@ __device__ __forceinline__ void block_cgemm(int M, int N, int K, const C* A, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Complex GEMM with general strides, all threads of the block, operands and
+// result anywhere (shared or global memory):
+//   Cm[m * ldc + n] = scale * sum_k A[m * sam + k * sak] * B[k * sbk + n * sbn]
+// Each thread computes outputs (m, n) with n = lane + 32 j of a 4-row group.
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ void block_cgemm_strided(int M, int N, int K, const C* A, long sam, long sak,
+                                                    const C* B, long sbk, long sbn, C* Cm, long ldc,
+                                                    typename real_of<C>::type scale) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nrb = (M + 3) / 4, ncb = (N + 31) / 32;
+  for (int item = w; item < nrb * ncb; item += nw) {
+    const int m0 = (item / ncb) * 4, n = (item % ncb) * 32 + lane;
+    C acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = czero<C>();
+    if (n < N) {
+      for (int k = 0; k < K; ++k) {
+        const C b = B[k * sbk + n * sbn];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (m0 + i < M) cfma(acc[i], A[(m0 + i) * sam + k * sak], b);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (m0 + i < M) Cm[(m0 + i) * ldc + n] = mk<C>(acc[i].x * scale, acc[i].y * scale);
+    }
+  }
+}
+
 }  // namespace fmm

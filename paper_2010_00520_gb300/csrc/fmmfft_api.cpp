@@ -36,6 +36,9 @@ struct fmmfft_plan_s {
   int n_stages = 0;
   int yz_fmt = 0;
   int rmax_a = 0, rmax_b = 0;
+  void* d_slabs = nullptr;      // large planes: per-block slab slots
+  size_t slabs_bytes = 0;
+  int large_grid = 0;           // blocks of the persistent large-plane kernel
   void* d_inter = nullptr;
   size_t inter_bytes = 0;
   void* d_io = nullptr;       // device copies for fmmfft_translate_host
@@ -81,6 +84,8 @@ void release_operator(fmmfft_plan_s* p) {
   free_dev(d);
   p->d_gemm = nullptr;
   p->n_stages = 0;
+  free_dev(p->d_slabs);
+  p->slabs_bytes = 0;
   p->ready = false;
 }
 
@@ -156,7 +161,37 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   for (int i = 0; i < p->n_stages; ++i) a.stages[i] = p->stages[i];
   a.status = p->d_status;
   a.tc = fmm::tc_restore_applies(a) ? 1 : 0;
+  fmm::plan_yz(a);
+  a.large_grid = p->large_grid;
+  a.slab_scratch = p->d_slabs;
   return a;
+}
+
+// Blocks of the persistent large-plane yz kernel: two per SM of the current
+// device (its shared memory allows no more).
+int query_large_grid(fmmfft_plan_s* p) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  p->large_grid = 2 * sms;
+  return FMMFFT_OK;
+}
+
+// Slab slots of the large-plane kernel for a compressed plan that needs them.
+int ensure_slabs(fmmfft_plan_s* p) {
+  fmm::TranslateArgs a = base_args(p);
+  if (!a.large || a.yz_fmt == 0) return FMMFFT_OK;
+  const size_t bytes = (size_t)a.large_grid * (size_t)a.slot_elems * elem_bytes(p);
+  if (bytes <= p->slabs_bytes && p->d_slabs) return FMMFFT_OK;
+  free_dev(p->d_slabs);
+  p->slabs_bytes = 0;
+  int st = dev_alloc(&p->d_slabs, bytes);
+  if (st != FMMFFT_OK) return st;
+  p->slabs_bytes = bytes;
+  return FMMFFT_OK;
 }
 
 // Plain store: T~_p scaled by 1/(n1 n2 n3), [p][x][z][y].  `That` is indexed
@@ -325,8 +360,10 @@ int install_layout(fmmfft_plan_s* p, const fmm::Layout& L) {
   release_operator(p);
   adopt_layout_shape(p, L);
   if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
-  int st = upload_layout(p, L);
+  int st = query_large_grid(p);
   if (st != FMMFFT_OK) return st;
+  if ((st = upload_layout(p, L)) != FMMFFT_OK) return st;
+  if ((st = ensure_slabs(p)) != FMMFFT_OK) return st;
   if ((st = ensure_common(p)) != FMMFFT_OK) return st;
   p->ready = true;
   return FMMFFT_OK;
@@ -443,6 +480,7 @@ int fmmfft_compress(fmmfft_plan p) {
   if (p->format == FMMFFT_FORMAT_NONE) {
     if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
     release_operator(p);
+    if ((st = query_large_grid(p)) != FMMFFT_OK) return st;
     const fmm::OperatorSpec s = spec_of(p);
     std::vector<std::vector<cdouble>> ops(p->n_dir);
     fmm::parallel_for(p->n_dir, [&](int d) { fmm::fft_operator(s, &p->khat[3 * d], ops[d]); });
@@ -464,9 +502,11 @@ int fmmfft_import_plain(fmmfft_plan p, const double* That) {
   if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   release_operator(p);
+  int st = query_large_grid(p);
+  if (st != FMMFFT_OK) return st;
   const size_t per = (size_t)p->n[0] * p->n[1] * p->n[2];
   const cdouble* T = reinterpret_cast<const cdouble*>(That);
-  int st = upload_plain(p, [&](int d) { return T + per * d; });
+  st = upload_plain(p, [&](int d) { return T + per * d; });
   if (st != FMMFFT_OK) return st;
   if ((st = ensure_common(p)) != FMMFFT_OK) return st;
   p->ready = true;
@@ -787,7 +827,7 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   o->elements_compressed = p->elements_compressed;
   o->saving = p->elements_plain ? 1.0 - (double)p->elements_compressed / (double)p->elements_plain : 0.0;
   o->device_bytes_operator = p->bytes_operator;
-  o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes) + p->bytes_restore;
+  o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes + p->slabs_bytes) + p->bytes_restore;
   o->setup_seconds = p->setup_seconds;
   o->restore_on_tensor_cores = p->ready ? base_args(p).tc : 0;
   return FMMFFT_OK;

@@ -62,6 +62,11 @@ struct TranslateArgs {
   const SlabDesc* slab;              // device, n_dir entries
   int rmax_a, rmax_b;                // largest ra, rb over directions
   int tc;                            // 1: slab restores on the tensor cores (3xTF32)
+  // large y-z planes (persistent yz kernel, slabs in global scratch)
+  int large;                         // set by plan_yz
+  long long slot_elems;              // scratch elements per block (set by plan_yz)
+  int large_grid;                    // blocks of the persistent kernel
+  void* slab_scratch;                // large_grid * slot_elems elements
   int n_stages;                      // pre-pass launches, in order
   GemmStage stages[kMaxGemmStages];
   int* status;                       // device status word
@@ -75,6 +80,10 @@ cudaError_t launch_translate(const TranslateArgs& a);
 // 0 if the sizes are not supported by the compiled kernels.
 size_t yz_smem_bytes(const TranslateArgs& a);
 bool translate_supported(const TranslateArgs& a);
+// Choose the yz kernel for the args: the fused one when its shared memory
+// fits, else the large-plane one; sets a.large and a.slot_elems.  False when
+// neither fits.
+bool plan_yz(TranslateArgs& a);
 // Whether the slab restores of these args run on the tensor cores (3xTF32).
 bool tc_restore_applies(const TranslateArgs& a);
 

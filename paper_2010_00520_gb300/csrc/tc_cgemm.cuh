@@ -30,7 +30,7 @@ namespace fmm {
 
 constexpr int kTcKC = 16;                              // complex K per chunk
 constexpr int kTcTileFloats = 128 * kTcKC;             // one 128 x KC operand split
-constexpr size_t kTcSmemBytes = 4 * kTcTileFloats * sizeof(float) + 16;  // A big/small, B big/small, mbarrier
+constexpr size_t kTcSmemBytes = 4 * kTcTileFloats * sizeof(float);  // A big/small, B big/small
 constexpr int kTcCols = 128;                           // TMEM columns of D
 constexpr unsigned kTcWaitLimit = 1u << 24;            // mbarrier poll limit
 
@@ -152,12 +152,13 @@ struct TcState {
 };
 
 // Block-wide set-up: `buf` (kTcSmemBytes, 16-byte aligned) holds the operand
-// chunks and the mbarrier; `slot` receives the TMEM address.  Warp 0
+// chunks, `bar` is the mbarrier (8 bytes of shared memory that nothing else
+// uses while the state lives) and `slot` receives the TMEM address.  Warp 0
 // allocates kTcCols columns.  All threads call it.
-__device__ __forceinline__ TcState tc_setup(void* buf, uint32_t* slot) {
+__device__ __forceinline__ TcState tc_setup(void* buf, uint64_t* bar, uint32_t* slot) {
   TcState s;
   s.buf = reinterpret_cast<float*>(buf);
-  s.mbar = smem_u32(s.buf + 4 * kTcTileFloats);
+  s.mbar = smem_u32(bar);
   if (threadIdx.x == 0) {
     mbar_init(s.mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

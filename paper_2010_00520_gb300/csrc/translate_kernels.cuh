@@ -56,13 +56,16 @@ struct YZParams {
   int rmax_a, rmax_b;  // shared-memory capacity of the launch (ranks)
   int* status;
   int tc;              // 1: restore on the tensor cores (TcRestore)
+  int n_dir;
+  void* slab_scratch;  // large planes: one slot of slot_elems per block
+  long long slot_elems;
 };
 
 // Plans whose restore runs on the tensor cores (3xTF32): complex64, 64 x 64
 // planes, and for the Tucker-like format at most 64 columns of H_p[x].
 template <typename R, int N2, int N3, int FMT>
 struct TcRestore {
-  static constexpr bool available = sizeof(R) == 4 && N2 == 64 && N3 == 64 && FMT != 0;
+  static constexpr bool available = sizeof(R) == 4 && N2 % 64 == 0 && N3 % 64 == 0 && FMT != 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -209,6 +212,68 @@ __global__ void __launch_bounds__(kThreads) cgemm_batched_kernel(const GemmDesc*
 }
 
 // ---------------------------------------------------------------------------
+// The per-field work of a yz block (x, p): for each field of direction p,
+// forward y DFT of rows z < Kz, z DFT x Hadamard with the slab x inverse z DFT
+// of every column, inverse y DFT, corner written back in place.  `op` is the
+// slab T~_p[x] as [z][y] with row pitch `op_pitch` (shared or global memory);
+// `plane` holds N3 / 2 rows of pitch N2 + 1.
+// ---------------------------------------------------------------------------
+template <typename R, int N2, int N3>
+__device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>* plane, cx<R>* xs,
+                                          const cx<R>* tw2, const cx<R>* tw3, const cx<R>* op,
+                                          int op_pitch) {
+  using C = cx<R>;
+  constexpr int PY = N2 + 1;
+  const int tid = threadIdx.x;
+  const int Ky = P.Ky, Kz = P.Kz;
+  __syncthreads();
+  // rows Kz .. N3/2 - 1 stay zero for every field
+  for (int i = tid; i < (N3 / 2 - Kz) * N2; i += kThreads) {
+    const int z = Kz + i / N2, y = i % N2;
+    plane[z * PY + y] = czero<C>();
+  }
+  TeamPos<N2> ty;
+  TeamPos<N3> tz;
+  C* xy = ty.xs(xs);
+  C* xz = tz.xs(xs);
+  C* inter = reinterpret_cast<C*>(P.inter);
+  const int hy = N2 / 2;
+  for (int j = 0; j < P.nf; ++j) {
+    const size_t f = (size_t)p * P.nf + j;
+    C* io = inter + (f * P.n1 + x) * (size_t)(Kz * Ky);
+    __syncthreads();
+    for (int i = tid; i < Kz * hy; i += kThreads) {
+      const int z = i / hy, y = i - z * hy;
+      plane[z * PY + y] = (y < Ky) ? io[z * Ky + y] : czero<C>();
+    }
+    __syncthreads();
+    for (int base = 0; base < Kz; base += Line<N2>::LPI) {
+      const int ln = base + ty.line;
+      const bool act = ln < Kz;
+      line_fft<N2, -1, true>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, N2);
+    }
+    __syncthreads();
+    for (int base = 0; base < N2; base += Line<N3>::LPI) {
+      const int col = base + tz.line;
+      const bool act = col < N2;
+      const int cc = act ? col : 0;
+      line_conv<N3>(plane + cc, PY, xz, tw3, op + cc, op_pitch, tz.t, act, Kz);
+    }
+    __syncthreads();
+    for (int base = 0; base < Kz; base += Line<N2>::LPI) {
+      const int ln = base + ty.line;
+      const bool act = ln < Kz;
+      line_fft<N2, +1, false>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, Ky);
+    }
+    __syncthreads();
+    for (int i = tid; i < Kz * Ky; i += kThreads) {
+      const int z = i / Ky, y = i - z * Ky;
+      io[i] = plane[z * PY + y];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // yz pass.  FMT 0: plain operator from global memory.  FMT 1: Tucker-like
 // restore of the slab (Fig. 3(a) steps 2-3, with the factors of the format):
 //   T~_p[x][y][z] = sum_{b,c} U2[y][b] H_p[x][b][c] U3[z][c]
@@ -275,7 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
     if constexpr (TC) {
       // tensor cores, 3xTF32 (tc_cgemm.cuh); factors read straight from L2
       __shared__ uint32_t tmem_slot;
-      TcState tc = tc_setup(work, &tmem_slot);
+      __shared__ uint64_t tc_bar;
+      TcState tc = tc_setup(work, &tc_bar, &tmem_slot);
       const float2* U3 = reinterpret_cast<const float2*>(d.u3);
       const float2* Hf = reinterpret_cast<const float2*>(H);
       if constexpr (FMT == 1) {
@@ -328,52 +394,114 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
     }
   }
-  __syncthreads();
+  yz_fields<R, N2, N3>(P, x, p, plane, xs, tw2, tw3, Tt, PY);
+}
 
-  const int Ky = P.Ky, Kz = P.Kz;
-  // rows Kz .. N3/2 - 1 stay zero for every field
-  for (int i = tid; i < (N3 / 2 - Kz) * N2; i += kThreads) {
-    const int z = Kz + i / N2, y = i % N2;
-    plane[z * PY + y] = czero<C>();
+// ---------------------------------------------------------------------------
+// yz pass for y-z planes too large for the slab and the field plane to share
+// the shared memory (n2 x n3 = 128 x 128, 256 x 64, 256 x 128).  Persistent
+// blocks walk the (x, p) items; the slab T~_p[x] stays in global memory: the
+// plain operator in place, a restored slab in the block's own scratch slot,
+// which stays resident in L2 while the block's fields use it.  Shared memory
+// holds the twiddles, half a field plane and the exchange buffers; the
+// restore's staging (tensor-core operand chunks) reuses the plane.
+// ---------------------------------------------------------------------------
+template <typename R, int N2, int N3>
+struct YZLLayout {
+  static constexpr int PY = N2 + 1;
+  static constexpr int XW = (Line<N2>::XW > Line<N3>::XW) ? Line<N2>::XW : Line<N3>::XW;
+  static constexpr size_t plane_elems = (size_t)(N3 / 2) * PY + kWarps * XW;
+  static size_t smem_bytes(int fmt, bool tc) {
+    size_t work = sizeof(cx<R>) * plane_elems;
+    if (fmt != 0 && tc && kTcSmemBytes > work) work = kTcSmemBytes;
+    return sizeof(cx<R>) * (N2 + N3) + work;
   }
-  TeamPos<N2> ty;
-  TeamPos<N3> tz;
-  C* xy = ty.xs(xs);
-  C* xz = tz.xs(xs);
-  C* inter = reinterpret_cast<C*>(P.inter);
-  const int hy = N2 / 2;
-  for (int j = 0; j < P.nf; ++j) {
-    const size_t f = (size_t)p * P.nf + j;
-    C* io = inter + (f * P.n1 + x) * (size_t)(Kz * Ky);
-    __syncthreads();
-    for (int i = tid; i < Kz * hy; i += kThreads) {
-      const int z = i / hy, y = i - z * hy;
-      plane[z * PY + y] = (y < Ky) ? io[z * Ky + y] : czero<C>();
+  // global scratch per block: the slab, then G (rb x N2) of the Tucker-like
+  // restore
+  static long long slot_elems(int fmt, int rb) {
+    return fmt == 0 ? 0 : (long long)N3 * N2 + (fmt == 1 ? (long long)rb * N2 : 0);
+  }
+};
+
+template <typename R, int N2, int N3, int FMT, bool TC>
+__global__ void __launch_bounds__(kThreads, 1) yzl_kernel(YZParams P) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw2 = reinterpret_cast<C*>(smem_raw);
+  C* tw3 = tw2 + N2;
+  C* plane = tw3 + N3;                      // N3/2 x (N2 + 1), then exchange
+  C* xs = plane + (N3 / 2) * (N2 + 1);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N2; i += kThreads) tw2[i] = reinterpret_cast<const C*>(P.tw2)[i];
+  for (int i = tid; i < N3; i += kThreads) tw3[i] = reinterpret_cast<const C*>(P.tw3)[i];
+  C* slot = nullptr;
+  C* G = nullptr;
+  if constexpr (FMT != 0) {
+    slot = reinterpret_cast<C*>(P.slab_scratch) + (size_t)blockIdx.x * P.slot_elems;
+    G = slot + (size_t)N3 * N2;
+  }
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint64_t tc_bar;
+  TcState tc;
+  if constexpr (TC) tc = tc_setup(plane, &tc_bar, &tmem_slot);
+  const int items = P.n1 * P.n_dir;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int x = it % P.n1, p = it / P.n1;
+    const C* op;
+    if constexpr (FMT == 0) {
+      op = reinterpret_cast<const C*>(P.op) + ((size_t)p * P.n1 + x) * (N3 * N2);
+    } else {
+      const SlabDesc d = P.desc[p];
+      const int ra = d.ra, rb = d.rb;
+      const bool bad = ra > P.rmax_a || rb > P.rmax_b || (TC && FMT == 1 && rb > 64);
+      if (bad) {
+        if (tid == 0) atomicOr(P.status, kStatusRankOverflow);
+        continue;                                  // uniform over the block
+      }
+      const C* H = reinterpret_cast<const C*>(d.h) + (size_t)x * d.hx;
+      const C* U2 = reinterpret_cast<const C*>(d.u2);
+      const C* U3 = reinterpret_cast<const C*>(d.u3);
+      __syncthreads();                             // previous item done with slot and plane
+      if constexpr (TC) {
+        const float2* Hf = reinterpret_cast<const float2*>(H);
+        const float2* U2f = reinterpret_cast<const float2*>(U2);
+        const float2* U3f = reinterpret_cast<const float2*>(U3);
+        float2* Gf = reinterpret_cast<float2*>(G);
+        float2* Sf = reinterpret_cast<float2*>(slot);
+        if constexpr (FMT == 1) {
+          for (int y0 = 0; y0 < N2; y0 += 64)
+            tc_cgemm64(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+                       [&](int b, int y) { return U2f[(y0 + y) * ra + b]; }, Gf + y0, N2, 1.0f);
+          for (int z0 = 0; z0 < N3; z0 += 64)
+            for (int y0 = 0; y0 < N2; y0 += 64)
+              tc_cgemm64(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
+                         [&](int c, int y) { return Gf[c * N2 + y0 + y]; }, Sf + (size_t)z0 * N2 + y0, N2,
+                         (float)P.scale);
+        } else {
+          for (int z0 = 0; z0 < N3; z0 += 64)
+            for (int y0 = 0; y0 < N2; y0 += 64)
+              tc_cgemm64(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
+                         [&](int b, int y) { return Hf[(y0 + y) * rb + b]; }, Sf + (size_t)z0 * N2 + y0, N2,
+                         (float)P.scale);
+        }
+      } else {
+        if constexpr (FMT == 1) {
+          // G[c][y] = sum_b H[x][b][c] U2[y][b]
+          block_cgemm_strided(rb, N2, ra, H, 1, rb, U2, 1, ra, G, N2, (R)1);
+          __syncthreads();
+          block_cgemm_strided(N3, N2, rb, U3, rb, 1, G, N2, 1, slot, N2, (R)P.scale);
+        } else {
+          block_cgemm_strided(N3, N2, rb, U3, rb, 1, H, 1, rb, slot, N2, (R)P.scale);
+        }
+      }
+      __syncthreads();
+      op = slot;
     }
-    __syncthreads();
-    for (int base = 0; base < Kz; base += Line<N2>::LPI) {
-      const int ln = base + ty.line;
-      const bool act = ln < Kz;
-      line_fft<N2, -1, true>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, N2);
-    }
-    __syncthreads();
-    for (int base = 0; base < N2; base += Line<N3>::LPI) {
-      const int col = base + tz.line;
-      const bool act = col < N2;
-      const int cc = act ? col : 0;
-      line_conv<N3>(plane + cc, PY, xz, tw3, Tt + cc, PY, tz.t, act, Kz);
-    }
-    __syncthreads();
-    for (int base = 0; base < Kz; base += Line<N2>::LPI) {
-      const int ln = base + ty.line;
-      const bool act = ln < Kz;
-      line_fft<N2, +1, false>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, Ky);
-    }
-    __syncthreads();
-    for (int i = tid; i < Kz * Ky; i += kThreads) {
-      const int z = i / Ky, y = i - z * Ky;
-      io[i] = plane[z * PY + y];
-    }
+    yz_fields<R, N2, N3>(P, x, p, plane, xs, tw2, tw3, op, N2);
+  }
+  if constexpr (TC) {
+    if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
+    tc_teardown(tc);
   }
 }
 

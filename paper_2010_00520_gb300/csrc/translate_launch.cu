@@ -13,6 +13,16 @@ FMM_YZ_DECL(f64, 0)
 FMM_YZ_DECL(f64, 1)
 FMM_YZ_DECL(f64, 2)
 #undef FMM_YZ_DECL
+#define FMM_YZL_DECL(TAG, F)                                                                  \
+  cudaError_t launch_yzl_##TAG##_##F(const YZParams& P, int n2, int n3, dim3 grid, size_t smem, \
+                                     cudaStream_t s);
+FMM_YZL_DECL(f32, 0)
+FMM_YZL_DECL(f32, 1)
+FMM_YZL_DECL(f32, 2)
+FMM_YZL_DECL(f64, 0)
+FMM_YZL_DECL(f64, 1)
+FMM_YZL_DECL(f64, 2)
+#undef FMM_YZL_DECL
 
 static const size_t kMaxSmem = 227 * 1024;
 
@@ -90,29 +100,87 @@ static size_t yz_smem_any(int n2, int n3, int fmt, int ra, int rb, bool tc) {
 }
 
 bool tc_restore_applies(const TranslateArgs& a) {
-  return a.precision == FMMFFT_PREC_C64_3XTF32 && a.yz_fmt != 0 && a.n[1] == 64 && a.n[2] == 64 &&
+  return a.precision == FMMFFT_PREC_C64_3XTF32 && a.yz_fmt != 0 && a.n[1] % 64 == 0 && a.n[2] % 64 == 0 &&
          (a.yz_fmt == 2 || a.rmax_b <= 64);
 }
 
-size_t yz_smem_bytes(const TranslateArgs& a) {
+template <typename R>
+static bool yzl_shape(int n2, int n3, int fmt, bool tc, int rb, size_t* smem, long long* slot) {
+#define FMM_YZL_SHAPE(A, B)                                    \
+  if (n2 == A && n3 == B) {                                    \
+    *smem = YZLLayout<R, A, B>::smem_bytes(fmt, tc);           \
+    *slot = YZLLayout<R, A, B>::slot_elems(fmt, rb);           \
+    return true;                                               \
+  }
+  FMM_YZL_SHAPE(128, 128)
+  FMM_YZL_SHAPE(256, 64)
+  FMM_YZL_SHAPE(256, 128)
+#undef FMM_YZL_SHAPE
+  return false;
+}
+
+static size_t yzl_smem_bytes(const TranslateArgs& a, long long* slot) {
+  size_t smem = 0;
+  long long sl = 0;
+  const bool ok = a.precision == FMMFFT_PREC_C128
+                      ? yzl_shape<double>(a.n[1], a.n[2], a.yz_fmt, false, a.rmax_b, &smem, &sl)
+                      : yzl_shape<float>(a.n[1], a.n[2], a.yz_fmt, a.tc != 0, a.rmax_b, &smem, &sl);
+  if (slot) *slot = sl;
+  return ok ? smem : 0;
+}
+
+static size_t yz_fused_smem_bytes(const TranslateArgs& a) {
   const bool tc = a.tc != 0;
+  if (a.n[1] > 128) return 0;
   return a.precision == FMMFFT_PREC_C128
              ? yz_smem_any<double>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b, false)
              : yz_smem_any<float>(a.n[1], a.n[2], a.yz_fmt, a.rmax_a, a.rmax_b, tc);
 }
 
+bool plan_yz(TranslateArgs& a) {
+  a.large = 0;
+  a.slot_elems = 0;
+  const size_t fused = yz_fused_smem_bytes(a);
+  if (fused != 0 && fused <= kMaxSmem) return true;
+  long long slot = 0;
+  const size_t large = yzl_smem_bytes(a, &slot);
+  if (large == 0 || large > kMaxSmem) return false;
+  a.large = 1;
+  a.slot_elems = slot;
+  return true;
+}
+
+size_t yz_smem_bytes(const TranslateArgs& a) {
+  return a.large ? yzl_smem_bytes(a, nullptr) : yz_fused_smem_bytes(a);
+}
+
 bool translate_supported(const TranslateArgs& a) {
-  if (!pow2_in(a.n[0], 4, 256) || !pow2_in(a.n[1], 4, 128) || !pow2_in(a.n[2], 4, 128)) return false;
+  if (!pow2_in(a.n[0], 4, 256) || !pow2_in(a.n[1], 4, 256) || !pow2_in(a.n[2], 4, 128)) return false;
   if (a.yz_fmt < 0 || a.yz_fmt > 2) return false;
-  const size_t s = yz_smem_bytes(a);
-  if (s == 0 || s > kMaxSmem) return false;
+  TranslateArgs b = a;
   // x-pass shared memory at the largest rows-per-block candidate is bounded
   // by construction (<= 96 KB)
-  return true;
+  return plan_yz(b);
 }
 
 static cudaError_t launch_yz(const TranslateArgs& a, const YZParams& Y, dim3 grid, size_t smem) {
   const int n2 = a.n[1], n3 = a.n[2];
+  if (a.large) {
+    if (a.precision == FMMFFT_PREC_C128) {
+      switch (a.yz_fmt) {
+        case 0: return launch_yzl_f64_0(Y, n2, n3, grid, smem, a.stream);
+        case 1: return launch_yzl_f64_1(Y, n2, n3, grid, smem, a.stream);
+        case 2: return launch_yzl_f64_2(Y, n2, n3, grid, smem, a.stream);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    switch (a.yz_fmt) {
+      case 0: return launch_yzl_f32_0(Y, n2, n3, grid, smem, a.stream);
+      case 1: return launch_yzl_f32_1(Y, n2, n3, grid, smem, a.stream);
+      case 2: return launch_yzl_f32_2(Y, n2, n3, grid, smem, a.stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.precision == FMMFFT_PREC_C128) {
     switch (a.yz_fmt) {
       case 0: return launch_yz_f64_0(Y, n2, n3, grid, smem, a.stream);
@@ -170,8 +238,13 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   Y.rmax_b = a.rmax_b;
   Y.status = a.status;
   Y.tc = a.tc;
+  Y.n_dir = a.n_dir;
+  Y.slab_scratch = a.slab_scratch;
+  Y.slot_elems = a.slot_elems;
   const size_t smem = yz_smem_bytes(a);
-  dim3 grid(a.n[0], a.n_dir);
+  if (a.large && a.yz_fmt != 0 && !a.slab_scratch) return cudaErrorInvalidValue;
+  const int items = a.n[0] * a.n_dir;
+  dim3 grid = a.large ? dim3((unsigned)(items < a.large_grid ? items : a.large_grid)) : dim3(a.n[0], a.n_dir);
   if ((e = launch_yz(a, Y, grid, smem)) != cudaSuccess) return e;
   mark(3);
 

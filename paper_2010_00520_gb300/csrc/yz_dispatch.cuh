@@ -54,6 +54,36 @@ cudaError_t launch_yz_fmt(const YZParams& P, int n2, int n3, dim3 grid, size_t s
   }
 }
 
+template <typename R, int N2, int N3, int FMT, bool TC>
+cudaError_t launch_yzl_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
+  static size_t configured = 0;
+  auto kern = yzl_kernel<R, N2, N3, FMT, TC>;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  kern<<<grid, kThreads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+template <typename R, int N2, int N3, int FMT>
+cudaError_t launch_yzl_inst(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
+  if constexpr (TcRestore<R, N2, N3, FMT>::available) {
+    if (P.tc) return launch_yzl_tc<R, N2, N3, FMT, true>(P, grid, smem, s);
+  }
+  return launch_yzl_tc<R, N2, N3, FMT, false>(P, grid, smem, s);
+}
+
+// Large-plane shapes (slab and plane do not fit shared memory together).
+template <typename R, int FMT>
+cudaError_t launch_yzl_fmt(const YZParams& P, int n2, int n3, dim3 grid, size_t smem, cudaStream_t s) {
+  if (n2 == 128 && n3 == 128) return launch_yzl_inst<R, 128, 128, FMT>(P, grid, smem, s);
+  if (n2 == 256 && n3 == 64) return launch_yzl_inst<R, 256, 64, FMT>(P, grid, smem, s);
+  if (n2 == 256 && n3 == 128) return launch_yzl_inst<R, 256, 128, FMT>(P, grid, smem, s);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace fmm
 
 // One translation unit per (type, format).
@@ -62,5 +92,9 @@ cudaError_t launch_yz_fmt(const YZParams& P, int n2, int n3, dim3 grid, size_t s
   cudaError_t launch_yz_##TAG##_##FMT(const YZParams& P, int n2, int n3, dim3 grid, size_t smem, \
                                       cudaStream_t s) {                                      \
     return launch_yz_fmt<R, FMT>(P, n2, n3, grid, smem, s);                                  \
+  }                                                                                          \
+  cudaError_t launch_yzl_##TAG##_##FMT(const YZParams& P, int n2, int n3, dim3 grid, size_t smem, \
+                                       cudaStream_t s) {                                     \
+    return launch_yzl_fmt<R, FMT>(P, n2, n3, grid, smem, s);                                 \
   }                                                                                          \
   }

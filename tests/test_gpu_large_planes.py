@@ -1,0 +1,82 @@
+"""GPU parity on y-z planes too large for the fused yz kernel (128 x 128 and
+256 x 64, the plane shapes of the 64^3-box and 128 x 128 x 32-box workloads),
+which run the persistent large-plane kernel with the slab in a global (L2)
+scratch slot.  Reduced x extent and few directions keep the oracle fast.
+
+Same operator / factors on both sides: rel L2 <= 2e-6 (complex64, FP32 or
+3xTF32 restores), <= 1e-10 (complex128)."""
+import numpy as np
+import pytest
+
+from oracle import pipeline as pl
+from seeded_inputs import field_spectra
+
+pytestmark = pytest.mark.gpu
+
+TWO_PI = 2 * np.pi
+SHAPES = [((8, 64, 64), 1, 2), ((8, 128, 32), 1, 1)]     # n = (16,128,128), (16,256,64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _run(F, torch, h, S, nrhs, c128=False):
+    x = torch.from_numpy(np.ascontiguousarray(S.astype(np.complex128 if c128 else np.complex64))).to("cuda")
+    y = torch.empty_like(x)
+    F.fmmfft_translate(h, x, y, nrhs, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert F.fmmfft_poll_status(h) == 0
+    return y.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("K,L,nrhs", SHAPES)
+@pytest.mark.parametrize("c128", [False, True])
+def test_large_plane_plain(native, cuda, K, L, nrhs, c128):
+    F, torch = native, cuda
+    plan = pl.Plan(K=K, L=L)
+    assert plan.n[1] * plan.n[2] >= 128 * 128
+    ops = pl.operators(plan)
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, 0, 0, 0.0)
+    try:
+        if c128:
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C128)
+        F.fmmfft_import_plain(h, np.stack(ops))
+        S = field_spectra(91, plan.n_dir, nrhs, K)
+        out = _run(F, torch, h, S, nrhs, c128)
+        assert _rel(out, pl.translate_with(lambda p: ops[p], S)) <= (1e-10 if c128 else 2e-6)
+    finally:
+        F.fmmfft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("K,L,nrhs", SHAPES)
+@pytest.mark.parametrize("fmt,dec,prec", [("3d", "tucker", 1), ("3d", "tucker", 2), ("4d", "tt", 2),
+                                          ("4d", "htucker", 2), ("3d", "tt", 1)])
+def test_large_plane_compressed(native, cuda, K, L, nrhs, fmt, dec, prec):
+    F, torch = native, cuda
+    plan = pl.Plan(K=K, L=L)
+    ops = pl.operators(plan)
+    tol = 1e-4
+    comp = pl.compress(ops, fmt, dec, tol)
+    FMT = {"3d": 3, "4d": 4}[fmt]
+    DEC = {"tucker": 1, "tt": 2, "htucker": 3}[dec]
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, FMT, DEC, tol)
+    try:
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, prec)
+        P = comp.parts
+        cat = lambda xs: np.concatenate([np.ravel(x) for x in xs])
+        if fmt == "3d" and dec == "tucker":
+            F.fmmfft_import_tucker3d(h, np.array([t.ranks for t in P], dtype=np.int32), cat([t.core for t in P]),
+                                     *[cat([t.factors[i] for t in P]) for i in range(3)])
+        elif fmt == "3d":
+            F.fmmfft_import_tt3d(h, np.array([t.ranks for t in P], dtype=np.int32), cat([t.U1 for t in P]),
+                                 cat([t.cores[0] for t in P]), cat([t.Ud for t in P]))
+        elif dec == "tt":
+            F.fmmfft_import_tt4d(h, np.array(P.ranks, dtype=np.int32), P.U1, P.cores[0], P.cores[1], P.Ud)
+        else:
+            F.fmmfft_import_htucker(h, np.array(P.ranks, dtype=np.int32), *P.U, P.C12, P.C34, P.B)
+        S = field_spectra(93 + DEC, plan.n_dir, nrhs, K)
+        out = _run(F, torch, h, S, nrhs)
+        assert _rel(out, pl.translate_with(comp.restore, S)) <= 2e-6
+    finally:
+        F.fmmfft_plan_destroy(h)
