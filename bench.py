@@ -39,8 +39,24 @@ if ROOT not in sys.path:
 
 METRIC = "translation Gvoxel·dir/s, compressed vs plain on one GB300, at rel err ≤1e-4"
 UNIT = "Gvoxel·dir/s"
-WL = dict(name="tucker3d_32cube_L8_tol1e-4_2pol_4rhs", K=(32, 32, 32), L=8, a=0.5, k0=2 * math.pi,
-          tol=1e-4, nrhs=4, seed=1002)
+# Workloads (box edge 0.5 wavelength, k0 = 2 pi, seeded complex Gaussian fields).
+# fmt / dec: FMMFFT_FORMAT_* / FMMFFT_DECOMP_* of the compressed arm (0 / 0: the
+# workload has only the plain arm); c128: complex128 arithmetic.
+WORKLOADS = {
+    # the headline: Tucker-3D per direction, 3xTF32 restores
+    "tucker3d_32cube_L8_tol1e-4_2pol_4rhs": dict(K=(32, 32, 32), L=8, tol=1e-4, nrhs=4, seed=1002, fmt=3, dec=1),
+    "plain_c128_8cube_L5_2pol_1rhs": dict(K=(8, 8, 8), L=5, tol=0.0, nrhs=1, seed=1001, fmt=0, dec=0, c128=True),
+    "tt4d_64cube_L10_tol1e-3_2pol_1rhs": dict(K=(64, 64, 64), L=10, tol=1e-3, nrhs=1, seed=1003, fmt=4, dec=2),
+    "htucker4d_64cube_L10_tol1e-3_2pol_1rhs": dict(K=(64, 64, 64), L=10, tol=1e-3, nrhs=1, seed=1003, fmt=4, dec=3),
+    "tucker3d_128x128x32_L6_tol1e-4_2pol_16rhs": dict(K=(128, 128, 32), L=6, tol=1e-4, nrhs=16, seed=1005,
+                                                     fmt=3, dec=1),
+    "htucker4d_128x128x32_L6_tol1e-4_2pol_16rhs": dict(K=(128, 128, 32), L=6, tol=1e-4, nrhs=16, seed=1005,
+                                                      fmt=4, dec=3),
+}
+DEFAULT_WL = "tucker3d_32cube_L8_tol1e-4_2pol_4rhs"
+WL = dict(WORKLOADS[DEFAULT_WL], name=DEFAULT_WL, a=0.5, k0=2 * math.pi)
+FORMAT_NAMES = {(3, 1): "tucker3d", (3, 2): "tt3d", (4, 1): "tucker4d", (4, 2): "tt4d", (4, 3): "htucker4d",
+                (0, 0): "none"}
 CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
 # version of the yz kernel the committed DRAM-traffic figure was taken on
 YZ_KERNEL_VERSION = 2
@@ -233,27 +249,37 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # flop / byte models of one step (nominal 5 N log2 N flops per complex DFT)
 # ---------------------------------------------------------------------------
-def yz_flops(K, n, n_dir, nrhs, ranks=None):
+def yz_flops(K, n, n_dir, nrhs, slab_ranks=None):
+    """Nominal flops of one yz launch.  slab_ranks: per direction (ra, rb) of
+    the slab restore (Tucker-like: ra = r2, rb = r3; TT-like: ra = 0, rb = r2)."""
     Kx, Ky, Kz = K
     n1, n2, n3 = n
     lg2, lg3 = math.log2(n2), math.log2(n3)
     per_field_slab = 2 * Kz * 5 * n2 * lg2 + n2 * (2 * 5 * n3 * lg3 + 6 * n3)
     f = n1 * n_dir * 2 * nrhs * per_field_slab
-    if ranks is not None:
-        # slab restore per block: (n2 x r2)(r2 x r3) and (n3 x r3)(r3 x n2), 8 flops per complex MAC
-        f += n1 * sum(8 * (n2 * r2 * r3 + n3 * n2 * r3) for (_, r2, r3) in ranks)
+    if slab_ranks is not None:
+        # per block: (n2 x ra)(ra x rb) when ra > 0, then (n3 x rb)(rb x n2); 8 flops per complex MAC
+        f += n1 * sum(8 * (n2 * ra * rb + n3 * n2 * rb) for (ra, rb) in slab_ranks)
     return f
 
 
-def step_flops(K, n, n_dir, nrhs, ranks=None):
+def step_flops(K, n, n_dir, nrhs, slab_ranks=None):
     Kx, Ky, Kz = K
     n1, n2, n3 = n
     F = n_dir * 2 * nrhs
     x = F * 2 * Ky * Kz * 5 * n1 * math.log2(n1)
-    f = x + yz_flops(K, n, n_dir, nrhs, ranks)
-    if ranks is not None:
-        f += sum(8 * n1 * r1 * r2 * r3 for (r1, r2, r3) in ranks)
-    return f
+    return x + yz_flops(K, n, n_dir, nrhs, slab_ranks)
+
+
+def slab_ranks_of(F, h, fmt, dec, n_dir):
+    st = F.fmmfft_plan_stats(h)
+    r = st["max_rank"]
+    if fmt == 3:
+        pr = F.fmmfft_plan_ranks(h)
+        return [(int(a[1]), int(a[2])) if dec == 1 else (0, int(a[1])) for a in pr]
+    if dec == 2:
+        return [(0, int(r[1]))] * n_dir
+    return [(int(r[1]), int(r[2]))] * n_dir
 
 
 def main():
@@ -268,6 +294,9 @@ def main():
     ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "fp32"],
                     help="restore arithmetic of the compressed arm: tensor cores (3xTF32) or FP32 CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=DEFAULT_WL, choices=sorted(WORKLOADS),
+                    help="workload (default: the headline Tucker-3D one); others print their own line "
+                         "without CPU baseline and end-to-end arms")
     ap.add_argument("--cpu-baseline-child", type=int, default=0)
     ap.add_argument("--reference-child", type=int, nargs=2, default=None)
     args = ap.parse_args()
@@ -300,25 +329,54 @@ def main():
         from paper_2010_00520_gb300 import build as _b
         _b.build()
 
-    K, L, nrhs = WL["K"], WL["L"], (args.nrhs or WL["nrhs"])
+    wl_name = args.workload
+    W = dict(WORKLOADS[wl_name], a=0.5, k0=2 * math.pi)
+    if wl_name != DEFAULT_WL:
+        args.no_e2e = True
+        args.no_cpu_baseline = True
+    K, L, nrhs = W["K"], W["L"], (args.nrhs or W["nrhs"])
+    c128 = W.get("c128", False)
+    fmt_c, dec_c = W["fmt"], W["dec"]
     plans = {}
-    arms = [a for a in (("compressed", 3, 1, WL["tol"]), ("plain", 0, 0, 0.0))
-            if args.only in ("both", a[0])]
+    arms = [("plain", 0, 0, 0.0)]
+    if fmt_c:
+        arms.insert(0, ("compressed", fmt_c, dec_c, W["tol"]))
+    arms = [a for a in arms if args.only in ("both", a[0])]
+    t_setup = {}
     for name, fmt, dec, tol in arms:
-        h = F.fmmfft_plan_create(K[0], K[1], K[2], WL["a"], WL["k0"], L, fmt, dec, tol)
-        prec = F.FMMFFT_PREC_C64_3XTF32 if (name == "compressed" and args.restore == "3xtf32") else F.FMMFFT_PREC_C64
+        h = F.fmmfft_plan_create(K[0], K[1], K[2], W["a"], W["k0"], L, fmt, dec, tol)
+        if c128:
+            prec = F.FMMFFT_PREC_C128
+        elif name == "compressed" and args.restore == "3xtf32":
+            prec = F.FMMFFT_PREC_C64_3XTF32
+        else:
+            prec = F.FMMFFT_PREC_C64
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, prec)
+        t0 = time.perf_counter()
         F.fmmfft_compress(h)
+        t_setup[name] = time.perf_counter() - t0
         plans[name] = h
     main_arm = "compressed" if "compressed" in plans else "plain"
     st = F.fmmfft_plan_stats(plans[main_arm])
     n, n_dir = tuple(st["n"]), st["n_dir"]
-    ranks = ([tuple(int(v) for v in r) for r in F.fmmfft_plan_ranks(plans["compressed"])]
-             if "compressed" in plans else None)
-    S_host = field_spectra(WL["seed"], n_dir, nrhs, K).astype(np.complex64)
-    x = torch.from_numpy(S_host).to("cuda")
-    y = torch.empty_like(x)
+    sranks = slab_ranks_of(F, plans["compressed"], fmt_c, dec_c, n_dir) if "compressed" in plans else None
+    cdt = np.complex128 if c128 else np.complex64
+    tdt = torch.complex128 if c128 else torch.complex64
     stream = torch.cuda.current_stream()
+    S_host = None
+    if wl_name == DEFAULT_WL:
+        S_host = field_spectra(W["seed"], n_dir, nrhs, K).astype(cdt)
+        x = torch.from_numpy(S_host).to("cuda")
+    else:
+        # generated one direction at a time straight into device memory
+        from seeded_inputs import field_spectra_rows
+        x = torch.empty((n_dir, 2, nrhs, K[2], K[1], K[0]), dtype=tdt, device="cuda")
+        nf = 2 * nrhs
+        for p in range(n_dir):
+            rows = field_spectra_rows(W["seed"], n_dir, nrhs, K, np.arange(p * nf, (p + 1) * nf))
+            x[p] = torch.from_numpy(rows.astype(cdt).reshape(2, nrhs, K[2], K[1], K[0])).to("cuda")
+    y = torch.empty_like(x)
+    io_bytes = x.numel() * x.element_size()
 
     def barrier():
         if dist is not None:
@@ -367,7 +425,6 @@ def main():
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PROFILE, 0)
         stage[name] = {k: v / nst for k, v in zip(("restore", "xfwd", "yz", "xinv"), acc)}
 
-    io_bytes = S_host.nbytes
     e2e = None
     if not args.no_e2e:
         # end to end through the host-buffer entry point (pinned memory)
@@ -392,7 +449,7 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s, FMA = 2 flops
     yz_ms = stage[main_arm]["yz"]
-    yz_fl = yz_flops(K, n, n_dir, nrhs, ranks)
+    yz_fl = yz_flops(K, n, n_dir, nrhs, sranks)
     achieved = yz_fl / (yz_ms * 1e-3) / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "yz_kernel_tucker3d_32cube_L8.traffic.json")
@@ -400,20 +457,26 @@ def main():
         with open(prof) as f:
             tj = json.load(f)
         # counters only count for the kernel they were taken on
-        if tj.get("kernel_version") == YZ_KERNEL_VERSION and nrhs == WL["nrhs"] and args.restore == "3xtf32":
+        if (tj.get("kernel_version") == YZ_KERNEL_VERSION and wl_name == DEFAULT_WL and nrhs == W["nrhs"]
+                and args.restore == "3xtf32"):
             traffic = tj.get("dram_bytes_per_launch")
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
         "metric": METRIC, "value": value[main_arm], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms[main_arm], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
-        "config": {"workload": WL["name"] if nrhs == WL["nrhs"] else WL["name"].replace("4rhs", f"{nrhs}rhs"),
+        "vs_baseline": None, "dtype": "c128 (fp64)" if c128 else "c64 (fp32)", "data": "synthetic",
+        "config": {"workload": wl_name if nrhs == W["nrhs"] else wl_name.replace(f"{W['nrhs']}rhs", f"{nrhs}rhs"),
                    "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
-                   "nrhs": nrhs, "fields": n_dir * 2 * nrhs, "format": "tucker3d" if main_arm == "compressed" else "none",
-                   "tol": WL["tol"],
-                   "precision": ("FP32 FFTs, 3xTF32 restores on the tensor cores (tcgen05, FP32 accumulate)"
+                   "nrhs": nrhs, "fields": n_dir * 2 * nrhs,
+                   "format": FORMAT_NAMES[(fmt_c, dec_c)] if main_arm == "compressed" else "none",
+                   "tol": W["tol"],
+                   "precision": ("FP64 FFTs" if c128 else
+                                 "FP32 FFTs, 3xTF32 restores on the tensor cores (tcgen05, FP32 accumulate)"
                                  if st.get("restore_on_tensor_cores") else "FP32 FFTs and FP32 restores"),
-                   "l2": "inputs and outputs each larger than the 129 MB L2; no flush"},
+                   "large_planes": bool(st.get("large_planes")),
+                   "setup_s": {k: round(v, 2) for k, v in t_setup.items()},
+                   "l2": ("inputs and outputs each larger than the 129 MB L2; no flush" if io_bytes > 129e6 else
+                          "inputs smaller than L2 (parity-sized workload); no flush")},
         "stages_ms": stage,
         "roofline": {"kernel": "yz_kernel (slab restore + y/z FFTs + Hadamard)",
                      "bound": "alu",
@@ -425,16 +488,16 @@ def main():
                 "achieved_gbs": step_bytes / (ms[main_arm] * 1e-3) / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"),
                 "frac": step_bytes / (ms[main_arm] * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
-        "step_tflops_nominal": step_flops(K, n, n_dir, nrhs, ranks) / (ms[main_arm] * 1e-3) / 1e12,
+        "step_tflops_nominal": step_flops(K, n, n_dir, nrhs, sranks) / (ms[main_arm] * 1e-3) / 1e12,
         "clocks": clk,
-        "gpu_launches": (4 if main_arm == "compressed" else 3) * args.steps,
+        "gpu_launches": int(st["kernel_launches"]) * args.steps,
     }
     if "plain" in plans and "compressed" in plans:
         out["plain"] = {"value": value["plain"], "ms_per_step": ms["plain"]}
         out["ratio_compressed_over_plain_time"] = ms["compressed"] / ms["plain"]
         out["memory"] = {"operator_bytes_compressed": st["device_bytes_operator"],
                          "operator_bytes_plain": F.fmmfft_plan_stats(plans["plain"])["device_bytes_operator"],
-                         "saving": st["saving"], "max_rank": st["max_rank"][:3],
+                         "saving": st["saving"], "max_rank": [int(v) for v in st["max_rank"] if v],
                          "mean_rank": [round(v, 2) for v in st["mean_rank"]]}
     if e2e is not None:
         out["e2e"] = e2e

@@ -87,8 +87,8 @@ enum {
   FMMFFT_PREC_C64_3XTF32 = 2,    /* FP32 fields and FFTs, restores on the tensor
                                     cores as three TF32 products (big x big,
                                     big x small, small x big), FP32 accumulate;
-                                    planes other than n2 = n3 = 64 restore on
-                                    the CUDA cores in FP32 instead           */
+                                    y-z planes whose sides are not multiples of
+                                    64 restore on the CUDA cores in FP32     */
   FMMFFT_PREC_C64_BF16X3 = 3     /* as above with bf16 hi/lo splits         */
 };
 
@@ -134,8 +134,13 @@ typedef struct fmmfft_stats {
   int64_t device_bytes_scratch;  /* device bytes of scratch buffers currently held */
   double setup_seconds;          /* wall time of the last fmmfft_compress    */
   int restore_on_tensor_cores;   /* 1 when the slab restores run on the tensor
-                                    cores (FMMFFT_PREC_C64_3XTF32, 64 x 64 y-z
-                                    planes); 0 otherwise (CUDA cores)        */
+                                    cores (FMMFFT_PREC_C64_3XTF32, y-z planes
+                                    with n2, n3 multiples of 64); 0 otherwise
+                                    (CUDA cores)                             */
+  int kernel_launches;           /* kernels one fmmfft_translate launches    */
+  int large_planes;              /* 1 when the y-z pass keeps restored slabs
+                                    in global scratch (planes too large for
+                                    shared memory)                           */
 } fmmfft_stats;
 
 /*

@@ -70,7 +70,8 @@ class _Stats(ctypes.Structure):
         ("elements_plain", ctypes.c_int64), ("elements_compressed", ctypes.c_int64),
         ("saving", ctypes.c_double), ("device_bytes_operator", ctypes.c_int64),
         ("device_bytes_scratch", ctypes.c_int64), ("setup_seconds", ctypes.c_double),
-        ("restore_on_tensor_cores", ctypes.c_int),
+        ("restore_on_tensor_cores", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+        ("large_planes", ctypes.c_int),
     ]
 
 

@@ -829,7 +829,12 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   o->device_bytes_operator = p->bytes_operator;
   o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes + p->slabs_bytes) + p->bytes_restore;
   o->setup_seconds = p->setup_seconds;
-  o->restore_on_tensor_cores = p->ready ? base_args(p).tc : 0;
+  if (p->ready) {
+    const fmm::TranslateArgs a = base_args(p);
+    o->restore_on_tensor_cores = a.tc;
+    o->kernel_launches = a.n_stages + 3;
+    o->large_planes = a.large;
+  }
   return FMMFFT_OK;
 }
 

@@ -12,8 +12,10 @@ namespace fmm {
 
 // Implicit-shift QL iterations on the real symmetric tridiagonal matrix with
 // diagonal d[0..n) and off-diagonal e[i] = T[i+1][i] (e[n-1] unused); the
-// rotations are accumulated into the columns of Z (row-major n x n).
-static void tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
+// rotations are accumulated into the eigenvector matrix, stored transposed
+// (Zt[j] is eigenvector j, contiguous) so that a rotation of two vectors
+// touches two contiguous rows.
+static void tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Zt) {
   const double eps = 2.220446049250313e-16;
   e.resize(n);
   e[n - 1] = 0.0;
@@ -49,11 +51,12 @@ static void tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, st
         p = s * r;
         d[i + 1] = g + p;
         g = c * r - b;
+        double* za = &Zt[(size_t)i * n];
+        double* zb = &Zt[(size_t)(i + 1) * n];
         for (int k = 0; k < n; ++k) {
-          double* zr = &Z[(size_t)k * n];
-          const double zi1 = zr[i + 1], zi = zr[i];
-          zr[i + 1] = s * zi + c * zi1;
-          zr[i] = c * zi - s * zi1;
+          const double zi = za[k], zi1 = zb[k];
+          zb[k] = s * zi + c * zi1;
+          za[k] = c * zi - s * zi1;
         }
       }
       if (underflow) continue;
@@ -122,15 +125,15 @@ void hermitian_eig_tridiag(int n, std::vector<cdouble>& A, std::vector<double>& 
     e[k] = a;
     ph[k + 1] = a > 0.0 ? ph[k] * (ek / a) : ph[k];
   }
-  std::vector<double> Z((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
-  tridiag_ql(n, d, e, Z);
+  std::vector<double> Zt((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Zt[(size_t)i * n + i] = 1.0;
+  tridiag_ql(n, d, e, Zt);
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int i, int j) { return d[i] > d[j]; });
   lam.assign(n, 0.0);
   for (int c = 0; c < n; ++c) lam[c] = d[idx[c]];
-  // V = Q D Z (columns reordered)
+  // V = Q D Z (columns reordered); Z[j][col] = Zt[col][j]
   V.assign((size_t)n * n, cdouble(0.0, 0.0));
   parallel_for(n, [&](int r) {
     const cdouble* q = &Q[(size_t)r * n];
@@ -138,9 +141,9 @@ void hermitian_eig_tridiag(int n, std::vector<cdouble>& A, std::vector<double>& 
     std::vector<cdouble> qd(n);
     for (int j = 0; j < n; ++j) qd[j] = q[j] * ph[j];
     for (int c = 0; c < n; ++c) {
-      const int col = idx[c];
+      const double* z = &Zt[(size_t)idx[c] * n];
       cdouble acc(0.0, 0.0);
-      for (int j = 0; j < n; ++j) acc += qd[j] * Z[(size_t)j * n + col];
+      for (int j = 0; j < n; ++j) acc += qd[j] * z[j];
       out[c] = acc;
     }
   });
@@ -185,11 +188,14 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
   } else {
     // G = A^H A (N x N): G[i][j] = sum_row conj(A[row][i]) A[row][j]
     std::vector<cdouble> G((size_t)N * N, cdouble(0.0, 0.0));
+    // row i of G accumulates conj(A[row][i]) A[row][j>=i] over the rows of A,
+    // each read contiguously
     parallel_for((int)N, [&](int i) {
-      for (int64_t j = i; j < N; ++j) {
-        cdouble acc(0.0, 0.0);
-        for (int64_t row = 0; row < m; ++row) acc += std::conj(A[(size_t)row * N + i]) * A[(size_t)row * N + j];
-        G[(size_t)i * N + j] = acc;
+      cdouble* g = &G[(size_t)i * N];
+      for (int64_t row = 0; row < m; ++row) {
+        const cdouble* a = A + (size_t)row * N;
+        const cdouble ci = std::conj(a[i]);
+        for (int64_t j = i; j < N; ++j) g[j] += ci * a[j];
       }
     });
     for (int64_t i = 0; i < N; ++i)
@@ -205,11 +211,13 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
     for (int c = 0; c < r; ++c) isig[c] = lam[c] > 0.0 ? 1.0 / std::sqrt(lam[c]) : 0.0;
     parallel_for((int)m, [&](int row) {
       const cdouble* a = A + (size_t)row * N;
-      for (int c = 0; c < r; ++c) {
-        cdouble acc(0.0, 0.0);
-        for (int64_t k = 0; k < N; ++k) acc += a[k] * V[(size_t)k * N + c];
-        U[(size_t)row * r + c] = acc * isig[c];
+      cdouble* u = &U[(size_t)row * r];
+      for (int64_t k = 0; k < N; ++k) {
+        const cdouble ak = a[k];
+        const cdouble* v = &V[(size_t)k * N];
+        for (int c = 0; c < r; ++c) u[c] += ak * v[c];
       }
+      for (int c = 0; c < r; ++c) u[c] *= isig[c];
     });
   }
   // Q = U^H A (r x N)
