@@ -186,8 +186,10 @@ __device__ __forceinline__ void tc_teardown(const TcState& s) {
 
 // C[m * ldc + n] = scale * sum_k A(m, k) B(k, n) for m < M, n < N (M, N <= 64)
 // with A(m, k), B(k, n) complex (float2) supplied by the functors.  Every
-// thread of the 256-thread block calls it; C is in shared memory.
-template <typename FA, typename FB>
+// thread of the 256-thread block calls it.  C_GLOBAL: C is in global memory,
+// so the epilogue combines the quadrants in shared memory and writes C once,
+// coalesced; otherwise C (shared memory) is written directly, one row per lane.
+template <bool C_GLOBAL, typename FA, typename FB>
 __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a_of, FB b_of, float2* C,
                                            int ldc, float scale) {
   const int tid = threadIdx.x;
@@ -259,48 +261,92 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
     tc_fence_after();
   }
   // epilogue: lanes m (warps 0, 1 and 4, 5) hold the ReA rows, lanes 64 + m
-  // (warps 2, 3 and 6, 7) the ImA rows; warps w and w + 4 split the columns
+  // (warps 2, 3 and 6, 7) the ImA rows; warps w and w + 4 split the columns.
   const int w = tid >> 5, q = w & 3, half = w >> 2;
   const int row = q * 32 + (tid & 31);
   const uint32_t lane_addr = s.tmem + ((uint32_t)(q * 32) << 16);
   float v[16];
-  if (q < 2) {
-    const int m = row;
+  if constexpr (C_GLOBAL) {
+    // combine in the (now idle) operand buffer, a 64 x 64 complex tile with
+    // columns XOR-swizzled by the row, then copy to C with consecutive
+    // threads on consecutive columns
+    float2* T = reinterpret_cast<float2*>(s.buf);
+    if (q < 2) {
+      const int m = row;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      tmem_ld16(lane_addr + half * 64 + c * 16, v);
-      if (m < M) {
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(lane_addr + half * 64 + c * 16, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int n = c * 16 + j;
-          if (n < N) {
-            if (half == 0) C[m * ldc + n].x = v[j];   // ReA ReB
-            else C[m * ldc + n].y = v[j];              // ReA ImB
+          float2* t = &T[m * 64 + ((c * 16 + j) ^ (m & 31))];
+          if (half == 0) t->x = v[j];      // ReA ReB
+          else t->y = v[j];                // ReA ImB
+        }
+      }
+    }
+    __syncthreads();
+    if (q >= 2) {
+      const int m = row - 64;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(lane_addr + half * 64 + c * 16, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float2* t = &T[m * 64 + ((c * 16 + j) ^ (m & 31))];
+          if (half == 0) t->y += v[j];     // + ImA ReB
+          else t->x -= v[j];               // - ImA ImB
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    for (int i = tid; i < M * 64; i += 256) {
+      const int m = i >> 6, n = i & 63;
+      if (n < N) {
+        const float2 t = T[m * 64 + (n ^ (m & 31))];
+        C[m * ldc + n] = make_float2(t.x * scale, t.y * scale);
+      }
+    }
+    __syncthreads();
+  } else {
+    if (q < 2) {
+      const int m = row;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(lane_addr + half * 64 + c * 16, v);
+        if (m < M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = c * 16 + j;
+            if (n < N) {
+              if (half == 0) C[m * ldc + n].x = v[j];   // ReA ReB
+              else C[m * ldc + n].y = v[j];              // ReA ImB
+            }
           }
         }
       }
     }
-  }
-  __syncthreads();
-  if (q >= 2) {
-    const int m = row - 64;
+    __syncthreads();
+    if (q >= 2) {
+      const int m = row - 64;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      tmem_ld16(lane_addr + half * 64 + c * 16, v);
-      if (m < M) {
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(lane_addr + half * 64 + c * 16, v);
+        if (m < M) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c * 16 + j;
-          if (n < N) {
-            if (half == 0) C[m * ldc + n].y = (C[m * ldc + n].y + v[j]) * scale;   // + ImA ReB
-            else C[m * ldc + n].x = (C[m * ldc + n].x - v[j]) * scale;             // - ImA ImB
+          for (int j = 0; j < 16; ++j) {
+            const int n = c * 16 + j;
+            if (n < N) {
+              if (half == 0) C[m * ldc + n].y = (C[m * ldc + n].y + v[j]) * scale;   // + ImA ReB
+              else C[m * ldc + n].x = (C[m * ldc + n].x - v[j]) * scale;             // - ImA ImB
+            }
           }
         }
       }
     }
+    tc_fence_before();
+    __syncthreads();
   }
-  tc_fence_before();
-  __syncthreads();
 }
 
 }  // namespace fmm

@@ -349,15 +349,15 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
         const float2* U2 = reinterpret_cast<const float2*>(d.u2);
         // G[c][y] = sum_b H_p[x][b][c] U2[y][b]; odd pitch PY: the epilogue
         // writes one row per lane
-        tc_cgemm64(tc, rb, N2, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+        tc_cgemm64<false>(tc, rb, N2, ra, [&](int c, int b) { return Hf[b * rb + c]; },
                    [&](int b, int y) { return U2[y * ra + b]; }, G, PY, 1.0f);
         // slab[z][y] = scale sum_c U3[z][c] G[c][y]
-        tc_cgemm64(tc, N3, N2, rb, [&](int z, int c) { return U3[z * rb + c]; },
+        tc_cgemm64<false>(tc, N3, N2, rb, [&](int z, int c) { return U3[z * rb + c]; },
                    [&](int c, int y) { return G[c * PY + y]; }, reinterpret_cast<float2*>(Tt), PY,
                    (float)P.scale);
       } else {
         // slab[z][y] = scale sum_b R_p[z][b] T1[x][y][b]
-        tc_cgemm64(tc, N3, N2, rb, [&](int z, int b) { return U3[z * rb + b]; },
+        tc_cgemm64<false>(tc, N3, N2, rb, [&](int z, int b) { return U3[z * rb + b]; },
                    [&](int b, int y) { return Hf[y * rb + b]; }, reinterpret_cast<float2*>(Tt), PY,
                    (float)P.scale);
       }
@@ -470,17 +470,17 @@ __global__ void __launch_bounds__(kThreads, 1) yzl_kernel(YZParams P) {
         float2* Sf = reinterpret_cast<float2*>(slot);
         if constexpr (FMT == 1) {
           for (int y0 = 0; y0 < N2; y0 += 64)
-            tc_cgemm64(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+            tc_cgemm64<true>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
                        [&](int b, int y) { return U2f[(y0 + y) * ra + b]; }, Gf + y0, N2, 1.0f);
           for (int z0 = 0; z0 < N3; z0 += 64)
             for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
+              tc_cgemm64<true>(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
                          [&](int c, int y) { return Gf[c * N2 + y0 + y]; }, Sf + (size_t)z0 * N2 + y0, N2,
                          (float)P.scale);
         } else {
           for (int z0 = 0; z0 < N3; z0 += 64)
             for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
+              tc_cgemm64<true>(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
                          [&](int b, int y) { return Hf[(y0 + y) * rb + b]; }, Sf + (size_t)z0 * N2 + y0, N2,
                          (float)P.scale);
         }
