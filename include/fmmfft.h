@@ -52,6 +52,7 @@ extern "C" {
 #endif
 
 typedef struct fmmfft_plan_s* fmmfft_plan;
+typedef struct fmmfft_batch_s* fmmfft_batch;
 
 /* ---- status codes ------------------------------------------------------ */
 enum {
@@ -314,6 +315,32 @@ int fmmfft_compress_direction_host(fmmfft_plan plan, int p, int* ranks_out, doub
  * ((p * n1 + x) * n2 + y) * n3 + z.  INVALID_ARG for format NONE.
  */
 int fmmfft_compress_host(fmmfft_plan plan, int* ranks_out, double* restored_out);
+
+/*
+ * Batches of independent translations (many FMM-FFT instances with uneven
+ * grids, ranks and RHS counts, Sec. II.C restores per instance).
+ *
+ * fmmfft_batch_create: a batch over nplans >= 1 existing plans (not copied;
+ * they must outlive the batch and be compressed before the first translate).
+ * fmmfft_batch_translate: translates instance i from S_in[i] to S_out[i]
+ * with nrhs[i] RHS (device pointers and layouts as fmmfft_translate), all
+ * asynchronous on `stream`: the instances are forked over up to four internal
+ * streams so that small ones run side by side, and joined back into `stream`.
+ * A call with the same pointers and RHS counts as the previous call is
+ * captured as one CUDA graph on its first repetition and replayed from then
+ * on (never for the legacy default stream, NULL).  Each plan's intermediate
+ * is allocated, if needed, before anything is launched.
+ * Errors: those of fmmfft_translate for any instance (nothing of that call is
+ * launched when an argument is invalid), CUDA.  A batch is not thread-safe,
+ * and its plans must not be translated on their own while a batch call of
+ * theirs may still run.
+ * fmmfft_batch_destroy: waits for the batch's streams, frees its resources
+ * (not the plans).
+ */
+int fmmfft_batch_create(fmmfft_batch* out, const fmmfft_plan* plans, int nplans);
+int fmmfft_batch_translate(fmmfft_batch batch, const void* const* S_in, void* const* S_out,
+                           const int* nrhs, void* stream);
+int fmmfft_batch_destroy(fmmfft_batch batch);
 
 /* Fill *out (see fmmfft_stats). */
 int fmmfft_plan_stats(fmmfft_plan plan, fmmfft_stats* out);

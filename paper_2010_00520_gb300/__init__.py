@@ -53,6 +53,7 @@ EXPORTED = (
     "fmmfft_operator_host", "fmmfft_compress_direction_host", "fmmfft_stage_times",
     "fmmfft_plan_ranks", "fmmfft_translate_noalloc", "fmmfft_import_tt3d", "fmmfft_import_tucker4d",
     "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
+    "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy",
 )
 
 
@@ -99,6 +100,9 @@ def lib() -> ctypes.CDLL:
         "fmmfft_import_htucker": [vp, ip, dp, dp, dp, dp, dp, dp, dp],
         "fmmfft_import_tt4d": [vp, ip, dp, dp, dp, dp],
         "fmmfft_compress_host": [vp, ip, dp],
+        "fmmfft_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i],
+        "fmmfft_batch_translate": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp],
+        "fmmfft_batch_destroy": [vp],
         "fmmfft_translate": [vp, vp, vp, i, vp],
         "fmmfft_translate_host": [vp, vp, vp, i, vp],
         "fmmfft_translate_noalloc": [vp, vp, vp, i, vp],
@@ -232,6 +236,25 @@ def fmmfft_compress_host(plan, restored=True):
     _check(lib().fmmfft_compress_host(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                       _dptr(out) if restored else None), "fmmfft_compress_host")
     return (r.reshape(nd, 3) if is3d else r), out
+
+
+def fmmfft_batch_create(plans) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = ctypes.c_void_p()
+    _check(lib().fmmfft_batch_create(ctypes.byref(h), arr, len(plans)), "fmmfft_batch_create")
+    return h.value
+
+
+def fmmfft_batch_translate(batch, S_in, S_out, nrhs, stream=None):
+    n = len(S_in)
+    ins = (ctypes.c_void_p * n)(*[_ptr(x) for x in S_in])
+    outs = (ctypes.c_void_p * n)(*[_ptr(x) for x in S_out])
+    r, rp = _ints(nrhs)
+    _check(lib().fmmfft_batch_translate(batch, ins, outs, rp, _stream(stream)), "fmmfft_batch_translate")
+
+
+def fmmfft_batch_destroy(batch):
+    _check(lib().fmmfft_batch_destroy(batch), "fmmfft_batch_destroy")
 
 
 def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):

@@ -1,0 +1,152 @@
+// Batched translation of several independent plans (uneven grids, ranks and
+// RHS counts): one call launches every instance, forked over a few streams so
+// that small instances run side by side, and repeated calls with the same
+// buffers replay one captured CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fmmfft.h"
+#include "plan_internal.h"
+
+struct fmmfft_batch_s {
+  std::vector<fmmfft_plan> plans;
+  std::vector<cudaStream_t> side;       // fork streams
+  std::vector<cudaEvent_t> joined;      // one per side stream
+  cudaEvent_t forked = nullptr;
+  // the last call's arguments and, once they repeat, its captured graph
+  std::vector<const void*> key_in;
+  std::vector<void*> key_out;
+  std::vector<int> key_nrhs;
+  int key_seen = 0;                     // consecutive calls with this key
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int kSideStreams = 4;
+
+void drop_graph(fmmfft_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Fork from `stream`, launch every instance on a side stream, join back.
+int launch_all(fmmfft_batch_s* b, const void* const* in, void* const* out, const int* nrhs,
+               const std::vector<void*>& inter, const std::vector<size_t>& cap, cudaStream_t stream) {
+  if (cudaEventRecord(b->forked, stream) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  for (auto s : b->side)
+    if (cudaStreamWaitEvent(s, b->forked, 0) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const int st = fmm::translate_into(b->plans[i], in[i], out[i], nrhs[i], b->side[i % b->side.size()],
+                                       inter[i], cap[i]);
+    if (st != FMMFFT_OK) return st;
+  }
+  for (size_t k = 0; k < b->side.size(); ++k) {
+    if (cudaEventRecord(b->joined[k], b->side[k]) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    if (cudaStreamWaitEvent(stream, b->joined[k], 0) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmmfft_batch_create(fmmfft_batch* out, const fmmfft_plan* plans, int nplans) {
+  if (!out || !plans || nplans < 1) return FMMFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < nplans; ++i)
+    if (!plans[i]) return FMMFFT_ERR_INVALID_ARG;
+  fmmfft_batch_s* b = new (std::nothrow) fmmfft_batch_s();
+  if (!b) return FMMFFT_ERR_OOM;
+  b->plans.assign(plans, plans + nplans);
+  const int ns = nplans < kSideStreams ? nplans : kSideStreams;
+  b->side.assign(ns, nullptr);
+  b->joined.assign(ns, nullptr);
+  bool ok = cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < ns; ++k)
+    ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->joined[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    fmmfft_batch_destroy(b);
+    return FMMFFT_ERR_CUDA;
+  }
+  *out = b;
+  return FMMFFT_OK;
+}
+
+int fmmfft_batch_translate(fmmfft_batch b, const void* const* S_in, void* const* S_out, const int* nrhs,
+                           void* stream) {
+  if (!b || !S_in || !S_out || !nrhs) return FMMFFT_ERR_INVALID_ARG;
+  const size_t n = b->plans.size();
+  cudaStream_t s = (cudaStream_t)stream;
+  // every instance's intermediate exists before anything is launched or
+  // captured (an allocation would synchronise)
+  std::vector<void*> inter(n);
+  std::vector<size_t> cap(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (!S_in[i] || !S_out[i]) return FMMFFT_ERR_INVALID_ARG;
+    const int st = fmm::plan_intermediate(b->plans[i], nrhs[i], stream, &inter[i], &cap[i]);
+    if (st != FMMFFT_OK) return st;
+  }
+  const bool same = b->key_in.size() == n &&
+                    std::equal(b->key_in.begin(), b->key_in.end(), S_in) &&
+                    std::equal(b->key_out.begin(), b->key_out.end(), S_out) &&
+                    std::equal(b->key_nrhs.begin(), b->key_nrhs.end(), nrhs);
+  int st = FMMFFT_OK;
+  if (same && b->exec) {
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) st = FMMFFT_ERR_CUDA;
+  } else if (same && b->key_seen >= 1 && s != nullptr) {
+    // second call with the same arguments: capture once, replay from now on
+    drop_graph(b);
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return FMMFFT_ERR_CUDA;
+    }
+    st = launch_all(b, S_in, S_out, nrhs, inter, cap, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st == FMMFFT_OK && (e != cudaSuccess || !g)) st = FMMFFT_ERR_CUDA;
+    if (st == FMMFFT_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = FMMFFT_ERR_CUDA;
+    b->graph = g;
+    if (st == FMMFFT_OK && cudaGraphLaunch(b->exec, s) != cudaSuccess) st = FMMFFT_ERR_CUDA;
+    if (st != FMMFFT_OK) {
+      cudaGetLastError();
+      drop_graph(b);
+    }
+  } else {
+    st = launch_all(b, S_in, S_out, nrhs, inter, cap, s);
+  }
+  if (!same) {
+    drop_graph(b);
+    b->key_in.assign(S_in, S_in + n);
+    b->key_out.assign(S_out, S_out + n);
+    b->key_nrhs.assign(nrhs, nrhs + n);
+    b->key_seen = 0;
+  }
+  b->key_seen += 1;
+  for (auto p : b->plans) fmm::plan_set_last_stream(p, stream);
+  return st;
+}
+
+int fmmfft_batch_destroy(fmmfft_batch b) {
+  if (!b) return FMMFFT_ERR_INVALID_ARG;
+  for (auto s : b->side)
+    if (s) cudaStreamSynchronize(s);
+  drop_graph(b);
+  for (auto s : b->side)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : b->joined)
+    if (e) cudaEventDestroy(e);
+  if (b->forked) cudaEventDestroy(b->forked);
+  delete b;
+  return FMMFFT_OK;
+}
+
+}  // extern "C"

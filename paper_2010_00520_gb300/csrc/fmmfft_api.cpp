@@ -712,6 +712,28 @@ int translate_scratch_bytes(fmmfft_plan p, int nrhs, size_t* bytes) {
   return FMMFFT_OK;
 }
 
+int plan_intermediate(fmmfft_plan p, int nrhs, void* stream, void** inter, size_t* bytes) {
+  size_t need = 0;
+  int st = translate_scratch_bytes(p, nrhs, &need);
+  if (st != FMMFFT_OK) return st;
+  if (need > p->inter_bytes) {
+    if (p->d_inter) {
+      cudaStreamSynchronize((cudaStream_t)stream);
+      free_dev(p->d_inter);
+    }
+    p->inter_bytes = 0;
+    if ((st = dev_alloc(&p->d_inter, need)) != FMMFFT_OK) return st;
+    p->inter_bytes = need;
+  }
+  *inter = p->d_inter;
+  *bytes = p->inter_bytes;
+  return FMMFFT_OK;
+}
+
+void plan_set_last_stream(fmmfft_plan p, void* stream) {
+  if (p) p->last_stream = (cudaStream_t)stream;
+}
+
 int translate_into(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* stream,
                    void* scratch, size_t scratch_bytes) {
   size_t need = 0;

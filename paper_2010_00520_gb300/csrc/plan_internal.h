@@ -95,5 +95,10 @@ bool tc_restore_applies(const TranslateArgs& a);
 int translate_scratch_bytes(fmmfft_plan p, int nrhs, size_t* bytes);
 int translate_into(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* stream,
                    void* scratch, size_t scratch_bytes);
+// The plan's own intermediate for nrhs RHS, allocated (after synchronising
+// `stream`) when it is smaller; outputs its address and size.
+int plan_intermediate(fmmfft_plan p, int nrhs, void* stream, void** inter, size_t* bytes);
+// Stream that fmmfft_poll_status synchronises for this plan.
+void plan_set_last_stream(fmmfft_plan p, void* stream);
 
 }  // namespace fmm
