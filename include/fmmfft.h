@@ -364,6 +364,20 @@ int fmmfft_stage_times(fmmfft_plan plan, float* ms);
  * Synchronises the plan's last stream. */
 int fmmfft_poll_status(fmmfft_plan plan, int* device_status);
 
+/*
+ * Save a plan to a file and load it back (no counterpart in the paper: the
+ * FP64 set-up of the 4D formats takes minutes, a load seconds).  The file
+ * holds the plan's parameters and options and, for compressed plans, the
+ * stored factors (in FP64) with their restore schedule; plain plans are
+ * regenerated on load.  fmmfft_plan_save needs a compressed (ready) plan;
+ * fmmfft_plan_load creates a ready plan on the current device (*out, to be
+ * destroyed by the caller).  Errors: IO (file cannot be opened, read or
+ * written), INVALID_ARG (not a plan file of this version, or inconsistent
+ * contents), and those of fmmfft_compress on load.
+ */
+int fmmfft_plan_save(fmmfft_plan plan, const char* path);
+int fmmfft_plan_load(fmmfft_plan* out, const char* path);
+
 /* Release every resource of the plan (device memory included). */
 int fmmfft_plan_destroy(fmmfft_plan plan);
 

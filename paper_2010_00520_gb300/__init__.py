@@ -53,7 +53,8 @@ EXPORTED = (
     "fmmfft_operator_host", "fmmfft_compress_direction_host", "fmmfft_stage_times",
     "fmmfft_plan_ranks", "fmmfft_translate_noalloc", "fmmfft_import_tt3d", "fmmfft_import_tucker4d",
     "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
-    "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy",
+    "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy", "fmmfft_plan_save",
+    "fmmfft_plan_load",
 )
 
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "fmmfft_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i],
         "fmmfft_batch_translate": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp],
         "fmmfft_batch_destroy": [vp],
+        "fmmfft_plan_save": [vp, ctypes.c_char_p],
+        "fmmfft_plan_load": [ctypes.POINTER(vp), ctypes.c_char_p],
         "fmmfft_translate": [vp, vp, vp, i, vp],
         "fmmfft_translate_host": [vp, vp, vp, i, vp],
         "fmmfft_translate_noalloc": [vp, vp, vp, i, vp],
@@ -236,6 +239,16 @@ def fmmfft_compress_host(plan, restored=True):
     _check(lib().fmmfft_compress_host(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                       _dptr(out) if restored else None), "fmmfft_compress_host")
     return (r.reshape(nd, 3) if is3d else r), out
+
+
+def fmmfft_plan_save(plan, path):
+    _check(lib().fmmfft_plan_save(plan, os.fsencode(path)), "fmmfft_plan_save")
+
+
+def fmmfft_plan_load(path) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fmmfft_plan_load(ctypes.byref(h), os.fsencode(path)), "fmmfft_plan_load")
+    return h.value
 
 
 def fmmfft_batch_create(plans) -> int:

@@ -1,5 +1,6 @@
 // C ABI of the translation library: plan life cycle, set-up, translation.
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -55,6 +56,7 @@ struct fmmfft_plan_s {
   int64_t elements_plain = 0, elements_compressed = 0;
   int64_t bytes_operator = 0, bytes_restore = 0;
   double setup_seconds = 0;
+  fmm::Layout layout;           // host copy of the compressed store (plan save)
 };
 
 namespace {
@@ -358,6 +360,7 @@ void build_layout(const fmmfft_plan_s* p, fmm::Layout& L) {
 // Adopt a compressed layout: support check, upload, common buffers.
 int install_layout(fmmfft_plan_s* p, const fmm::Layout& L) {
   release_operator(p);
+  p->layout = L;
   adopt_layout_shape(p, L);
   if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   int st = query_large_grid(p);
@@ -889,6 +892,223 @@ int fmmfft_poll_status(fmmfft_plan p, int* device_status) {
   if (cudaMemcpy(device_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return FMMFFT_ERR_CUDA;
   if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  return FMMFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan files: header, options, and for compressed plans the stored factors
+// with their restore schedule (the FP64 set-up is not repeated on load)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+const char kMagic[8] = {'F', 'M', 'M', 'F', 'F', 'T', 'P', '1'};
+const uint32_t kFileVersion = 1;
+
+struct Writer {
+  FILE* f;
+  bool ok = true;
+  template <typename T> void put(const T& v) { ok = ok && fwrite(&v, sizeof(T), 1, f) == 1; }
+  template <typename T> void put_vec(const std::vector<T>& v) {
+    put<uint64_t>(v.size());
+    if (!v.empty()) ok = ok && fwrite(v.data(), sizeof(T), v.size(), f) == v.size();
+  }
+  void put_ref(const fmm::BufRef& r) { put<int32_t>(r.buf); put<int64_t>(r.off); }
+};
+
+struct Reader {
+  FILE* f;
+  bool ok = true;
+  template <typename T> T get() {
+    T v{};
+    ok = ok && fread(&v, sizeof(T), 1, f) == 1;
+    return v;
+  }
+  template <typename T> void get_vec(std::vector<T>& v, uint64_t limit) {
+    const uint64_t n = get<uint64_t>();
+    if (!ok || n > limit) { ok = false; return; }
+    v.resize(n);
+    if (n) ok = ok && fread(v.data(), sizeof(T), n, f) == n;
+  }
+  fmm::BufRef get_ref() {
+    fmm::BufRef r;
+    r.buf = get<int32_t>();
+    r.off = get<int64_t>();
+    if (r.buf != 0 && r.buf != 1) ok = false;
+    return r;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int fmmfft_plan_save(fmmfft_plan p, const char* path) {
+  if (!p || !path) return FMMFFT_ERR_INVALID_ARG;
+  if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return FMMFFT_ERR_IO;
+  Writer w{f};
+  if (fwrite(kMagic, 1, 8, f) != 8) w.ok = false;
+  w.put<uint32_t>(kFileVersion);
+  for (int i = 0; i < 3; ++i) w.put<int32_t>(p->K[i]);
+  w.put<int32_t>(p->L);
+  w.put<double>(p->a);
+  w.put<double>(p->k0);
+  w.put<double>(p->tol);
+  w.put<int32_t>(p->format);
+  w.put<int32_t>(p->decomp);
+  w.put<int32_t>(p->precision);
+  w.put<int32_t>(p->nphi_rule);
+  w.put<int32_t>(p->near_rule);
+  w.put<double>(p->kappa);
+  w.put<int32_t>(p->prefactor);
+  w.put<int32_t>(p->trunc_rule);
+  w.put<int32_t>(p->n_dir);
+  if (p->format != FMMFFT_FORMAT_NONE) {
+    const fmm::Layout& L = p->layout;
+    for (int i = 0; i < 3; ++i) w.put<int32_t>(L.n[i]);
+    w.put<int32_t>(L.n_dir);
+    w.put<int32_t>(L.yz_fmt);
+    w.put_vec(L.pack);
+    w.put<int64_t>(L.scratch);
+    w.put<uint64_t>(L.stages.size());
+    for (const auto& st : L.stages) {
+      w.put<uint64_t>(st.size());
+      for (const auto& g : st) {
+        w.put_ref(g.A);
+        w.put_ref(g.B);
+        w.put_ref(g.C);
+        w.put<int32_t>(g.M);
+        w.put<int32_t>(g.N);
+        w.put<int32_t>(g.K);
+      }
+    }
+    w.put<uint64_t>(L.slabs.size());
+    for (const auto& sl : L.slabs) {
+      w.put_ref(sl.h);
+      w.put_ref(sl.u2);
+      w.put_ref(sl.u3);
+      w.put<int64_t>(sl.hx);
+      w.put<int32_t>(sl.ra);
+      w.put<int32_t>(sl.rb);
+    }
+    w.put<int64_t>(L.elements);
+    for (int i = 0; i < 6; ++i) w.put<int32_t>(L.rank[i]);
+    for (int i = 0; i < 3; ++i) w.put<double>(L.mean_rank[i]);
+    w.put_vec(L.ranks3);
+  }
+  const bool closed = std::fclose(f) == 0;
+  return (w.ok && closed) ? FMMFFT_OK : FMMFFT_ERR_IO;
+}
+
+int fmmfft_plan_load(fmmfft_plan* out, const char* path) {
+  if (!out || !path) return FMMFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return FMMFFT_ERR_IO;
+  Reader r{f};
+  char magic[8] = {};
+  const bool got = fread(magic, 1, 8, f) == 8;
+  if (!got || std::memcmp(magic, kMagic, 8) != 0 || r.get<uint32_t>() != kFileVersion) {
+    std::fclose(f);
+    return got ? FMMFFT_ERR_INVALID_ARG : FMMFFT_ERR_IO;
+  }
+  int K[3];
+  for (int i = 0; i < 3; ++i) K[i] = r.get<int32_t>();
+  const int L = r.get<int32_t>();
+  const double a = r.get<double>(), k0 = r.get<double>(), tol = r.get<double>();
+  const int format = r.get<int32_t>(), decomp = r.get<int32_t>(), precision = r.get<int32_t>();
+  const int nphi_rule = r.get<int32_t>(), near_rule = r.get<int32_t>();
+  const double kappa = r.get<double>();
+  const int prefactor = r.get<int32_t>(), trunc_rule = r.get<int32_t>(), n_dir = r.get<int32_t>();
+  fmmfft_plan p = nullptr;
+  int st = r.ok ? fmmfft_plan_create(&p, K[0], K[1], K[2], a, k0, L, format, decomp, tol) : FMMFFT_ERR_IO;
+  const std::pair<int, double> opts[] = {{FMMFFT_KEY_PRECISION, precision}, {FMMFFT_KEY_NPHI_RULE, nphi_rule},
+                                         {FMMFFT_KEY_NEAR_RULE, near_rule},  {FMMFFT_KEY_KAPPA, kappa},
+                                         {FMMFFT_KEY_PREFACTOR, prefactor},  {FMMFFT_KEY_TRUNC_RULE, trunc_rule}};
+  for (const auto& o : opts)
+    if (st == FMMFFT_OK) st = fmmfft_plan_set(p, o.first, o.second);
+  if (st == FMMFFT_OK && p->n_dir != n_dir) st = FMMFFT_ERR_INVALID_ARG;
+  if (st == FMMFFT_OK && format == FMMFFT_FORMAT_NONE) {
+    std::fclose(f);
+    f = nullptr;
+    st = fmmfft_compress(p);
+  } else if (st == FMMFFT_OK) {
+    fmm::Layout Lt;
+    const uint64_t big = (uint64_t)1 << 40;
+    for (int i = 0; i < 3; ++i) Lt.n[i] = r.get<int32_t>();
+    Lt.n_dir = r.get<int32_t>();
+    Lt.yz_fmt = r.get<int32_t>();
+    r.get_vec(Lt.pack, big);
+    Lt.scratch = r.get<int64_t>();
+    const uint64_t nst = r.get<uint64_t>();
+    if (nst > (uint64_t)fmm::kMaxGemmStages) r.ok = false;
+    for (uint64_t s = 0; r.ok && s < nst; ++s) {
+      const uint64_t cnt = r.get<uint64_t>();
+      if (cnt > (uint64_t)1 << 24) { r.ok = false; break; }
+      std::vector<fmm::GemmSpec> stage(cnt);
+      for (auto& g : stage) {
+        g.A = r.get_ref();
+        g.B = r.get_ref();
+        g.C = r.get_ref();
+        g.M = r.get<int32_t>();
+        g.N = r.get<int32_t>();
+        g.K = r.get<int32_t>();
+      }
+      Lt.stages.push_back(stage);
+    }
+    const uint64_t ns = r.get<uint64_t>();
+    if (ns != (uint64_t)n_dir) r.ok = false;
+    for (uint64_t s = 0; r.ok && s < ns; ++s) {
+      fmm::SlabSpec sl;
+      sl.h = r.get_ref();
+      sl.u2 = r.get_ref();
+      sl.u3 = r.get_ref();
+      sl.hx = r.get<int64_t>();
+      sl.ra = r.get<int32_t>();
+      sl.rb = r.get<int32_t>();
+      Lt.slabs.push_back(sl);
+    }
+    Lt.elements = r.get<int64_t>();
+    for (int i = 0; i < 6; ++i) Lt.rank[i] = r.get<int32_t>();
+    for (int i = 0; i < 3; ++i) Lt.mean_rank[i] = r.get<double>();
+    r.get_vec(Lt.ranks3, (uint64_t)n_dir * 3);
+    Lt.rmax_a = 0;
+    Lt.rmax_b = 0;
+    for (const auto& sl : Lt.slabs) {
+      Lt.rmax_a = std::max(Lt.rmax_a, sl.ra);
+      Lt.rmax_b = std::max(Lt.rmax_b, sl.rb);
+    }
+    // every reference must stay inside the buffers it names
+    const int64_t sizes[2] = {(int64_t)Lt.pack.size(), Lt.scratch};
+    auto inside = [&](const fmm::BufRef& b, int64_t count) {
+      return b.off >= 0 && count >= 0 && b.off + count <= sizes[b.buf];
+    };
+    for (const auto& stage : Lt.stages)
+      for (const auto& g : stage)
+        if (g.M < 1 || g.N < 1 || g.K < 1 || !inside(g.A, (int64_t)g.M * g.K) ||
+            !inside(g.B, (int64_t)g.K * g.N) || !inside(g.C, (int64_t)g.M * g.N) || g.C.buf != 1)
+          r.ok = false;
+    for (const auto& sl : Lt.slabs)
+      if (sl.rb < 1 || sl.ra < 0 ||
+          !inside(sl.h, sl.hx * (int64_t)(Lt.n[0] - 1) + (int64_t)(Lt.yz_fmt == 1 ? sl.ra : Lt.n[1]) * sl.rb) ||
+          (sl.ra > 0 && !inside(sl.u2, (int64_t)Lt.n[1] * sl.ra)) || !inside(sl.u3, (int64_t)Lt.n[2] * sl.rb))
+        r.ok = false;
+    for (int i = 0; i < 3; ++i)
+      if (Lt.n[i] != p->n[i]) r.ok = false;
+    if (Lt.n_dir != n_dir || (Lt.yz_fmt != 1 && Lt.yz_fmt != 2)) r.ok = false;
+    std::fclose(f);
+    f = nullptr;
+    st = r.ok ? install_layout(p, Lt) : FMMFFT_ERR_INVALID_ARG;
+  }
+  if (f) std::fclose(f);
+  if (st != FMMFFT_OK) {
+    if (p) fmmfft_plan_destroy(p);
+    return st;
+  }
+  *out = p;
   return FMMFFT_OK;
 }
 

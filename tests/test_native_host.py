@@ -115,3 +115,21 @@ def test_hosvd_setup_matches_oracle(native, tol):
             assert abs(err - ref) <= 1e-9 + 1e-6 * ref
     finally:
         native.fmmfft_plan_destroy(h)
+
+
+def test_plan_load_rejects_missing_and_foreign_files(native, tmp_path):
+    with pytest.raises(native.FmmfftError) as e:
+        native.fmmfft_plan_load(str(tmp_path / "missing.plan"))
+    assert e.value.status == native.FMMFFT_ERR_IO
+    bad = tmp_path / "bad.plan"
+    bad.write_bytes(b"not a plan file at all, just some bytes")
+    with pytest.raises(native.FmmfftError) as e:
+        native.fmmfft_plan_load(str(bad))
+    assert e.value.status == native.FMMFFT_ERR_INVALID_ARG
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, 2, 0, 0, 0.0)
+    try:
+        with pytest.raises(native.FmmfftError) as e:
+            native.fmmfft_plan_save(h, str(tmp_path / "x.plan"))
+        assert e.value.status == native.FMMFFT_ERR_NOT_COMPRESSED
+    finally:
+        native.fmmfft_plan_destroy(h)
