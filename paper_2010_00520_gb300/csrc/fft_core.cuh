@@ -169,6 +169,17 @@ __device__ __forceinline__ void dft_combine(C* x, const C* e, const C* o) {
   }
 }
 
+// w[c] = w1^c for c < CNT (w[0] = 1), by repeated squaring / multiplication
+// (depth log2 CNT): the stage-1 twiddles W^(a c) of one lane from the single
+// table value W^a, trading CNT - 2 shared-memory loads for complex products.
+template <int CNT, typename C>
+__device__ __forceinline__ void twiddle_powers(C w1, C* w) {
+  w[0] = mk<C>(1, 0);
+  if constexpr (CNT > 1) w[1] = w1;
+#pragma unroll
+  for (int c = 2; c < CNT; ++c) w[c] = (c % 2 == 0) ? cmul(w[c / 2], w[c / 2]) : cmul(w[c - 1], w1);
+}
+
 // ---------------------------------------------------------------------------
 // Line shapes: N = R1 * R2 with R1 <= R2, a team of T = R1 lanes per line.
 // ---------------------------------------------------------------------------
@@ -232,9 +243,11 @@ __device__ __forceinline__ void line_fft(C* ln, int es, C* xs, const C* tw, int 
 #pragma unroll
       for (int b = 0; b < NZ1; ++b) v[b] = ln[(a + R2 * b) * es];
       dft<R1, NZ1, S>(v);
+      C w[R1];
+      twiddle_powers<R1>(tw[a], w);
       xs[a] = v[0];
 #pragma unroll
-      for (int c = 1; c < R1; ++c) xs[c * (R2 + 1) + a] = twmul<S>(v[c], tw[a * c]);
+      for (int c = 1; c < R1; ++c) xs[c * (R2 + 1) + a] = twmul<S>(v[c], w[c]);
     }
   }
   __syncwarp();
@@ -272,9 +285,11 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
 #pragma unroll
       for (int b = 0; b < NZ1; ++b) v[b] = ln[(a + R2 * b) * es];
       dft<R1, NZ1, -1>(v);
+      C w[R1];
+      twiddle_powers<R1>(tw[a], w);
       xs[a] = v[0];
 #pragma unroll
-      for (int c = 1; c < R1; ++c) xs[c * (R2 + 1) + a] = twmul<-1>(v[c], tw[a * c]);
+      for (int c = 1; c < R1; ++c) xs[c * (R2 + 1) + a] = twmul<-1>(v[c], w[c]);
     }
   }
   __syncwarp();
@@ -292,9 +307,13 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
     // inverse stage 1 of the swapped shape (R1' = R2, R2' = R1): a' = t,
     // inputs x[t + R1 b'] = v[b'] for b' < R2
     dft<R2, R2, +1>(v);
-    xs[t] = v[0];
+    {
+      C w[R2];
+      twiddle_powers<R2>(tw[t], w);
+      xs[t] = v[0];
 #pragma unroll
-    for (int c = 1; c < R2; ++c) xs[c * (R1 + 1) + t] = twmul<+1>(v[c], tw[t * c]);
+      for (int c = 1; c < R2; ++c) xs[c * (R1 + 1) + t] = twmul<+1>(v[c], w[c]);
+    }
   }
   __syncwarp();
   if (active) {
