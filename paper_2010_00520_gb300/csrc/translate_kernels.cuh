@@ -238,13 +238,39 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
   C* xz = tz.xs(xs);
   C* inter = reinterpret_cast<C*>(P.inter);
   const int hy = N2 / 2;
+  // each thread owns up to kPre elements of the Kz x N2/2 input corner; the
+  // next field's are loaded into registers while this one is transformed
+  constexpr int kCorner = (N3 / 2) * (N2 / 2) / kThreads;
+  constexpr int kPre = kCorner < 1 ? 1 : (kCorner > 8 ? 8 : kCorner);    // register budget
+  const bool fits = kCorner <= 8 && Kz * hy <= kPre * kThreads;
+  C pre[kPre];
+  auto prefetch = [&](int j) {
+    const C* io = inter + (((size_t)p * P.nf + j) * P.n1 + x) * (size_t)(Kz * Ky);
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int i = tid + k * kThreads;
+      const int z = i / hy, y = i - z * hy;
+      pre[k] = (i < Kz * hy && y < Ky) ? io[z * Ky + y] : czero<C>();
+    }
+  };
+  if (fits) prefetch(0);
   for (int j = 0; j < P.nf; ++j) {
     const size_t f = (size_t)p * P.nf + j;
     C* io = inter + (f * P.n1 + x) * (size_t)(Kz * Ky);
     __syncthreads();
-    for (int i = tid; i < Kz * hy; i += kThreads) {
-      const int z = i / hy, y = i - z * hy;
-      plane[z * PY + y] = (y < Ky) ? io[z * Ky + y] : czero<C>();
+    if (fits) {
+#pragma unroll
+      for (int k = 0; k < kPre; ++k) {
+        const int i = tid + k * kThreads;
+        const int z = i / hy, y = i - z * hy;
+        if (i < Kz * hy) plane[z * PY + y] = pre[k];
+      }
+      if (j + 1 < P.nf) prefetch(j + 1);
+    } else {
+      for (int i = tid; i < Kz * hy; i += kThreads) {
+        const int z = i / hy, y = i - z * hy;
+        plane[z * PY + y] = (y < Ky) ? io[z * Ky + y] : czero<C>();
+      }
     }
     __syncthreads();
     for (int base = 0; base < Kz; base += Line<N2>::LPI) {
