@@ -46,6 +46,8 @@ struct fmmfft_plan_s {
   size_t io_bytes = 0;
   int* d_status = nullptr;
   cudaStream_t last_stream = nullptr;
+  cudaStream_t side = nullptr;  // restore pre-pass, overlapped with the x pass
+  cudaEvent_t fork = nullptr, join = nullptr;
   bool profile = false;
   bool profiled_run = false;
   cudaEvent_t events[FMMFFT_NUM_STAGES + 1] = {};
@@ -134,6 +136,14 @@ int ensure_common(fmmfft_plan_s* p) {
     int st = upload_complex(&p->d_tw[ax], tw, dbl);
     if (st != FMMFFT_OK) return st;
   }
+  if (!p->side && p->format != FMMFFT_FORMAT_NONE) {
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return FMMFFT_ERR_CUDA;
+    }
+  }
   if (!p->d_status) {
     void* s = nullptr;
     int st = dev_alloc(&s, sizeof(int));
@@ -166,6 +176,9 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   fmm::plan_yz(a);
   a.large_grid = p->large_grid;
   a.slab_scratch = p->d_slabs;
+  a.side = p->side;
+  a.fork = p->fork;
+  a.join = p->join;
   return a;
 }
 
@@ -1120,6 +1133,12 @@ int fmmfft_plan_destroy(fmmfft_plan p) {
   free_dev(p->d_io);
   for (auto& ev : p->events)
     if (ev) cudaEventDestroy(ev);
+  if (p->side) {
+    cudaStreamSynchronize(p->side);
+    cudaStreamDestroy(p->side);
+  }
+  if (p->fork) cudaEventDestroy(p->fork);
+  if (p->join) cudaEventDestroy(p->join);
   void* s = p->d_status;
   free_dev(s);
   delete p;

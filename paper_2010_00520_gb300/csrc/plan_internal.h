@@ -72,6 +72,10 @@ struct TranslateArgs {
   int* status;                       // device status word
   cudaEvent_t* events;               // FMMFFT_NUM_STAGES + 1 events, or null
   cudaStream_t stream;
+  // the restore pre-pass runs on `side`, overlapped with the forward x pass,
+  // when side and both events are given and no stage events are recorded
+  cudaStream_t side;
+  cudaEvent_t fork, join;
 };
 
 // Kernel launchers (translate_launch.cu).  Return a cudaError_t.

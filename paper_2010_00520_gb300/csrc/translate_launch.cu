@@ -206,12 +206,22 @@ static cudaError_t launch_all(const TranslateArgs& a) {
     if (a.events) cudaEventRecord(a.events[i], a.stream);
   };
   mark(0);
+  // the pre-pass needs only the stored factors: overlap it with the forward
+  // x pass on the side stream (serially when stage times are recorded)
+  const bool overlap = a.n_stages > 0 && a.side && a.fork && a.join && !a.events;
+  cudaStream_t ps = a.stream;
+  if (overlap) {
+    if ((e = cudaEventRecord(a.fork, a.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(a.side, a.fork, 0)) != cudaSuccess) return e;
+    ps = a.side;
+  }
   for (int i = 0; i < a.n_stages; ++i) {
     const GemmStage& g = a.stages[i];
     dim3 grid((g.max_n + kGemmT - 1) / kGemmT, (g.max_m + kGemmT - 1) / kGemmT, g.batch);
-    cgemm_batched_kernel<R><<<grid, kThreads, 0, a.stream>>>(g.desc);
+    cgemm_batched_kernel<R><<<grid, kThreads, 0, ps>>>(g.desc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (overlap && (e = cudaEventRecord(a.join, a.side)) != cudaSuccess) return e;
   mark(1);
   XPassParams X;
   X.src = a.s_in;
@@ -221,6 +231,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   X.rows = rows;
   X.rows_per_block = 0;
   if ((e = launch_x<R>(true, a.n[0], X, F, a.stream)) != cudaSuccess) return e;
+  if (overlap && (e = cudaStreamWaitEvent(a.stream, a.join, 0)) != cudaSuccess) return e;
   mark(2);
 
   YZParams Y;
