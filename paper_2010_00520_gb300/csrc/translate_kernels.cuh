@@ -300,6 +300,34 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
 }
 
 // ---------------------------------------------------------------------------
+// The same batched products on the tensor cores (3xTF32, complex64): block
+// (bx, by, g) computes the 64 x 64 output tile (by, bx) of product g with
+// tc_cgemm64.  The launch asks for kTcGemmSmem bytes of shared memory so
+// that at most four blocks share an SM and its 512 TMEM columns.
+// ---------------------------------------------------------------------------
+constexpr size_t kTcGemmSmem = 56 * 1024;
+
+template <typename R>   // float only; a template so that every unit may include it
+__global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDesc* __restrict__ descs,
+                                                                    int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint64_t tc_bar;
+  const GemmDesc d = descs[blockIdx.z];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  if (m0 >= d.M || n0 >= d.N) return;                     // uniform over the block
+  const float2* A = reinterpret_cast<const float2*>(d.A) + (size_t)m0 * d.K;
+  const float2* B = reinterpret_cast<const float2*>(d.B) + n0;
+  float2* Cm = reinterpret_cast<float2*>(d.C) + (size_t)m0 * d.N + n0;
+  const int K = d.K, N = d.N;
+  TcState tc = tc_setup(smem_raw, &tc_bar, &tmem_slot);
+  tc_cgemm64<true>(tc, min(64, d.M - m0), min(64, d.N - n0), K, [&](int m, int k) { return A[(size_t)m * K + k]; },
+                   [&](int k, int n) { return B[(size_t)k * N + n]; }, Cm, N, 1.0f);
+  if (!tc.ok && threadIdx.x == 0) atomicOr(status, kStatusTcTimeout);
+  tc_teardown(tc);
+}
+
+// ---------------------------------------------------------------------------
 // yz pass.  FMT 0: plain operator from global memory.  FMT 1: Tucker-like
 // restore of the slab (Fig. 3(a) steps 2-3, with the factors of the format):
 //   T~_p[x][y][z] = sum_{b,c} U2[y][b] H_p[x][b][c] U3[z][c]

@@ -215,10 +215,22 @@ static cudaError_t launch_all(const TranslateArgs& a) {
     if ((e = cudaStreamWaitEvent(a.side, a.fork, 0)) != cudaSuccess) return e;
     ps = a.side;
   }
+  // 3xTF32 plans run the pre-pass products on the tensor cores too
+  const bool tc_gemm = a.precision == FMMFFT_PREC_C64_3XTF32;
+  if (tc_gemm) {
+    static bool configured = false;
+    if (!configured) {
+      e = cudaFuncSetAttribute(cgemm_batched_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTcGemmSmem);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+  }
   for (int i = 0; i < a.n_stages; ++i) {
     const GemmStage& g = a.stages[i];
     dim3 grid((g.max_n + kGemmT - 1) / kGemmT, (g.max_m + kGemmT - 1) / kGemmT, g.batch);
-    cgemm_batched_kernel<R><<<grid, kThreads, 0, ps>>>(g.desc);
+    if (tc_gemm && sizeof(R) == 4) cgemm_batched_tc_kernel<float><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status);
+    else cgemm_batched_kernel<R><<<grid, kThreads, 0, ps>>>(g.desc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (overlap && (e = cudaEventRecord(a.join, a.side)) != cudaSuccess) return e;

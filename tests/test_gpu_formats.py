@@ -3,8 +3,12 @@ Tucker-4D (Fig. 3(b)), H-Tucker (Fig. 3(c)) and TT-4D (Fig. 4(b)).
 
 * imported oracle factors: the GPU restores the oracle's own decomposition;
   compared with the oracle translating with its restoration of the same
-  factors (kernel arithmetic only): rel L2 <= 2e-6 in complex64, <= 1e-10 in
-  complex128;
+  factors (kernel arithmetic only): rel L2 <= 2e-6 in complex64 with FP32
+  restores, <= 5e-6 with 3xTF32 tensor-core restores, <= 1e-10 in complex128.
+  The 3xTF32 bound: each tensor-core product keeps big*big + small*big +
+  big*small of the TF32 splits, a relative error near 2^-21 (~5e-7) per
+  product; the H-Tucker restore chains four of them (E = C12 B, the core
+  C_p = E V_p, H_p = U1 C_p, the slab) before the FP32 FFTs (~2e-7);
 * the library's own compression against the oracle's uncompressed FP64
   translation: rel L2 <= tol + 1e-5 (acceptance bound).
 """
@@ -134,7 +138,7 @@ def test_tensor_core_restore_matches_oracle(native, cuda, fmt, dec):
         assert F.fmmfft_plan_stats(h)["restore_on_tensor_cores"] == 1
         S = field_spectra(81 + DEC[dec], plan.n_dir, nrhs, K)
         out = _run(F, torch, h, S, nrhs)
-        assert _rel(out, pl.translate_with(comp.restore, S)) <= 2e-6
+        assert _rel(out, pl.translate_with(comp.restore, S)) <= 5e-6
     finally:
         F.fmmfft_plan_destroy(h)
 

@@ -3,8 +3,9 @@
 which run the persistent large-plane kernel with the slab in a global (L2)
 scratch slot.  Reduced x extent and few directions keep the oracle fast.
 
-Same operator / factors on both sides: rel L2 <= 2e-6 (complex64, FP32 or
-3xTF32 restores), <= 1e-10 (complex128)."""
+Same operator / factors on both sides: rel L2 <= 2e-6 (complex64, FP32
+restores), <= 5e-6 (3xTF32 tensor-core restores and pre-pass products, see
+test_gpu_formats.py), <= 1e-10 (complex128)."""
 import numpy as np
 import pytest
 
@@ -77,6 +78,6 @@ def test_large_plane_compressed(native, cuda, K, L, nrhs, fmt, dec, prec):
             F.fmmfft_import_htucker(h, np.array(P.ranks, dtype=np.int32), *P.U, P.C12, P.C34, P.B)
         S = field_spectra(93 + DEC, plan.n_dir, nrhs, K)
         out = _run(F, torch, h, S, nrhs)
-        assert _rel(out, pl.translate_with(comp.restore, S)) <= 2e-6
+        assert _rel(out, pl.translate_with(comp.restore, S)) <= (5e-6 if prec == 2 else 2e-6)
     finally:
         F.fmmfft_plan_destroy(h)
