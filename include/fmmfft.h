@@ -142,6 +142,11 @@ typedef struct fmmfft_stats {
   int large_planes;              /* 1 when the y-z pass keeps restored slabs
                                     in global scratch (planes too large for
                                     shared memory)                           */
+  int schedule[4];               /* fmmfft_autotune's choices: x-pass rows per
+                                    block multiple (0 = default 2), slab restore
+                                    on tensor cores (-1 default, 0 off, 1 on),
+                                    pre-pass on tensor cores (same), pre-pass
+                                    serial (1) or overlapped (0)            */
 } fmmfft_stats;
 
 /*
@@ -341,6 +346,26 @@ int fmmfft_batch_create(fmmfft_batch* out, const fmmfft_plan* plans, int nplans)
 int fmmfft_batch_translate(fmmfft_batch batch, const void* const* S_in, void* const* S_out,
                            const int* nrhs, void* stream);
 int fmmfft_batch_destroy(fmmfft_batch batch);
+
+/*
+ * Autotuner (no counterpart in the paper): times the plan's candidate
+ * schedules for `nrhs` RHS with CUDA events on a private stream and applies
+ * the fastest.  Candidates: x-pass rows per block (1, 2 or 4 block-line
+ * multiples), slab restores and pre-pass products on the tensor cores or the
+ * FP32 CUDA cores (3xTF32 plans; the FP32 route is at least as accurate), the
+ * pre-pass overlapped with the forward x pass or in line with it.  Stops
+ * starting new candidates once budget_ms of wall time has passed (the first
+ * always runs).  Allocates and frees two field buffers for the timing.  When
+ * the environment variable FMMFFT_TUNE_CACHE names a file, a schedule stored
+ * there for the same device, grid, format, precision, ranks and nrhs is
+ * applied without timing, and a newly tuned one is appended.  The schedule
+ * changes only speed, not the results beyond rounding; fmmfft_stats reports
+ * it.  Errors: NOT_COMPRESSED, INVALID_ARG, OOM, CUDA.
+ * fmmfft_batch_autotune: the same for every plan of a batch (nrhs[i] RHS,
+ * budget_ms shared evenly); drops the batch's captured graph.
+ */
+int fmmfft_autotune(fmmfft_plan plan, int nrhs, double budget_ms);
+int fmmfft_batch_autotune(fmmfft_batch batch, const int* nrhs, double budget_ms);
 
 /* Fill *out (see fmmfft_stats). */
 int fmmfft_plan_stats(fmmfft_plan plan, fmmfft_stats* out);

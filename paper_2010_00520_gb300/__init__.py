@@ -54,7 +54,7 @@ EXPORTED = (
     "fmmfft_plan_ranks", "fmmfft_translate_noalloc", "fmmfft_import_tt3d", "fmmfft_import_tucker4d",
     "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
     "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy", "fmmfft_plan_save",
-    "fmmfft_plan_load",
+    "fmmfft_plan_load", "fmmfft_autotune", "fmmfft_batch_autotune",
 )
 
 
@@ -73,7 +73,7 @@ class _Stats(ctypes.Structure):
         ("saving", ctypes.c_double), ("device_bytes_operator", ctypes.c_int64),
         ("device_bytes_scratch", ctypes.c_int64), ("setup_seconds", ctypes.c_double),
         ("restore_on_tensor_cores", ctypes.c_int), ("kernel_launches", ctypes.c_int),
-        ("large_planes", ctypes.c_int),
+        ("large_planes", ctypes.c_int), ("schedule", ctypes.c_int * 4),
     ]
 
 
@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
         "fmmfft_batch_translate": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp],
         "fmmfft_batch_destroy": [vp],
         "fmmfft_plan_save": [vp, ctypes.c_char_p],
+        "fmmfft_autotune": [vp, i, d],
+        "fmmfft_batch_autotune": [vp, ip, d],
         "fmmfft_plan_load": [ctypes.POINTER(vp), ctypes.c_char_p],
         "fmmfft_translate": [vp, vp, vp, i, vp],
         "fmmfft_translate_host": [vp, vp, vp, i, vp],
@@ -239,6 +241,15 @@ def fmmfft_compress_host(plan, restored=True):
     _check(lib().fmmfft_compress_host(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                       _dptr(out) if restored else None), "fmmfft_compress_host")
     return (r.reshape(nd, 3) if is3d else r), out
+
+
+def fmmfft_autotune(plan, nrhs, budget_ms=2000.0):
+    _check(lib().fmmfft_autotune(plan, int(nrhs), float(budget_ms)), "fmmfft_autotune")
+
+
+def fmmfft_batch_autotune(batch, nrhs, budget_ms=2000.0):
+    r, rp = _ints(nrhs)
+    _check(lib().fmmfft_batch_autotune(batch, rp, float(budget_ms)), "fmmfft_batch_autotune")
 
 
 def fmmfft_plan_save(plan, path):

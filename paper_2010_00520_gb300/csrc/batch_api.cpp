@@ -135,6 +135,22 @@ int fmmfft_batch_translate(fmmfft_batch b, const void* const* S_in, void* const*
   return st;
 }
 
+int fmmfft_batch_autotune(fmmfft_batch b, const int* nrhs, double budget_ms) {
+  if (!b || !nrhs || !(budget_ms > 0)) return FMMFFT_ERR_INVALID_ARG;
+  const double each = budget_ms / (double)b->plans.size();
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const int st = fmmfft_autotune(b->plans[i], nrhs[i], each);
+    if (st != FMMFFT_OK) return st;
+  }
+  // schedules changed: the captured graph no longer matches
+  drop_graph(b);
+  b->key_in.clear();
+  b->key_out.clear();
+  b->key_nrhs.clear();
+  b->key_seen = 0;
+  return FMMFFT_OK;
+}
+
 int fmmfft_batch_destroy(fmmfft_batch b) {
   if (!b) return FMMFFT_ERR_INVALID_ARG;
   for (auto s : b->side)

@@ -1,6 +1,10 @@
 // C ABI of the translation library: plan life cycle, set-up, translation.
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+#include <string>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -48,6 +52,7 @@ struct fmmfft_plan_s {
   cudaStream_t last_stream = nullptr;
   cudaStream_t side = nullptr;  // restore pre-pass, overlapped with the x pass
   cudaEvent_t fork = nullptr, join = nullptr;
+  fmm::Schedule sched;          // fmmfft_autotune's choices
   bool profile = false;
   bool profiled_run = false;
   cudaEvent_t events[FMMFFT_NUM_STAGES + 1] = {};
@@ -172,7 +177,10 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   a.n_stages = p->n_stages;
   for (int i = 0; i < p->n_stages; ++i) a.stages[i] = p->stages[i];
   a.status = p->d_status;
-  a.tc = fmm::tc_restore_applies(a) ? 1 : 0;
+  a.tc = fmm::tc_restore_applies(a) && p->sched.tc_slab != 0 ? 1 : 0;
+  a.tc_gemm = p->precision == FMMFFT_PREC_C64_3XTF32 && p->sched.tc_gemm != 0 ? 1 : 0;
+  a.xrows = p->sched.xrows;
+  a.no_overlap = p->sched.no_overlap;
   fmm::plan_yz(a);
   a.large_grid = p->large_grid;
   a.slab_scratch = p->d_slabs;
@@ -872,6 +880,10 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
     o->restore_on_tensor_cores = a.tc;
     o->kernel_launches = a.n_stages + 3;
     o->large_planes = a.large;
+    o->schedule[0] = p->sched.xrows;
+    o->schedule[1] = p->sched.tc_slab;
+    o->schedule[2] = p->sched.tc_gemm;
+    o->schedule[3] = p->sched.no_overlap;
   }
   return FMMFFT_OK;
 }
@@ -1123,6 +1135,144 @@ int fmmfft_plan_load(fmmfft_plan* out, const char* path) {
   }
   *out = p;
   return FMMFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time the plan's candidate schedules, keep the fastest
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+std::string tune_signature(const fmmfft_plan_s* p, int nrhs) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "unknown";
+  int sms = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+    name = prop.name;
+    sms = prop.multiProcessorCount;
+  }
+  cudaGetLastError();
+  for (auto& c : name)
+    if (c == ' ' || c == ';') c = '_';
+  std::ostringstream o;
+  o << "dev=" << name << ";sm=" << sms << ";K=" << p->K[0] << "," << p->K[1] << "," << p->K[2]
+    << ";n_dir=" << p->n_dir << ";fmt=" << p->format << ";dec=" << p->decomp << ";prec=" << p->precision
+    << ";ranks=" << p->rmax_a << "," << p->rmax_b << ";stages=" << p->n_stages << ";nrhs=" << nrhs;
+  return o.str();
+}
+
+bool tune_cache_lookup(const char* path, const std::string& sig, fmm::Schedule& out) {
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string key;
+    fmm::Schedule sc;
+    double ms = 0;
+    if ((is >> key >> sc.xrows >> sc.tc_slab >> sc.tc_gemm >> sc.no_overlap >> ms) && key == sig) {
+      out = sc;
+      found = true;   // the last entry for a signature wins
+    }
+  }
+  return found;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmmfft_autotune(fmmfft_plan p, int nrhs, double budget_ms) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
+  if (nrhs < 1 || nrhs > 4096 || !(budget_ms > 0)) return FMMFFT_ERR_INVALID_ARG;
+  const std::string sig = tune_signature(p, nrhs);
+  const char* cache = std::getenv("FMMFFT_TUNE_CACHE");
+  const fmm::Schedule before = p->sched;
+  if (cache && *cache) {
+    fmm::Schedule sc;
+    if (tune_cache_lookup(cache, sig, sc)) {
+      p->sched = sc;
+      if (check_supported(p) && ensure_slabs(p) == FMMFFT_OK) return FMMFFT_OK;
+      p->sched = before;   // stale entry: tune again
+    }
+  }
+  // candidates, the current default first
+  std::vector<fmm::Schedule> cand;
+  const fmm::TranslateArgs a0 = base_args(p);
+  const bool tc_slab_applies = fmm::tc_restore_applies(a0);
+  const bool stages = p->n_stages > 0;
+  for (int xr : {2, 1, 4})
+    for (int ts : tc_slab_applies ? std::vector<int>{-1, 0} : std::vector<int>{-1})
+      for (int tg : (stages && p->precision == FMMFFT_PREC_C64_3XTF32) ? std::vector<int>{-1, 0} : std::vector<int>{-1})
+        for (int no : stages ? std::vector<int>{0, 1} : std::vector<int>{0}) {
+          fmm::Schedule sc;
+          sc.xrows = xr;
+          sc.tc_slab = ts;
+          sc.tc_gemm = tg;
+          sc.no_overlap = no;
+          cand.push_back(sc);
+        }
+  const size_t bytes = (size_t)p->n_dir * 2 * nrhs * p->K[0] * p->K[1] * p->K[2] * elem_bytes(p);
+  void *din = nullptr, *dout = nullptr;
+  int st = dev_alloc(&din, bytes);
+  if (st == FMMFFT_OK) st = dev_alloc(&dout, bytes);
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == FMMFFT_OK && (cudaMemset(din, 0, bytes) != cudaSuccess ||
+                          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+                          cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    st = FMMFFT_ERR_CUDA;
+  const bool profile = p->profile;
+  p->profile = false;
+  fmm::Schedule best = before;
+  float best_ms = 0.f;
+  bool have = false;
+  const auto t_start = std::chrono::steady_clock::now();
+  for (size_t c = 0; st == FMMFFT_OK && c < cand.size(); ++c) {
+    if (have && std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count() >
+                    budget_ms)
+      break;
+    p->sched = cand[c];
+    if (!check_supported(p) || ensure_slabs(p) != FMMFFT_OK) continue;
+    int rs = FMMFFT_OK;
+    for (int w = 0; w < 2 && rs == FMMFFT_OK; ++w) rs = fmmfft_translate(p, din, dout, nrhs, s);
+    const int reps = 5;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && rs == FMMFFT_OK; ++r) rs = fmmfft_translate(p, din, dout, nrhs, s);
+    cudaEventRecord(e1, s);
+    if (rs != FMMFFT_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (!have || ms < best_ms) {
+      best = cand[c];
+      best_ms = ms;
+      have = true;
+    }
+  }
+  p->profile = profile;
+  p->sched = have ? best : before;
+  if (st == FMMFFT_OK && (!check_supported(p) || ensure_slabs(p) != FMMFFT_OK)) st = FMMFFT_ERR_UNSUPPORTED;
+  if (s) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  free_dev(din);
+  free_dev(dout);
+  if (st == FMMFFT_OK && have && cache && *cache) {
+    std::ofstream f(cache, std::ios::app);
+    if (f) f << sig << " " << best.xrows << " " << best.tc_slab << " " << best.tc_gemm << " " << best.no_overlap << " "
+             << best_ms << "\n";
+  }
+  return st;
 }
 
 int fmmfft_plan_destroy(fmmfft_plan p) {

@@ -76,6 +76,19 @@ struct TranslateArgs {
   // when side and both events are given and no stage events are recorded
   cudaStream_t side;
   cudaEvent_t fork, join;
+  // schedule knobs (fmmfft_autotune); 0 = default
+  int xrows;                         // x-pass rows per block as a multiple of the
+                                     // lines one block iteration covers (1, 2, 4)
+  int no_overlap;                    // 1: pre-pass in line with the x pass
+  int tc_gemm;                       // pre-pass products on the tensor cores
+};
+
+// A translation schedule: the choices fmmfft_autotune makes for a plan.
+struct Schedule {
+  int xrows = 0;          // 0: default (2), else 1, 2 or 4
+  int tc_slab = -1;       // -1: default (tensor cores when they apply), 0 off, 1 on
+  int tc_gemm = -1;       // -1: default (tensor cores for 3xTF32 plans), 0 off, 1 on
+  int no_overlap = 0;
 };
 
 // Kernel launchers (translate_launch.cu).  Return a cudaError_t.

@@ -27,8 +27,8 @@ FMM_YZL_DECL(f64, 2)
 static const size_t kMaxSmem = 227 * 1024;
 
 template <typename R, int N1>
-static int xpass_rows_per_block(int rows) {
-  int rpb = 2 * Line<N1>::LPI;
+static int xpass_rows_per_block(int rows, int mult) {
+  int rpb = (mult > 0 ? mult : 2) * Line<N1>::LPI;
   while (rpb > Line<N1>::LPI && xpass_smem<R, N1>(rpb) > 96 * 1024) rpb /= 2;
   return rpb < rows ? rpb : rows;
 }
@@ -36,7 +36,7 @@ static int xpass_rows_per_block(int rows) {
 template <typename R, int N1>
 static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s) {
   static size_t configured_f = 0, configured_i = 0;
-  P.rows_per_block = xpass_rows_per_block<R, N1>(P.rows);
+  P.rows_per_block = xpass_rows_per_block<R, N1>(P.rows, P.rows_per_block);
   const size_t smem = xpass_smem<R, N1>(P.rows_per_block);
   dim3 grid((unsigned)(((P.rows + P.rows_per_block - 1) / P.rows_per_block) * (size_t)F));
   if (fwd) {
@@ -208,7 +208,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   mark(0);
   // the pre-pass needs only the stored factors: overlap it with the forward
   // x pass on the side stream (serially when stage times are recorded)
-  const bool overlap = a.n_stages > 0 && a.side && a.fork && a.join && !a.events;
+  const bool overlap = a.n_stages > 0 && a.side && a.fork && a.join && !a.events && !a.no_overlap;
   cudaStream_t ps = a.stream;
   if (overlap) {
     if ((e = cudaEventRecord(a.fork, a.stream)) != cudaSuccess) return e;
@@ -216,7 +216,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
     ps = a.side;
   }
   // 3xTF32 plans run the pre-pass products on the tensor cores too
-  const bool tc_gemm = a.precision == FMMFFT_PREC_C64_3XTF32;
+  const bool tc_gemm = a.tc_gemm != 0;
   if (tc_gemm) {
     static bool configured = false;
     if (!configured) {
@@ -241,7 +241,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   X.tw = a.tw[0];
   X.Kx = a.K[0];
   X.rows = rows;
-  X.rows_per_block = 0;
+  X.rows_per_block = a.xrows;   // multiplier in, rows per block chosen per launch
   if ((e = launch_x<R>(true, a.n[0], X, F, a.stream)) != cudaSuccess) return e;
   if (overlap && (e = cudaStreamWaitEvent(a.stream, a.join, 0)) != cudaSuccess) return e;
   mark(2);

@@ -133,3 +133,13 @@ def test_plan_load_rejects_missing_and_foreign_files(native, tmp_path):
         assert e.value.status == native.FMMFFT_ERR_NOT_COMPRESSED
     finally:
         native.fmmfft_plan_destroy(h)
+
+
+def test_autotune_needs_a_compressed_plan(native):
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, 2, 0, 0, 0.0)
+    try:
+        with pytest.raises(native.FmmfftError) as e:
+            native.fmmfft_autotune(h, 1, 100.0)
+        assert e.value.status == native.FMMFFT_ERR_NOT_COMPRESSED
+    finally:
+        native.fmmfft_plan_destroy(h)
