@@ -59,7 +59,7 @@ FORMAT_NAMES = {(3, 1): "tucker3d", (3, 2): "tt3d", (4, 1): "tucker4d", (4, 2): 
                 (0, 0): "none"}
 CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
 # version of the yz kernel the committed DRAM-traffic figure was taken on
-YZ_KERNEL_VERSION = 2
+YZ_KERNEL_VERSION = 3
 
 
 def _units(n, n_dir, nrhs):
@@ -294,6 +294,8 @@ def main():
     ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "fp32"],
                     help="restore arithmetic of the compressed arm: tensor cores (3xTF32) or FP32 CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default schedule instead of autotuning each arm before timing")
     ap.add_argument("--workload", default=DEFAULT_WL, choices=sorted(WORKLOADS),
                     help="workload (default: the headline Tucker-3D one); others print their own line "
                          "without CPU baseline and end-to-end arms")
@@ -355,6 +357,8 @@ def main():
         t0 = time.perf_counter()
         F.fmmfft_compress(h)
         t_setup[name] = time.perf_counter() - t0
+        if not args.no_autotune:
+            F.fmmfft_autotune(h, args.nrhs or W["nrhs"], 4000.0)
         plans[name] = h
     main_arm = "compressed" if "compressed" in plans else "plain"
     st = F.fmmfft_plan_stats(plans[main_arm])
@@ -458,7 +462,7 @@ def main():
             tj = json.load(f)
         # counters only count for the kernel they were taken on
         if (tj.get("kernel_version") == YZ_KERNEL_VERSION and wl_name == DEFAULT_WL and nrhs == W["nrhs"]
-                and args.restore == "3xtf32"):
+                and st.get("restore_on_tensor_cores") == 1):
             traffic = tj.get("dram_bytes_per_launch")
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
@@ -474,6 +478,9 @@ def main():
                                  "FP32 FFTs, 3xTF32 restores on the tensor cores (tcgen05, FP32 accumulate)"
                                  if st.get("restore_on_tensor_cores") else "FP32 FFTs and FP32 restores"),
                    "large_planes": bool(st.get("large_planes")),
+                   "schedule": {name: dict(zip(("xrows", "tc_slab", "tc_gemm", "serial_prepass"),
+                                               [int(v) for v in F.fmmfft_plan_stats(h)["schedule"]]))
+                                for name, h in plans.items()},
                    "setup_s": {k: round(v, 2) for k, v in t_setup.items()},
                    "l2": ("inputs and outputs each larger than the 129 MB L2; no flush" if io_bytes > 129e6 else
                           "inputs smaller than L2 (parity-sized workload); no flush")},
