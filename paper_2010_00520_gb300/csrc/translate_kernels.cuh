@@ -212,90 +212,119 @@ __global__ void __launch_bounds__(kThreads) cgemm_batched_kernel(const GemmDesc*
 }
 
 // ---------------------------------------------------------------------------
-// The per-field work of a yz block (x, p): for each field of direction p,
-// forward y DFT of rows z < Kz, z DFT x Hadamard with the slab x inverse z DFT
-// of every column, inverse y DFT, corner written back in place.  `op` is the
-// slab T~_p[x] as [z][y] with row pitch `op_pitch` (shared or global memory);
-// `plane` holds N3 / 2 rows of pitch N2 + 1.
+// The per-field work of a yz block (x, p), G fields per round: forward y DFT
+// of rows z < Kz, z DFT x Hadamard with the slab x inverse z DFT of every
+// column, inverse y DFT, corner written back in place.  `op` is the slab
+// T~_p[x] as [z][y] with row pitch `op_pitch` (shared or global memory);
+// `planes` holds G planes of N3 / 2 rows of pitch N2 + 1 (a forward z line
+// reads only its first half, an inverse one writes only rows z < Kz <= N3/2).
+// The G fields of a round share the phase barriers; each phase runs the
+// unchanged line loop once per field.
 // ---------------------------------------------------------------------------
-template <typename R, int N2, int N3>
-__device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>* plane, cx<R>* xs,
+template <typename R, int N2, int N3, int G>
+__device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>* planes, cx<R>* xs,
                                           const cx<R>* tw2, const cx<R>* tw3, const cx<R>* op,
                                           int op_pitch) {
   using C = cx<R>;
   constexpr int PY = N2 + 1;
+  constexpr int PS = (N3 / 2) * PY;          // plane stride
   const int tid = threadIdx.x;
   const int Ky = P.Ky, Kz = P.Kz;
   __syncthreads();
   // rows Kz .. N3/2 - 1 stay zero for every field
-  for (int i = tid; i < (N3 / 2 - Kz) * N2; i += kThreads) {
-    const int z = Kz + i / N2, y = i % N2;
-    plane[z * PY + y] = czero<C>();
-  }
+  for (int g = 0; g < G; ++g)
+    for (int i = tid; i < (N3 / 2 - Kz) * N2; i += kThreads) {
+      const int z = Kz + i / N2, y = i % N2;
+      planes[g * PS + z * PY + y] = czero<C>();
+    }
   TeamPos<N2> ty;
   TeamPos<N3> tz;
   C* xy = ty.xs(xs);
   C* xz = tz.xs(xs);
   C* inter = reinterpret_cast<C*>(P.inter);
   const int hy = N2 / 2;
-  // each thread owns up to kPre elements of the Kz x N2/2 input corner; the
-  // next field's are loaded into registers while this one is transformed
+  const size_t fstride = (size_t)P.n1 * Kz * Ky;   // between consecutive fields
+  // each thread owns up to kPre elements of a field's Kz x N2/2 input
+  // corner; the next round's are loaded into registers during this one
   constexpr int kCorner = (N3 / 2) * (N2 / 2) / kThreads;
-  constexpr int kPre = kCorner < 1 ? 1 : (kCorner > 8 ? 8 : kCorner);    // register budget
-  const bool fits = kCorner <= 8 && Kz * hy <= kPre * kThreads;
-  C pre[kPre];
-  auto prefetch = [&](int j) {
-    const C* io = inter + (((size_t)p * P.nf + j) * P.n1 + x) * (size_t)(Kz * Ky);
+  constexpr int kPre = kCorner < 1 ? 1 : kCorner;
+  constexpr bool kUsePre = kCorner * G <= 8;                                 // register budget
+  const bool fits = kUsePre && Kz * hy <= kPre * kThreads;
+  C pre[kUsePre ? G * kPre : 1];
+  auto prefetch = [&](int j0) {
+    if constexpr (kUsePre) {
+      const C* io = inter + (((size_t)p * P.nf + j0) * P.n1 + x) * (size_t)(Kz * Ky);
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      const int i = tid + k * kThreads;
-      const int z = i / hy, y = i - z * hy;
-      pre[k] = (i < Kz * hy && y < Ky) ? io[z * Ky + y] : czero<C>();
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) {
+          const int i = tid + k * kThreads;
+          const int z = i / hy, y = i - z * hy;
+          pre[g * kPre + k] = (j0 + g < P.nf && i < Kz * hy && y < Ky) ? io[g * fstride + z * Ky + y] : czero<C>();
+        }
     }
   };
   if (fits) prefetch(0);
-  for (int j = 0; j < P.nf; ++j) {
-    const size_t f = (size_t)p * P.nf + j;
-    C* io = inter + (f * P.n1 + x) * (size_t)(Kz * Ky);
+  for (int j0 = 0; j0 < P.nf; j0 += G) {
+    const int ng = min(G, P.nf - j0);
+    C* io = inter + (((size_t)p * P.nf + j0) * P.n1 + x) * (size_t)(Kz * Ky);
     __syncthreads();
     if (fits) {
+      if constexpr (kUsePre) {
 #pragma unroll
-      for (int k = 0; k < kPre; ++k) {
-        const int i = tid + k * kThreads;
-        const int z = i / hy, y = i - z * hy;
-        if (i < Kz * hy) plane[z * PY + y] = pre[k];
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+          for (int k = 0; k < kPre; ++k) {
+            const int i = tid + k * kThreads;
+            const int z = i / hy, y = i - z * hy;
+            if (g < ng && i < Kz * hy) planes[g * PS + z * PY + y] = pre[g * kPre + k];
+          }
       }
-      if (j + 1 < P.nf) prefetch(j + 1);
+      if (j0 + G < P.nf) prefetch(j0 + G);
     } else {
-      for (int i = tid; i < Kz * hy; i += kThreads) {
-        const int z = i / hy, y = i - z * hy;
-        plane[z * PY + y] = (y < Ky) ? io[z * Ky + y] : czero<C>();
+      for (int g = 0; g < ng; ++g)
+        for (int i = tid; i < Kz * hy; i += kThreads) {
+          const int z = i / hy, y = i - z * hy;
+          planes[g * PS + z * PY + y] = (y < Ky) ? io[g * fstride + z * Ky + y] : czero<C>();
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+      C* plane = planes + g * PS;
+      for (int base = 0; base < Kz; base += Line<N2>::LPI) {
+        const int ln = base + ty.line;
+        const bool act = ln < Kz;
+        line_fft<N2, -1, true>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, N2);
       }
     }
     __syncthreads();
-    for (int base = 0; base < Kz; base += Line<N2>::LPI) {
-      const int ln = base + ty.line;
-      const bool act = ln < Kz;
-      line_fft<N2, -1, true>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, N2);
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+      C* plane = planes + g * PS;
+      for (int base = 0; base < N2; base += Line<N3>::LPI) {
+        const int col = base + tz.line;
+        const bool act = col < N2;
+        const int cc = act ? col : 0;
+        line_conv<N3>(plane + cc, PY, xz, tw3, op + cc, op_pitch, tz.t, act, Kz);
+      }
     }
     __syncthreads();
-    for (int base = 0; base < N2; base += Line<N3>::LPI) {
-      const int col = base + tz.line;
-      const bool act = col < N2;
-      const int cc = act ? col : 0;
-      line_conv<N3>(plane + cc, PY, xz, tw3, op + cc, op_pitch, tz.t, act, Kz);
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+      C* plane = planes + g * PS;
+      for (int base = 0; base < Kz; base += Line<N2>::LPI) {
+        const int ln = base + ty.line;
+        const bool act = ln < Kz;
+        line_fft<N2, +1, false>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, Ky);
+      }
     }
     __syncthreads();
-    for (int base = 0; base < Kz; base += Line<N2>::LPI) {
-      const int ln = base + ty.line;
-      const bool act = ln < Kz;
-      line_fft<N2, +1, false>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, Ky);
-    }
-    __syncthreads();
-    for (int i = tid; i < Kz * Ky; i += kThreads) {
-      const int z = i / Ky, y = i - z * Ky;
-      io[i] = plane[z * PY + y];
-    }
+    for (int g = 0; g < ng; ++g)
+      for (int i = tid; i < Kz * Ky; i += kThreads) {
+        const int z = i / Ky, y = i - z * Ky;
+        io[g * fstride + i] = planes[g * PS + z * PY + y];
+      }
   }
 }
 
@@ -339,7 +368,8 @@ struct YZLayout {
   static constexpr int PY = N2 + 1;
   static constexpr int XW = (Line<N2>::XW > Line<N3>::XW) ? Line<N2>::XW : Line<N3>::XW;
   static constexpr size_t fixed_elems = (size_t)N3 * PY + N2 + N3;   // Tt + twiddles
-  static constexpr size_t plane_elems = (size_t)N3 * PY + kWarps * XW;
+  static constexpr int G = 2;                                          // fields per round
+  static constexpr size_t plane_elems = (size_t)G * (N3 / 2) * PY + kWarps * XW;
   // restore work space: Gt (rb x N2) plus, before stage B, Ht (rb x ra) and
   // U2t (ra x N2) [FMT 1] or nothing [FMT 2]; then U3 (N3 x rb)
   static size_t restore_elems(int fmt, int ra, int rb) {
@@ -370,8 +400,8 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
   C* tw2 = Tt + N3 * PY;
   C* tw3 = tw2 + N2;
   C* work = tw3 + N3;
-  C* plane = work;                          // N3 x PY, field [z][y]
-  C* xs = plane + N3 * PY;
+  C* plane = work;                          // LY::G planes of N3/2 x PY, field [z][y]
+  C* xs = plane + LY::G * (N3 / 2) * PY;
   const int x = blockIdx.x, p = blockIdx.y;
   const int tid = threadIdx.x;
   for (int i = tid; i < N2; i += kThreads) tw2[i] = reinterpret_cast<const C*>(P.tw2)[i];
@@ -448,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
     }
   }
-  yz_fields<R, N2, N3>(P, x, p, plane, xs, tw2, tw3, Tt, PY);
+  yz_fields<R, N2, N3, LY::G>(P, x, p, plane, xs, tw2, tw3, Tt, PY);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) yzl_kernel(YZParams P) {
       __syncthreads();
       op = slot;
     }
-    yz_fields<R, N2, N3>(P, x, p, plane, xs, tw2, tw3, op, N2);
+    yz_fields<R, N2, N3, 1>(P, x, p, plane, xs, tw2, tw3, op, N2);
   }
   if constexpr (TC) {
     if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
