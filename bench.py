@@ -319,9 +319,9 @@ def main():
     import paper_2010_00520_gb300 as F
     from seeded_inputs import field_spectra
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2010_00520_gb300.replicas import job_throughput, max_over_ranks, ranks_from_env, replica_seed
+    R_ = ranks_from_env()
+    world, rank, local = R_.world, R_.rank, R_.local
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -369,7 +369,7 @@ def main():
     stream = torch.cuda.current_stream()
     S_host = None
     if wl_name == DEFAULT_WL:
-        S_host = field_spectra(W["seed"], n_dir, nrhs, K).astype(cdt)
+        S_host = field_spectra(replica_seed(W["seed"], rank), n_dir, nrhs, K).astype(cdt)
         x = torch.from_numpy(S_host).to("cuda")
     else:
         # generated one direction at a time straight into device memory
@@ -377,7 +377,7 @@ def main():
         x = torch.empty((n_dir, 2, nrhs, K[2], K[1], K[0]), dtype=tdt, device="cuda")
         nf = 2 * nrhs
         for p in range(n_dir):
-            rows = field_spectra_rows(W["seed"], n_dir, nrhs, K, np.arange(p * nf, (p + 1) * nf))
+            rows = field_spectra_rows(replica_seed(W["seed"], rank), n_dir, nrhs, K, np.arange(p * nf, (p + 1) * nf))
             x[p] = torch.from_numpy(rows.astype(cdt).reshape(2, nrhs, K[2], K[1], K[0])).to("cuda")
     y = torch.empty_like(x)
     io_bytes = x.numel() * x.element_size()
@@ -401,11 +401,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1) / steps
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ms, dist, "cuda")
 
     units = _units(n, n_dir, nrhs)
     clocks = ClockSampler(local)
@@ -414,7 +410,7 @@ def main():
     clk = clocks.stop()
     for h in plans.values():
         assert F.fmmfft_poll_status(h) == 0
-    value = {name: world * units / (t * 1e-3) / 1e9 for name, t in ms.items()}
+    value = {name: job_throughput(units, world, t * 1e-3) / 1e9 for name, t in ms.items()}
 
     # per-stage device times (CUDA events on the launch stream, between kernels)
     stage = {}
@@ -441,12 +437,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(ne):
             F.fmmfft_translate_host(plans[main_arm], hin, hout, nrhs, stream)
-        e2e_s = (time.perf_counter() - t0) / ne
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * units / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / ne, dist, "cuda")
+        e2e = {"value": job_throughput(units, world, e2e_s) / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                "d2h_bytes_per_step": io_bytes}
 
     peaks, peak_src = _peaks()

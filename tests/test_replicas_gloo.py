@@ -1,0 +1,59 @@
+"""The multi-GPU bookkeeping on CPU: two `gloo` ranks in separate processes
+(the GPU runs use one process per GPU the same way).  Each rank derives its
+replica problem, times its own work, and the job throughput counts both ranks'
+work at the slower rank's time."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+from paper_2010_00520_gb300.replicas import (job_throughput, max_over_ranks, ranks_from_env,  # noqa: E402
+                                             replica_seed)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r = ranks_from_env()
+        seconds = 0.5 + r.rank                     # rank 1 is the slower one
+        worst = max_over_ranks(seconds, dist)
+        dist.barrier()
+        out[r.rank] = (r.world, r.rank, replica_seed(1002, r.rank), worst,
+                       job_throughput(1000.0, r.world, worst))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_timing_and_throughput():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    assert sorted(res) == [0, 1]
+    seeds = {res[r][2] for r in res}
+    assert len(seeds) == 2 and res[0][2] == 1002          # distinct problems, rank 0 keeps the seed
+    for r in res:
+        assert res[r][0] == world and res[r][1] == r
+        assert res[r][3] == 1.5                           # both ranks see the slowest time
+        assert res[r][4] == pytest.approx(2 * 1000.0 / 1.5)
+
+
+def test_ranks_from_env_alone_and_invalid():
+    r = ranks_from_env({})
+    assert (r.world, r.rank, r.local, r.leader) == (1, 0, 0, True)
+    with pytest.raises(ValueError):
+        ranks_from_env({"WORLD_SIZE": "2", "RANK": "2"})
+    assert max_over_ranks(3.0) == 3.0
