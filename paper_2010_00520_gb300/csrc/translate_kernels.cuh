@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
 // plain operator in place, a restored slab in the block's own scratch slot,
 // which stays resident in L2 while the block's fields use it.  Shared memory
 // holds the twiddles, half a field plane and the exchange buffers; the
-// restore's staging (tensor-core operand chunks) reuses the plane.
+// restore's staging (tensor-core operand chunks) reuses the plane.  Two FP32
+// blocks share an SM (the launch bound caps their registers at 128).
 // ---------------------------------------------------------------------------
 template <typename R, int N2, int N3>
 struct YZLLayout {
@@ -508,7 +509,7 @@ struct YZLLayout {
 };
 
 template <typename R, int N2, int N3, int FMT, bool TC>
-__global__ void __launch_bounds__(kThreads, 1) yzl_kernel(YZParams P) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(YZParams P) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw2 = reinterpret_cast<C*>(smem_raw);
