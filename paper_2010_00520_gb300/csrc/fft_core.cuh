@@ -59,6 +59,27 @@ template <typename C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
 }
 template <typename C> __device__ __forceinline__ C czero() { return mk<C>(0, 0); }
 
+// complex64 sums and differences as one packed two-lane FP32 instruction
+// (add/sub .f32x2) instead of two scalar ones
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
 // v times the table twiddle w = exp(-2 pi i m / N): S = -1 uses w, S = +1 conj(w)
 template <int S, typename C> __device__ __forceinline__ C twmul(C v, C w) {
   if constexpr (S < 0) return cmul(v, w); else return cmulc(v, w);
