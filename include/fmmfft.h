@@ -90,7 +90,9 @@ enum {
                                     big x small, small x big), FP32 accumulate;
                                     y-z planes whose sides are not multiples of
                                     64 restore on the CUDA cores in FP32     */
-  FMMFFT_PREC_C64_BF16X3 = 3     /* as above with bf16 hi/lo splits         */
+  FMMFFT_PREC_C64_BF16X3 = 3     /* as above with bf16 hi/lo splits (hi x hi +
+                                    lo x hi + hi x lo, kind::f16 products),
+                                    relative error near 2^-16 per product    */
 };
 
 /* ---- keys of fmmfft_plan_set (all before fmmfft_compress) -------------- */
@@ -134,10 +136,9 @@ typedef struct fmmfft_stats {
   int64_t device_bytes_operator; /* device bytes of the stored operator      */
   int64_t device_bytes_scratch;  /* device bytes of scratch buffers currently held */
   double setup_seconds;          /* wall time of the last fmmfft_compress    */
-  int restore_on_tensor_cores;   /* 1 when the slab restores run on the tensor
-                                    cores (FMMFFT_PREC_C64_3XTF32, y-z planes
-                                    with n2, n3 multiples of 64); 0 otherwise
-                                    (CUDA cores)                             */
+  int restore_on_tensor_cores;   /* slab restores on the tensor cores (y-z
+                                    planes with n2, n3 multiples of 64): 1 in
+                                    3xTF32, 2 in BF16x3; 0 CUDA cores         */
   int kernel_launches;           /* kernels one fmmfft_translate launches    */
   int large_planes;              /* 1 when the y-z pass keeps restored slabs
                                     in global scratch (planes too large for
@@ -250,8 +251,11 @@ int fmmfft_import_tt4d(fmmfft_plan plan, const int* ranks, const double* U1, con
  * the header comment, n_dir * 2 * nrhs * Kx * Ky * Kz complex each, must not
  * overlap.  nrhs >= 1.  The first call with a given nrhs (or a larger one than
  * before) allocates the plan's scratch; later calls allocate nothing.
- * Errors: NOT_COMPRESSED, INVALID_ARG, OOM, CUDA (launch failure), DEVICE
- * (a failure a kernel of an earlier call reported through the status word).
+ * Errors: NOT_COMPRESSED, INVALID_ARG, OOM, CUDA (launch failure).  A
+ * failure a kernel detects while running (a rank beyond its launch's shared
+ * memory, a tensor-core wait that ran out) is not a return value of this
+ * asynchronous call: it sets a bit of the plan's status word, which
+ * fmmfft_poll_status reads.
  */
 int fmmfft_translate(fmmfft_plan plan, const void* S_in, void* S_out, int nrhs, void* stream);
 

@@ -177,8 +177,8 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   a.n_stages = p->n_stages;
   for (int i = 0; i < p->n_stages; ++i) a.stages[i] = p->stages[i];
   a.status = p->d_status;
-  a.tc = fmm::tc_restore_applies(a) && p->sched.tc_slab != 0 ? 1 : 0;
-  a.tc_gemm = p->precision == FMMFFT_PREC_C64_3XTF32 && p->sched.tc_gemm != 0 ? 1 : 0;
+  a.tc = fmm::tc_restore_applies(a) && p->sched.tc_slab != 0 ? fmm::tc_kind(p->precision) : 0;
+  a.tc_gemm = p->sched.tc_gemm != 0 ? fmm::tc_kind(p->precision) : 0;
   a.xrows = p->sched.xrows;
   a.no_overlap = p->sched.no_overlap;
   fmm::plan_yz(a);
@@ -319,7 +319,7 @@ fmm::OperatorSpec spec_of(const fmmfft_plan_s* p) {
 
 bool precision_supported(const fmmfft_plan_s* p) {
   return p->precision == FMMFFT_PREC_C128 || p->precision == FMMFFT_PREC_C64 ||
-         p->precision == FMMFFT_PREC_C64_3XTF32;
+         p->precision == FMMFFT_PREC_C64_3XTF32 || p->precision == FMMFFT_PREC_C64_BF16X3;
 }
 
 bool check_supported(fmmfft_plan_s* p) {
@@ -1206,7 +1206,7 @@ int fmmfft_autotune(fmmfft_plan p, int nrhs, double budget_ms) {
   const bool stages = p->n_stages > 0;
   for (int xr : {2, 1, 4})
     for (int ts : tc_slab_applies ? std::vector<int>{-1, 0} : std::vector<int>{-1})
-      for (int tg : (stages && p->precision == FMMFFT_PREC_C64_3XTF32) ? std::vector<int>{-1, 0} : std::vector<int>{-1})
+      for (int tg : (stages && fmm::tc_kind(p->precision) != 0) ? std::vector<int>{-1, 0} : std::vector<int>{-1})
         for (int no : stages ? std::vector<int>{0, 1} : std::vector<int>{0}) {
           fmm::Schedule sc;
           sc.xrows = xr;

@@ -61,7 +61,7 @@ struct TranslateArgs {
   // compressed formats
   const SlabDesc* slab;              // device, n_dir entries
   int rmax_a, rmax_b;                // largest ra, rb over directions
-  int tc;                            // 1: slab restores on the tensor cores (3xTF32)
+  int tc;                            // slab restores on the tensor cores: 1 3xTF32, 2 BF16x3
   // large y-z planes (persistent yz kernel, slabs in global scratch)
   int large;                         // set by plan_yz
   long long slot_elems;              // scratch elements per block (set by plan_yz)
@@ -80,7 +80,7 @@ struct TranslateArgs {
   int xrows;                         // x-pass rows per block as a multiple of the
                                      // lines one block iteration covers (1, 2, 4)
   int no_overlap;                    // 1: pre-pass in line with the x pass
-  int tc_gemm;                       // pre-pass products on the tensor cores
+  int tc_gemm;                       // pre-pass products on the tensor cores: 1 3xTF32, 2 BF16x3
 };
 
 // A translation schedule: the choices fmmfft_autotune makes for a plan.
@@ -101,7 +101,9 @@ bool translate_supported(const TranslateArgs& a);
 // fits, else the large-plane one; sets a.large and a.slot_elems.  False when
 // neither fits.
 bool plan_yz(TranslateArgs& a);
-// Whether the slab restores of these args run on the tensor cores (3xTF32).
+// Tensor-core arithmetic of a precision: 1 3xTF32, 2 BF16x3, 0 none.
+int tc_kind(int precision);
+// Whether the slab restores of these args can run on the tensor cores.
 bool tc_restore_applies(const TranslateArgs& a);
 
 // Translation of a compressed plan with a caller-provided intermediate buffer

@@ -14,6 +14,11 @@
 // small*big + big*small: the dropped small*small term and the rounding of
 // `small` leave a relative error near 2^-21, the FP32 level.
 //
+// BF16 variant (template flag): the parts are bf16 (x = hi + lo, lo = the
+// bf16 rounding of x - hi), products of kind::f16 with BF16 inputs; a 32-bit
+// staging word holds two consecutive K elements, so the same staging layout
+// covers twice the K per chunk.  Relative error near 2^-16 per product.
+//
 // Operands are staged through shared memory in chunks of kTcKC along K, in
 // the no-swizzle K-major canonical layout of tcgen05: 8-row x 16-byte core
 // matrices, the 4 core matrices of a chunk's K extent adjacent (LBO = 128 B),
@@ -23,6 +28,7 @@
 // wait takes no shared-memory bandwidth from a co-resident block.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -69,6 +75,36 @@ __host__ __device__ constexpr uint32_t tc_idesc_tf32_128x128() {
          | (2u << 10)              // B format TF32
          | ((128u >> 3) << 17)     // N >> 3
          | ((128u >> 4) << 24);    // M >> 4
+}
+
+// instruction descriptor of kind::f16 with BF16 inputs, D in F32, A and B
+// K-major, M = N = 128
+__host__ __device__ constexpr uint32_t tc_idesc_bf16_128x128() {
+  return (1u << 4)                 // D format F32
+         | (1u << 7)               // A format BF16
+         | (1u << 10)              // B format BF16
+         | ((128u >> 3) << 17)     // N >> 3
+         | ((128u >> 4) << 24);    // M >> 4
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// hi and lo bf16 parts of two values, each pair packed into one word (first
+// value in the low half, the lower address)
+__device__ __forceinline__ void bf16_split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -184,82 +220,11 @@ __device__ __forceinline__ void tc_teardown(const TcState& s) {
   }
 }
 
-// C[m * ldc + n] = scale * sum_k A(m, k) B(k, n) for m < M, n < N (M, N <= 64)
-// with A(m, k), B(k, n) complex (float2) supplied by the functors.  Every
-// thread of the 256-thread block calls it.  C_GLOBAL: C is in global memory,
-// so the epilogue combines the quadrants in shared memory and writes C once,
-// coalesced; otherwise C (shared memory) is written directly, one row per lane.
-template <bool C_GLOBAL, typename FA, typename FB>
-__device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a_of, FB b_of, float2* C,
-                                           int ldc, float scale) {
+// Epilogue shared by the GEMM variants: D (128 x 128 FP32 in TMEM) to the
+// complex C tile.
+template <bool C_GLOBAL>
+__device__ __forceinline__ void tc_epilogue(TcState& s, int M, int N, float2* C, int ldc, float scale) {
   const int tid = threadIdx.x;
-  uint32_t* Ab = reinterpret_cast<uint32_t*>(s.buf);
-  uint32_t* As = Ab + kTcTileFloats;
-  uint32_t* Bb = As + kTcTileFloats;
-  uint32_t* Bs = Bb + kTcTileFloats;
-  constexpr uint32_t idesc = tc_idesc_tf32_128x128();
-  const int nchunks = (K + kTcKC - 1) / kTcKC;
-  // Element i of the first 64 rows of a chunk sits at float i of the tile:
-  // core matrix i / 32 (row group, K group), row (i % 32) / 4, column i % 4;
-  // the second 64 rows follow 1024 floats later.  Each thread owns i = tid +
-  // 256 j (j < 4); consecutive threads write consecutive words.
-  constexpr int kPer = 64 * kTcKC / 256;
-  float2 va[kPer], vb[kPer];
-  auto gather = [&](int k0) {
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int i = tid + 256 * j;
-      const int cm = i >> 5, w = i & 31;
-      const int m = (cm / (kTcKC / 4)) * 8 + (w >> 2);
-      const int gk = k0 + (cm % (kTcKC / 4)) * 4 + (w & 3);
-      va[j] = (gk < K && m < M) ? a_of(m, gk) : make_float2(0.f, 0.f);
-      vb[j] = (gk < K && m < N) ? b_of(gk, m) : make_float2(0.f, 0.f);
-    }
-  };
-  gather(0);
-  for (int ch = 0; ch < nchunks; ++ch) {
-    // stage chunk: A' rows m (real) and 64 + m (imaginary); B'^T rows n
-    // (real) and 64 + n (imaginary), K contiguous
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int o0 = tid + 256 * j, o1 = o0 + 64 * kTcKC;
-      const float2 a = va[j], b = vb[j];
-      const uint32_t arb = to_tf32(a.x), aib = to_tf32(a.y);
-      const uint32_t brb = to_tf32(b.x), bib = to_tf32(b.y);
-      Ab[o0] = arb;
-      Ab[o1] = aib;
-      As[o0] = to_tf32(a.x - __uint_as_float(arb));
-      As[o1] = to_tf32(a.y - __uint_as_float(aib));
-      Bb[o0] = brb;
-      Bb[o1] = bib;
-      Bs[o0] = to_tf32(b.x - __uint_as_float(brb));
-      Bs[o1] = to_tf32(b.y - __uint_as_float(bib));
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t ab = smem_u32(Ab), as = smem_u32(As), bb = smem_u32(Bb), bs = smem_u32(Bs);
-#pragma unroll
-      for (int ks = 0; ks < kTcKC / 8; ++ks) {
-        const uint32_t step = ks * 2 * 128;        // two core matrices along K
-        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
-        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bb + step), idesc, acc0);
-        tc_mma(s.tmem, tc_desc(as + step), tc_desc(bb + step), idesc, 1u);
-        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bs + step), idesc, 1u);
-      }
-      tc_commit(s.mbar);
-    }
-    // the next chunk's loads overlap the MMAs of this one
-    if (ch + 1 < nchunks) gather((ch + 1) * kTcKC);
-    // warp 0 polls the mbarrier (each poll is a shared-memory operation);
-    // the other warps sleep in the barrier, which also shares the outcome
-    bool timeout = false;
-    if (tid < 32) timeout = !mbar_wait(s.mbar, s.phase);
-    if (__syncthreads_or(timeout)) s.ok = false;
-    s.phase ^= 1u;
-    tc_fence_after();
-  }
   // epilogue: lanes m (warps 0, 1 and 4, 5) hold the ReA rows, lanes 64 + m
   // (warps 2, 3 and 6, 7) the ImA rows; warps w and w + 4 split the columns.
   const int w = tid >> 5, q = w & 3, half = w >> 2;
@@ -347,6 +312,164 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
     tc_fence_before();
     __syncthreads();
   }
+}
+
+// BF16x3 variant of tc_cgemm64 (see the header comment): word i of a staging
+// tile holds K elements 2 kw and 2 kw + 1 of row m, with (m, kw) placed as the
+// TF32 variant places (m, k); a chunk covers kTcKC words = 2 kTcKC elements.
+template <bool C_GLOBAL, typename FA, typename FB>
+__device__ __forceinline__ void tc_cgemm64_bf16(TcState& s, int M, int N, int K, FA a_of, FB b_of, float2* C,
+                                                int ldc, float scale) {
+  const int tid = threadIdx.x;
+  uint32_t* Ab = reinterpret_cast<uint32_t*>(s.buf);
+  uint32_t* As = Ab + kTcTileFloats;
+  uint32_t* Bb = As + kTcTileFloats;
+  uint32_t* Bs = Bb + kTcTileFloats;
+  constexpr uint32_t idesc = tc_idesc_bf16_128x128();
+  constexpr int KE = 2 * kTcKC;                    // K elements per chunk
+  const int nchunks = (K + KE - 1) / KE;
+  constexpr int kPer = 64 * kTcKC / 256;
+  float2 va[2 * kPer], vb[2 * kPer];
+  auto gather = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + 256 * j;
+      const int cm = i >> 5, w = i & 31;
+      const int m = (cm / (kTcKC / 4)) * 8 + (w >> 2);
+      const int gk = k0 + 2 * ((cm % (kTcKC / 4)) * 4 + (w & 3));
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        va[2 * j + e] = (gk + e < K && m < M) ? a_of(m, gk + e) : make_float2(0.f, 0.f);
+        vb[2 * j + e] = (gk + e < K && m < N) ? b_of(gk + e, m) : make_float2(0.f, 0.f);
+      }
+    }
+  };
+  gather(0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int o0 = tid + 256 * j, o1 = o0 + 64 * kTcKC;
+      const float2 a0 = va[2 * j], a1 = va[2 * j + 1], b0 = vb[2 * j], b1 = vb[2 * j + 1];
+      uint32_t hi, lo;
+      bf16_split2(a0.x, a1.x, hi, lo);
+      Ab[o0] = hi;
+      As[o0] = lo;
+      bf16_split2(a0.y, a1.y, hi, lo);
+      Ab[o1] = hi;
+      As[o1] = lo;
+      bf16_split2(b0.x, b1.x, hi, lo);
+      Bb[o0] = hi;
+      Bs[o0] = lo;
+      bf16_split2(b0.y, b1.y, hi, lo);
+      Bb[o1] = hi;
+      Bs[o1] = lo;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ab = smem_u32(Ab), as = smem_u32(As), bb = smem_u32(Bb), bs = smem_u32(Bs);
+#pragma unroll
+      for (int ks = 0; ks < kTcKC / 8; ++ks) {
+        const uint32_t step = ks * 2 * 128;        // two core matrices (16 bf16) along K
+        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+        tc_mma_bf16(s.tmem, tc_desc(ab + step), tc_desc(bb + step), idesc, acc0);
+        tc_mma_bf16(s.tmem, tc_desc(as + step), tc_desc(bb + step), idesc, 1u);
+        tc_mma_bf16(s.tmem, tc_desc(ab + step), tc_desc(bs + step), idesc, 1u);
+      }
+      tc_commit(s.mbar);
+    }
+    if (ch + 1 < nchunks) gather((ch + 1) * KE);
+    bool timeout = false;
+    if (tid < 32) timeout = !mbar_wait(s.mbar, s.phase);
+    if (__syncthreads_or(timeout)) s.ok = false;
+    s.phase ^= 1u;
+    tc_fence_after();
+  }
+  tc_epilogue<C_GLOBAL>(s, M, N, C, ldc, scale);
+}
+
+// C[m * ldc + n] = scale * sum_k A(m, k) B(k, n) for m < M, n < N (M, N <= 64)
+// with A(m, k), B(k, n) complex (float2) supplied by the functors.  Every
+// thread of the 256-thread block calls it.  C_GLOBAL: C is in global memory,
+// so the epilogue combines the quadrants in shared memory and writes C once,
+// coalesced; otherwise C (shared memory) is written directly, one row per lane.
+template <bool C_GLOBAL, bool BF16 = false, typename FA, typename FB>
+__device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a_of, FB b_of, float2* C,
+                                           int ldc, float scale) {
+  if constexpr (BF16) {
+    tc_cgemm64_bf16<C_GLOBAL>(s, M, N, K, a_of, b_of, C, ldc, scale);
+    return;
+  }
+  const int tid = threadIdx.x;
+  uint32_t* Ab = reinterpret_cast<uint32_t*>(s.buf);
+  uint32_t* As = Ab + kTcTileFloats;
+  uint32_t* Bb = As + kTcTileFloats;
+  uint32_t* Bs = Bb + kTcTileFloats;
+  constexpr uint32_t idesc = tc_idesc_tf32_128x128();
+  const int nchunks = (K + kTcKC - 1) / kTcKC;
+  // Element i of the first 64 rows of a chunk sits at float i of the tile:
+  // core matrix i / 32 (row group, K group), row (i % 32) / 4, column i % 4;
+  // the second 64 rows follow 1024 floats later.  Each thread owns i = tid +
+  // 256 j (j < 4); consecutive threads write consecutive words.
+  constexpr int kPer = 64 * kTcKC / 256;
+  float2 va[kPer], vb[kPer];
+  auto gather = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + 256 * j;
+      const int cm = i >> 5, w = i & 31;
+      const int m = (cm / (kTcKC / 4)) * 8 + (w >> 2);
+      const int gk = k0 + (cm % (kTcKC / 4)) * 4 + (w & 3);
+      va[j] = (gk < K && m < M) ? a_of(m, gk) : make_float2(0.f, 0.f);
+      vb[j] = (gk < K && m < N) ? b_of(gk, m) : make_float2(0.f, 0.f);
+    }
+  };
+  gather(0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    // stage chunk: A' rows m (real) and 64 + m (imaginary); B'^T rows n
+    // (real) and 64 + n (imaginary), K contiguous
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int o0 = tid + 256 * j, o1 = o0 + 64 * kTcKC;
+      const float2 a = va[j], b = vb[j];
+      const uint32_t arb = to_tf32(a.x), aib = to_tf32(a.y);
+      const uint32_t brb = to_tf32(b.x), bib = to_tf32(b.y);
+      Ab[o0] = arb;
+      Ab[o1] = aib;
+      As[o0] = to_tf32(a.x - __uint_as_float(arb));
+      As[o1] = to_tf32(a.y - __uint_as_float(aib));
+      Bb[o0] = brb;
+      Bb[o1] = bib;
+      Bs[o0] = to_tf32(b.x - __uint_as_float(brb));
+      Bs[o1] = to_tf32(b.y - __uint_as_float(bib));
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ab = smem_u32(Ab), as = smem_u32(As), bb = smem_u32(Bb), bs = smem_u32(Bs);
+#pragma unroll
+      for (int ks = 0; ks < kTcKC / 8; ++ks) {
+        const uint32_t step = ks * 2 * 128;        // two core matrices along K
+        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bb + step), idesc, acc0);
+        tc_mma(s.tmem, tc_desc(as + step), tc_desc(bb + step), idesc, 1u);
+        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bs + step), idesc, 1u);
+      }
+      tc_commit(s.mbar);
+    }
+    // the next chunk's loads overlap the MMAs of this one
+    if (ch + 1 < nchunks) gather((ch + 1) * kTcKC);
+    // warp 0 polls the mbarrier (each poll is a shared-memory operation);
+    // the other warps sleep in the barrier, which also shares the outcome
+    bool timeout = false;
+    if (tid < 32) timeout = !mbar_wait(s.mbar, s.phase);
+    if (__syncthreads_or(timeout)) s.ok = false;
+    s.phase ^= 1u;
+    tc_fence_after();
+  }
+  tc_epilogue<C_GLOBAL>(s, M, N, C, ldc, scale);
 }
 
 }  // namespace fmm

@@ -55,7 +55,7 @@ struct YZParams {
   double scale;        // restore scale 1 / (n1 n2 n3)
   int rmax_a, rmax_b;  // shared-memory capacity of the launch (ranks)
   int* status;
-  int tc;              // 1: restore on the tensor cores (TcRestore)
+  int tc;              // restore on the tensor cores (TcRestore): 1 3xTF32, 2 BF16x3
   int n_dir;
   void* slab_scratch;  // large planes: one slot of slot_elems per block
   long long slot_elems;
@@ -336,7 +336,7 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
 // ---------------------------------------------------------------------------
 constexpr size_t kTcGemmSmem = 56 * 1024;
 
-template <typename R>   // float only; a template so that every unit may include it
+template <bool BF16>   // BF16: BF16x3 products, else 3xTF32
 __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDesc* __restrict__ descs,
                                                                     int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDe
   float2* Cm = reinterpret_cast<float2*>(d.C) + (size_t)m0 * d.N + n0;
   const int K = d.K, N = d.N;
   TcState tc = tc_setup(smem_raw, &tc_bar, &tmem_slot);
-  tc_cgemm64<true>(tc, min(64, d.M - m0), min(64, d.N - n0), K, [&](int m, int k) { return A[(size_t)m * K + k]; },
+  tc_cgemm64<true, BF16>(tc, min(64, d.M - m0), min(64, d.N - n0), K, [&](int m, int k) { return A[(size_t)m * K + k]; },
                    [&](int k, int n) { return B[(size_t)k * N + n]; }, Cm, N, 1.0f);
   if (!tc.ok && threadIdx.x == 0) atomicOr(status, kStatusTcTimeout);
   tc_teardown(tc);
@@ -390,7 +390,7 @@ struct YZLayout {
   }
 };
 
-template <typename R, int N2, int N3, int FMT, bool TC>
+template <typename R, int N2, int N3, int FMT, int TC>   // TC: 0 CUDA cores, 1 3xTF32, 2 BF16x3
 __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
   using C = cx<R>;
   using LY = YZLayout<R, N2, N3>;
@@ -421,8 +421,8 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       return;
     }
     const C* H = reinterpret_cast<const C*>(d.h) + (size_t)x * d.hx;
-    if constexpr (TC) {
-      // tensor cores, 3xTF32 (tc_cgemm.cuh); factors read straight from L2
+    if constexpr (TC != 0) {
+      // tensor cores, 3xTF32 or BF16x3 (tc_cgemm.cuh); factors read straight from L2
       __shared__ uint32_t tmem_slot;
       __shared__ uint64_t tc_bar;
       TcState tc = tc_setup(work, &tc_bar, &tmem_slot);
@@ -433,15 +433,15 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
         const float2* U2 = reinterpret_cast<const float2*>(d.u2);
         // G[c][y] = sum_b H_p[x][b][c] U2[y][b]; odd pitch PY: the epilogue
         // writes one row per lane
-        tc_cgemm64<false>(tc, rb, N2, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+        tc_cgemm64<false, TC == 2>(tc, rb, N2, ra, [&](int c, int b) { return Hf[b * rb + c]; },
                    [&](int b, int y) { return U2[y * ra + b]; }, G, PY, 1.0f);
         // slab[z][y] = scale sum_c U3[z][c] G[c][y]
-        tc_cgemm64<false>(tc, N3, N2, rb, [&](int z, int c) { return U3[z * rb + c]; },
+        tc_cgemm64<false, TC == 2>(tc, N3, N2, rb, [&](int z, int c) { return U3[z * rb + c]; },
                    [&](int c, int y) { return G[c * PY + y]; }, reinterpret_cast<float2*>(Tt), PY,
                    (float)P.scale);
       } else {
         // slab[z][y] = scale sum_b R_p[z][b] T1[x][y][b]
-        tc_cgemm64<false>(tc, N3, N2, rb, [&](int z, int b) { return U3[z * rb + b]; },
+        tc_cgemm64<false, TC == 2>(tc, N3, N2, rb, [&](int z, int b) { return U3[z * rb + b]; },
                    [&](int b, int y) { return Hf[y * rb + b]; }, reinterpret_cast<float2*>(Tt), PY,
                    (float)P.scale);
       }
@@ -508,7 +508,7 @@ struct YZLLayout {
   }
 };
 
-template <typename R, int N2, int N3, int FMT, bool TC>
+template <typename R, int N2, int N3, int FMT, int TC>   // TC: 0 CUDA cores, 1 3xTF32, 2 BF16x3
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(YZParams P) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
   __shared__ uint32_t tmem_slot;
   __shared__ uint64_t tc_bar;
   TcState tc;
-  if constexpr (TC) tc = tc_setup(plane, &tc_bar, &tmem_slot);
+  if constexpr (TC != 0) tc = tc_setup(plane, &tc_bar, &tmem_slot);
   const int items = P.n1 * P.n_dir;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int x = it % P.n1, p = it / P.n1;
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
     } else {
       const SlabDesc d = P.desc[p];
       const int ra = d.ra, rb = d.rb;
-      const bool bad = ra > P.rmax_a || rb > P.rmax_b || (TC && FMT == 1 && rb > 64);
+      const bool bad = ra > P.rmax_a || rb > P.rmax_b || (TC != 0 && FMT == 1 && rb > 64);
       if (bad) {
         if (tid == 0) atomicOr(P.status, kStatusRankOverflow);
         continue;                                  // uniform over the block
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
       const C* U2 = reinterpret_cast<const C*>(d.u2);
       const C* U3 = reinterpret_cast<const C*>(d.u3);
       __syncthreads();                             // previous item done with slot and plane
-      if constexpr (TC) {
+      if constexpr (TC != 0) {
         const float2* Hf = reinterpret_cast<const float2*>(H);
         const float2* U2f = reinterpret_cast<const float2*>(U2);
         const float2* U3f = reinterpret_cast<const float2*>(U3);
@@ -555,17 +555,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
         float2* Sf = reinterpret_cast<float2*>(slot);
         if constexpr (FMT == 1) {
           for (int y0 = 0; y0 < N2; y0 += 64)
-            tc_cgemm64<true>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+            tc_cgemm64<true, TC == 2>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
                        [&](int b, int y) { return U2f[(y0 + y) * ra + b]; }, Gf + y0, N2, 1.0f);
           for (int z0 = 0; z0 < N3; z0 += 64)
             for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64<true>(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
+              tc_cgemm64<true, TC == 2>(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
                          [&](int c, int y) { return Gf[c * N2 + y0 + y]; }, Sf + (size_t)z0 * N2 + y0, N2,
                          (float)P.scale);
         } else {
           for (int z0 = 0; z0 < N3; z0 += 64)
             for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64<true>(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
+              tc_cgemm64<true, TC == 2>(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
                          [&](int b, int y) { return Hf[(y0 + y) * rb + b]; }, Sf + (size_t)z0 * N2 + y0, N2,
                          (float)P.scale);
         }
@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
     }
     yz_fields<R, N2, N3, 1>(P, x, p, plane, xs, tw2, tw3, op, N2);
   }
-  if constexpr (TC) {
+  if constexpr (TC != 0) {
     if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
     tc_teardown(tc);
   }

@@ -99,8 +99,12 @@ static size_t yz_smem_any(int n2, int n3, int fmt, int ra, int rb, bool tc) {
   }
 }
 
+int tc_kind(int precision) {
+  return precision == FMMFFT_PREC_C64_3XTF32 ? 1 : (precision == FMMFFT_PREC_C64_BF16X3 ? 2 : 0);
+}
+
 bool tc_restore_applies(const TranslateArgs& a) {
-  return a.precision == FMMFFT_PREC_C64_3XTF32 && a.yz_fmt != 0 && a.n[1] % 64 == 0 && a.n[2] % 64 == 0 &&
+  return tc_kind(a.precision) != 0 && a.yz_fmt != 0 && a.n[1] % 64 == 0 && a.n[2] % 64 == 0 &&
          (a.yz_fmt == 2 || a.rmax_b <= 64);
 }
 
@@ -220,8 +224,11 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   if (tc_gemm) {
     static bool configured = false;
     if (!configured) {
-      e = cudaFuncSetAttribute(cgemm_batched_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(cgemm_batched_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTcGemmSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cgemm_batched_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kTcGemmSmem);
       if (e != cudaSuccess) return e;
       configured = true;
     }
@@ -229,7 +236,10 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   for (int i = 0; i < a.n_stages; ++i) {
     const GemmStage& g = a.stages[i];
     dim3 grid((g.max_n + kGemmT - 1) / kGemmT, (g.max_m + kGemmT - 1) / kGemmT, g.batch);
-    if (tc_gemm && sizeof(R) == 4) cgemm_batched_tc_kernel<float><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status);
+    if (tc_gemm && sizeof(R) == 4 && a.tc_gemm == 2)
+      cgemm_batched_tc_kernel<true><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status);
+    else if (tc_gemm && sizeof(R) == 4)
+      cgemm_batched_tc_kernel<false><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status);
     else cgemm_batched_kernel<R><<<grid, kThreads, 0, ps>>>(g.desc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -7,7 +7,7 @@
 
 namespace fmm {
 
-template <typename R, int N2, int N3, int FMT, bool TC>
+template <typename R, int N2, int N3, int FMT, int TC>
 cudaError_t launch_yz_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
   static size_t configured = 0;
   auto kern = yz_kernel<R, N2, N3, FMT, TC>;
@@ -23,9 +23,10 @@ cudaError_t launch_yz_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t
 template <typename R, int N2, int N3, int FMT>
 cudaError_t launch_yz_inst(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
   if constexpr (TcRestore<R, N2, N3, FMT>::available) {
-    if (P.tc) return launch_yz_tc<R, N2, N3, FMT, true>(P, grid, smem, s);
+    if (P.tc == 1) return launch_yz_tc<R, N2, N3, FMT, 1>(P, grid, smem, s);
+    if (P.tc == 2) return launch_yz_tc<R, N2, N3, FMT, 2>(P, grid, smem, s);
   }
-  return launch_yz_tc<R, N2, N3, FMT, false>(P, grid, smem, s);
+  return launch_yz_tc<R, N2, N3, FMT, 0>(P, grid, smem, s);
 }
 
 template <typename R, int FMT, int N2>
@@ -54,7 +55,7 @@ cudaError_t launch_yz_fmt(const YZParams& P, int n2, int n3, dim3 grid, size_t s
   }
 }
 
-template <typename R, int N2, int N3, int FMT, bool TC>
+template <typename R, int N2, int N3, int FMT, int TC>
 cudaError_t launch_yzl_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
   static size_t configured = 0;
   auto kern = yzl_kernel<R, N2, N3, FMT, TC>;
@@ -70,9 +71,10 @@ cudaError_t launch_yzl_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_
 template <typename R, int N2, int N3, int FMT>
 cudaError_t launch_yzl_inst(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
   if constexpr (TcRestore<R, N2, N3, FMT>::available) {
-    if (P.tc) return launch_yzl_tc<R, N2, N3, FMT, true>(P, grid, smem, s);
+    if (P.tc == 1) return launch_yzl_tc<R, N2, N3, FMT, 1>(P, grid, smem, s);
+    if (P.tc == 2) return launch_yzl_tc<R, N2, N3, FMT, 2>(P, grid, smem, s);
   }
-  return launch_yzl_tc<R, N2, N3, FMT, false>(P, grid, smem, s);
+  return launch_yzl_tc<R, N2, N3, FMT, 0>(P, grid, smem, s);
 }
 
 // Large-plane shapes (slab and plane do not fit shared memory together).

@@ -239,9 +239,10 @@ def test_invalid_calls_return_errors(native, cuda):
         F.fmmfft_plan_destroy(h)
 
 
-def test_unsupported_precision_is_reported(native, cuda):
+def test_unsupported_size_is_reported(native, cuda):
+    """A z extent of 256 (Kz = 128) is outside the compiled y/z kernels."""
     F = native
-    h = _plan(F, (4, 4, 4), 2, 3, 1, 1e-3, prec=F.FMMFFT_PREC_C64_BF16X3)
+    h = _plan(F, (4, 4, 128), 2)
     try:
         with pytest.raises(F.FmmfftError) as e:
             F.fmmfft_compress(h)
