@@ -88,9 +88,23 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
   C* dst = reinterpret_cast<C*>(P.dst);
   for (int i = threadIdx.x; i < N1; i += kThreads) tw[i] = reinterpret_cast<const C*>(P.tw)[i];
   const int half = N1 / 2;
-  for (int i = threadIdx.x; i < nr * half; i += kThreads) {
-    const int r = i / half, x = i - r * half;
-    Q[r * PX + x] = (x < P.Kx) ? src[(size_t)r * P.Kx + x] : czero<C>();
+  // batches of kLd loads per thread are issued before their shared-memory
+  // stores, so that several global loads are in flight per thread
+  constexpr int kLd = 8;
+  for (int i0 = threadIdx.x; i0 < nr * half; i0 += kLd * kThreads) {
+    C v[kLd];
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int i = i0 + j * kThreads;
+      const int r = i / half, x = i - r * half;
+      v[j] = (i < nr * half && x < P.Kx) ? src[(size_t)r * P.Kx + x] : czero<C>();
+    }
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int i = i0 + j * kThreads;
+      const int r = i / half, x = i - r * half;
+      if (i < nr * half) Q[r * PX + x] = v[j];
+    }
   }
   __syncthreads();
   TeamPos<N1> tp;
