@@ -105,9 +105,16 @@ enum {
   FMMFFT_KEY_PREFACTOR = 5,      /* 0: c = 1 (default); 1: c = -k^2 eta/(16 pi^2) (Eq. 7) */
   FMMFFT_KEY_TRUNC_RULE = 6,     /* 0: discarded-energy rule (default);
                                     1: normalised singular value < gamma/sqrt(d) */
-  FMMFFT_KEY_PROFILE = 7         /* 1: record CUDA events between the kernels of
+  FMMFFT_KEY_PROFILE = 7,        /* 1: record CUDA events between the kernels of
                                     each translation (fmmfft_stage_times); may
                                     be changed at any time                      */
+  FMMFFT_KEY_EPS_R_RE = 8,       /* relative permittivity of the medium, real
+                                    part (> 0, default 1): k = k0 sqrt(eps_r),
+                                    eta = eta0 / sqrt(eps_r) in Eq. 7 (Sec. III.A.5,
+                                    Table IV)                                   */
+  FMMFFT_KEY_EPS_R_IM = 9        /* imaginary part (<= 0, default 0; a lossy
+                                    medium under the e^{j omega t} convention,
+                                    eps_r = eps' - j sigma / (omega eps0))      */
 };
 
 /* Stages of one translation, in launch order (fmmfft_stage_times). */
@@ -154,7 +161,8 @@ typedef struct fmmfft_stats {
  * Create a plan (host-only; touches no GPU).
  *   Nx, Ny, Nz  boxes per axis, each in [2, 128]        (Sec. II.A, K_x K_y K_z)
  *   a           box edge length (same length unit as 1/k0), > 0
- *   k0          real wavenumber, > 0 (2 pi / wavelength)
+ *   k0          free-space wavenumber, > 0 (2 pi / wavelength); the medium's
+ *               permittivity is set with FMMFFT_KEY_EPS_R_RE / _IM
  *   L           multipole count, 0 <= L <= 64            (Sec. II.A)
  *   format      FMMFFT_FORMAT_*; decomp FMMFFT_DECOMP_*; format NONE needs
  *               decomp NONE and vice versa; H-Tucker needs format 4D.
@@ -324,6 +332,20 @@ int fmmfft_compress_direction_host(fmmfft_plan plan, int p, int* ranks_out, doub
  * ((p * n1 + x) * n2 + y) * n3 + z.  INVALID_ARG for format NONE.
  */
 int fmmfft_compress_host(fmmfft_plan plan, int* ranks_out, double* restored_out);
+/* On a plan not yet compressed, fmmfft_compress_host also records the
+ * statistics of this host compression for fmmfft_plan_stats: ranks,
+ * elements_plain / elements_compressed / saving and setup_seconds. */
+
+/*
+ * The multipole count L of the excess-bandwidth rule (Sec. II.A) for boxes of
+ * edge a in a medium of relative permittivity eps_re + j eps_im:
+ *   L = floor(x + 1.8 digits^(2/3) x^(1/3)),  x = 2 |k| a sqrt(3)/2,
+ *   |k| = k0 |sqrt(eps_r)|,
+ * digits the accurate digits of the FMM approximation (the paper's Gamma term
+ * read as a digit count).  Host-only.  INVALID_ARG unless a, k0, eps_re,
+ * digits > 0 and eps_im <= 0.
+ */
+int fmmfft_multipole_count(double a, double k0, double eps_re, double eps_im, double digits, int* L_out);
 
 /*
  * Batches of independent translations (many FMM-FFT instances with uneven

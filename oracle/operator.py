@@ -7,6 +7,10 @@ a), with R = a |Delta| and R^ = Delta / |Delta|:
 
     T_p(Delta) = c * sum_{l=0}^{L} (-j)^l (2l + 1) h_l^(2)(k R) P_l(R^ . k_p)
 
+k is the wavenumber of the medium, k = k0 sqrt(eps_r) for a free-space
+wavenumber k0 and relative permittivity eps_r (complex with Im eps_r < 0 in a
+lossy medium, Sec. III.A.5 and Table IV), and eta = eta0 / sqrt(eps_r).
+
 Readings (the paper is ambiguous or silent here):
   * the sum starts at l = 0 (the printed lower limit 1 drops the monopole term
     that the plane-wave expansion of the Green's function needs);
@@ -48,17 +52,25 @@ def near_mask(dx, dy, dz, rule: str = "chebyshev", kappa: float = 4.0):
     return m | ((dx == 0) & (dy == 0) & (dz == 0))
 
 
-def prefactor_value(k0: complex, kind: str = "unit") -> complex:
+def medium_wavenumber(k0: float, eps_r: complex = 1.0) -> complex:
+    """k = k0 sqrt(eps_r), principal root (Im k <= 0 for Im eps_r <= 0)."""
+    eps = complex(eps_r)
+    return k0 * np.sqrt(eps) if eps.imag != 0 else k0 * np.sqrt(eps.real)
+
+
+def prefactor_value(k0: float, kind: str = "unit", eps_r: complex = 1.0) -> complex:
     if kind == "unit":
         return 1.0
     if kind == "paper":
-        return -(k0 ** 2) * ETA0 / (16.0 * np.pi ** 2)
+        k = medium_wavenumber(k0, eps_r)
+        eta = ETA0 / np.sqrt(complex(eps_r)) if complex(eps_r).imag != 0 else ETA0 / np.sqrt(complex(eps_r).real)
+        return -(k ** 2) * eta / (16.0 * np.pi ** 2)
     raise ValueError(f"unknown prefactor {kind!r}")
 
 
 def operator_at(khat, dx, dy, dz, a: float, k0: float, L: int,
                 near_rule: str = "chebyshev", prefactor: str = "unit",
-                kappa: float = 4.0):
+                kappa: float = 4.0, eps_r: complex = 1.0):
     """T(k, Delta) of Eq. 7 at arbitrary integer offsets (broadcast arrays).
 
     khat: (3,) unit vector.  Returns complex128 with the offsets' shape.
@@ -73,22 +85,22 @@ def operator_at(khat, dx, dy, dz, a: float, k0: float, L: int,
     d2f = d2[far]
     # Hankel values depend only on |Delta|^2: evaluate once per distinct value
     uniq, inv = np.unique(d2f, return_inverse=True)
-    kr = k0 * a * np.sqrt(uniq.astype(np.float64))
+    kr = medium_wavenumber(k0, eps_r) * a * np.sqrt(uniq.astype(np.float64))
     h = spherical_hankel2_all(L, kr)[:, inv]                  # (L+1, n_far)
     dist = np.sqrt(d2f.astype(np.float64))
     cosang = (khat[0] * dx[far] + khat[1] * dy[far] + khat[2] * dz[far]) / dist
     P = legendre_all(L, cosang)                                # (L+1, n_far)
     l = np.arange(L + 1)
     coef = ((-1j) ** l) * (2 * l + 1)
-    out[far] = prefactor_value(k0, prefactor) * np.einsum("l,ln,ln->n", coef, h, P)
+    out[far] = prefactor_value(k0, prefactor, eps_r) * np.einsum("l,ln,ln->n", coef, h, P)
     return out
 
 
-def operator_grid(khat, K, a, k0, L, near_rule="chebyshev", prefactor="unit", kappa=4.0):
+def operator_grid(khat, K, a, k0, L, near_rule="chebyshev", prefactor="unit", kappa=4.0, eps_r=1.0):
     """T_p(Delta) on the full offset grid, shape (2Kx-1, 2Ky-1, 2Kz-1), index d + K - 1."""
     ax = offset_axes(K)
     dx, dy, dz = np.meshgrid(*ax, indexing="ij")
-    return operator_at(khat, dx, dy, dz, a, k0, L, near_rule, prefactor, kappa)
+    return operator_at(khat, dx, dy, dz, a, k0, L, near_rule, prefactor, kappa, eps_r)
 
 
 def embed(Tgrid, K, n):
@@ -99,7 +111,7 @@ def embed(Tgrid, K, n):
     return out
 
 
-def fft_operator(khat, K, n, a, k0, L, near_rule="chebyshev", prefactor="unit", kappa=4.0):
+def fft_operator(khat, K, n, a, k0, L, near_rule="chebyshev", prefactor="unit", kappa=4.0, eps_r=1.0):
     """FFT'ed translation operator T~_p = FFT3(embed(T_p)) for one direction."""
-    T = operator_grid(khat, K, a, k0, L, near_rule, prefactor, kappa)
+    T = operator_grid(khat, K, a, k0, L, near_rule, prefactor, kappa, eps_r)
     return _fft.fftn(embed(T, K, n), axes=(0, 1, 2))

@@ -41,6 +41,8 @@ class Plan:
     nphi_rule: str = "baseline"
     near_rule: str = "chebyshev"
     prefactor: str = "unit"
+    kappa: float = 4.0
+    eps_r: complex = 1.0  # relative permittivity of the medium (Sec. III.A.5)
 
     @property
     def n(self):
@@ -59,7 +61,7 @@ def operators(plan: Plan, dirs=None) -> list:
     kh = plan.directions()
     idx = range(len(kh)) if dirs is None else dirs
     return [fft_operator(kh[p], plan.K, plan.n, plan.a, plan.k0, plan.L,
-                         plan.near_rule, plan.prefactor) for p in idx]
+                         plan.near_rule, plan.prefactor, plan.kappa, plan.eps_r) for p in idx]
 
 
 def stack4d(Thats) -> np.ndarray:

@@ -9,9 +9,16 @@ stable direction:
     sum_{l>=0} (2l + 1) j_l(x)^2 = 1, which holds for every x and so avoids
     the cancellation that a j_0 = sin(x)/x normalisation suffers at x = m pi.
 Both families satisfy f_{l+1}(x) = (2l + 1)/x f_l(x) - f_{l-1}(x).
+For a complex argument z (a lossy medium, Sec. III.A.5: Im z < 0) h_l^(2) is
+taken from its terminating series in 1/z,
+    h_l^(2)(z) = e^{-iz} sum_{k=0}^{l} (-i)^{k-l-1} a_k(l) / z^{k+1},
+    a_k(l) = (l + k)! / (2^k k! (l - k)!),
+which never forms j_l and y_l (both of size e^{|Im z|} there, cancelling).
 P_l(t) by Bonnet's recurrence (l + 1) P_{l+1} = (2l + 1) t P_l - l P_{l-1}.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -35,12 +42,15 @@ def spherical_jn_all(lmax: int, x: np.ndarray) -> np.ndarray:
     xmax = float(np.max(flat)) if flat.size else 1.0
     lstart = int(lmax + 40 + 2 * np.ceil(xmax))
     f = np.zeros((lstart + 2, flat.size))
-    f[lstart] = 1e-200
+    # start small but far from underflow: the normalisation sums f^2, and a
+    # start near 1e-200 leaves f^2 subnormal when the recurrence grows little
+    # (small lmax, moderate x); rescale whenever a value passes 1e100
+    f[lstart] = 1e-100
     for l in range(lstart, 0, -1):
         f[l - 1] = (2 * l + 1) / flat * f[l] - f[l + 1]
-        big = np.abs(f[l - 1]) > 1e150
+        big = np.abs(f[l - 1]) > 1e100
         if np.any(big):
-            f[:, big] *= 1e-150
+            f[:, big] *= 1e-100
     ls = np.arange(lstart + 2, dtype=np.float64)[:, None]
     norm = np.sqrt(np.sum((2 * ls + 1) * f * f, axis=0))
     j = f[: lmax + 1] / norm
@@ -54,8 +64,25 @@ def spherical_jn_all(lmax: int, x: np.ndarray) -> np.ndarray:
     return j.reshape((lmax + 1,) + x.shape)
 
 
+def spherical_hankel2_series(lmax: int, z: np.ndarray) -> np.ndarray:
+    """h_0^(2)..h_lmax^(2) at complex z (Re z > 0) from the terminating series."""
+    z = np.asarray(z, dtype=np.complex128)
+    out = np.empty((lmax + 1,) + z.shape, dtype=np.complex128)
+    e = np.exp(-1j * z)
+    for l in range(lmax + 1):
+        acc = np.zeros(z.shape, dtype=np.complex128)
+        for k in range(l + 1):
+            a_k = math.factorial(l + k) / (2.0 ** k * math.factorial(k) * math.factorial(l - k))
+            acc = acc + ((-1j) ** (k - l - 1)) * a_k / z ** (k + 1)
+        out[l] = e * acc
+    return out
+
+
 def spherical_hankel2_all(lmax: int, x: np.ndarray) -> np.ndarray:
-    """h_l^(2)(x) = j_l(x) - i y_l(x) for l = 0..lmax (complex128)."""
+    """h_l^(2)(x) = j_l(x) - i y_l(x) for l = 0..lmax (complex128); complex x
+    goes through the terminating series."""
+    if np.iscomplexobj(x):
+        return spherical_hankel2_series(lmax, x)
     return spherical_jn_all(lmax, x) - 1j * spherical_yn_all(lmax, x)
 
 

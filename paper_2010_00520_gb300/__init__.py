@@ -42,6 +42,8 @@ FMMFFT_KEY_KAPPA = 4
 FMMFFT_KEY_PREFACTOR = 5
 FMMFFT_KEY_TRUNC_RULE = 6
 FMMFFT_KEY_PROFILE = 7
+FMMFFT_KEY_EPS_R_RE = 8
+FMMFFT_KEY_EPS_R_IM = 9
 FMMFFT_STAGE_RESTORE, FMMFFT_STAGE_XFWD, FMMFFT_STAGE_YZ, FMMFFT_STAGE_XINV = 0, 1, 2, 3
 FMMFFT_NUM_STAGES = 4
 
@@ -54,7 +56,7 @@ EXPORTED = (
     "fmmfft_plan_ranks", "fmmfft_translate_noalloc", "fmmfft_import_tt3d", "fmmfft_import_tucker4d",
     "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
     "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy", "fmmfft_plan_save",
-    "fmmfft_plan_load", "fmmfft_autotune", "fmmfft_batch_autotune",
+    "fmmfft_plan_load", "fmmfft_autotune", "fmmfft_batch_autotune", "fmmfft_multipole_count",
 )
 
 
@@ -120,6 +122,7 @@ def lib() -> ctypes.CDLL:
         "fmmfft_compress_direction_host": [vp, i, ip, dp],
         "fmmfft_stage_times": [vp, ctypes.POINTER(ctypes.c_float)],
         "fmmfft_plan_ranks": [vp, ip],
+        "fmmfft_multipole_count": [d, d, d, d, d, ip],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -354,6 +357,15 @@ def fmmfft_poll_status(plan) -> int:
     return v.value
 
 
+def fmmfft_multipole_count(a, k0, digits, eps_r=1.0):
+    """L of the excess-bandwidth rule (Sec. II.A) for boxes of edge a, free-space
+    wavenumber k0, relative permittivity eps_r (complex, Im <= 0)."""
+    e = complex(eps_r)
+    L = ctypes.c_int(0)
+    _check(lib().fmmfft_multipole_count(a, k0, e.real, e.imag, digits, ctypes.byref(L)), "fmmfft_multipole_count")
+    return L.value
+
+
 def fmmfft_plan_destroy(plan):
     _check(lib().fmmfft_plan_destroy(plan), "fmmfft_plan_destroy")
 
@@ -366,7 +378,8 @@ class Plan:
         keys = {"precision": FMMFFT_KEY_PRECISION, "nphi_rule": FMMFFT_KEY_NPHI_RULE,
                 "near_rule": FMMFFT_KEY_NEAR_RULE, "kappa": FMMFFT_KEY_KAPPA,
                 "prefactor": FMMFFT_KEY_PREFACTOR, "trunc_rule": FMMFFT_KEY_TRUNC_RULE,
-                "profile": FMMFFT_KEY_PROFILE}
+                "profile": FMMFFT_KEY_PROFILE, "eps_r_re": FMMFFT_KEY_EPS_R_RE,
+                "eps_r_im": FMMFFT_KEY_EPS_R_IM}
         for k, v in opts.items():
             fmmfft_plan_set(self.handle, keys[k], v)
 

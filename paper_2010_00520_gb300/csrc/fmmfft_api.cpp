@@ -27,6 +27,7 @@ struct fmmfft_plan_s {
   int precision = FMMFFT_PREC_C64;
   int nphi_rule = 0, near_rule = 0, prefactor = 0, trunc_rule = 0;
   double kappa = 4.0;
+  double eps_re = 1.0, eps_im = 0.0;   // relative permittivity of the medium
   int n_dir = 0;
   std::vector<double> khat, weights;
   bool ready = false;
@@ -311,6 +312,8 @@ fmm::OperatorSpec spec_of(const fmmfft_plan_s* p) {
   s.L = p->L;
   s.a = p->a;
   s.k0 = p->k0;
+  s.eps_re = p->eps_re;
+  s.eps_im = p->eps_im;
   s.near_rule = p->near_rule;
   s.kappa = p->kappa;
   s.prefactor = p->prefactor;
@@ -491,6 +494,14 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->profile = iv == 1;
       return FMMFFT_OK;
+    case FMMFFT_KEY_EPS_R_RE:
+      if (!(v > 0) || !std::isfinite(v)) return FMMFFT_ERR_INVALID_ARG;
+      p->eps_re = v;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_EPS_R_IM:
+      if (!(v <= 0) || !std::isfinite(v)) return FMMFFT_ERR_INVALID_ARG;
+      p->eps_im = v;
+      return FMMFFT_OK;
     default:
       return FMMFFT_ERR_INVALID_ARG;
   }
@@ -665,8 +676,16 @@ int fmmfft_import_tt4d(fmmfft_plan p, const int* ranks, const double* U1, const 
 
 int fmmfft_compress_host(fmmfft_plan p, int* ranks, double* restored) {
   if (!p || !ranks || p->format == FMMFFT_FORMAT_NONE || !format_known(p)) return FMMFFT_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
   fmm::Layout L;
   build_layout(p, L);
+  if (!p->ready) {
+    // statistics of this host compression (ranks, memory saving, set-up time)
+    adopt_layout_shape(p, L);
+    p->elements_plain = (int64_t)p->n[0] * p->n[1] * p->n[2] * p->n_dir;
+    p->elements_compressed = L.elements;
+    p->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
   if (p->format == FMMFFT_FORMAT_3D) {
     std::memcpy(ranks, L.ranks3.data(), sizeof(int) * L.ranks3.size());
   } else {
@@ -888,6 +907,14 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   return FMMFFT_OK;
 }
 
+int fmmfft_multipole_count(double a, double k0, double eps_re, double eps_im, double digits, int* L_out) {
+  if (!L_out || !(a > 0) || !(k0 > 0) || !(eps_re > 0) || !(eps_im <= 0) || !(digits > 0) ||
+      !std::isfinite(a * k0 * eps_re * eps_im * digits))
+    return FMMFFT_ERR_INVALID_ARG;
+  *L_out = fmm::multipole_count(a, k0, eps_re, eps_im, digits);
+  return FMMFFT_OK;
+}
+
 int fmmfft_plan_ranks(fmmfft_plan p, int* ranks) {
   if (!p || !ranks || !p->ready || p->format != FMMFFT_FORMAT_3D) return FMMFFT_ERR_INVALID_ARG;
   std::memcpy(ranks, p->ranks3.data(), sizeof(int) * p->ranks3.size());
@@ -929,7 +956,7 @@ int fmmfft_poll_status(fmmfft_plan p, int* device_status) {
 namespace {
 
 const char kMagic[8] = {'F', 'M', 'M', 'F', 'F', 'T', 'P', '1'};
-const uint32_t kFileVersion = 1;
+const uint32_t kFileVersion = 2;   // 2: medium permittivity after trunc_rule
 
 struct Writer {
   FILE* f;
@@ -990,6 +1017,8 @@ int fmmfft_plan_save(fmmfft_plan p, const char* path) {
   w.put<double>(p->kappa);
   w.put<int32_t>(p->prefactor);
   w.put<int32_t>(p->trunc_rule);
+  w.put<double>(p->eps_re);
+  w.put<double>(p->eps_im);
   w.put<int32_t>(p->n_dir);
   if (p->format != FMMFFT_FORMAT_NONE) {
     const fmm::Layout& L = p->layout;
@@ -1047,12 +1076,15 @@ int fmmfft_plan_load(fmmfft_plan* out, const char* path) {
   const int format = r.get<int32_t>(), decomp = r.get<int32_t>(), precision = r.get<int32_t>();
   const int nphi_rule = r.get<int32_t>(), near_rule = r.get<int32_t>();
   const double kappa = r.get<double>();
-  const int prefactor = r.get<int32_t>(), trunc_rule = r.get<int32_t>(), n_dir = r.get<int32_t>();
+  const int prefactor = r.get<int32_t>(), trunc_rule = r.get<int32_t>();
+  const double eps_re = r.get<double>(), eps_im = r.get<double>();
+  const int n_dir = r.get<int32_t>();
   fmmfft_plan p = nullptr;
   int st = r.ok ? fmmfft_plan_create(&p, K[0], K[1], K[2], a, k0, L, format, decomp, tol) : FMMFFT_ERR_IO;
   const std::pair<int, double> opts[] = {{FMMFFT_KEY_PRECISION, precision}, {FMMFFT_KEY_NPHI_RULE, nphi_rule},
                                          {FMMFFT_KEY_NEAR_RULE, near_rule},  {FMMFFT_KEY_KAPPA, kappa},
-                                         {FMMFFT_KEY_PREFACTOR, prefactor},  {FMMFFT_KEY_TRUNC_RULE, trunc_rule}};
+                                         {FMMFFT_KEY_PREFACTOR, prefactor},  {FMMFFT_KEY_TRUNC_RULE, trunc_rule},
+                                         {FMMFFT_KEY_EPS_R_RE, eps_re},      {FMMFFT_KEY_EPS_R_IM, eps_im}};
   for (const auto& o : opts)
     if (st == FMMFFT_OK) st = fmmfft_plan_set(p, o.first, o.second);
   if (st == FMMFFT_OK && p->n_dir != n_dir) st = FMMFFT_ERR_INVALID_ARG;

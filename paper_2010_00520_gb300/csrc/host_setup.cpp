@@ -93,14 +93,23 @@ void direction_grid(int L, int nphi, std::vector<double>& khat, std::vector<doub
 // ---------------------------------------------------------------------------
 // operator (Eq. 7)
 // ---------------------------------------------------------------------------
-// h_l^(2)(x), l = 0..L, by upward recurrence from the closed forms
-// h_0 = j e^{-jx}/x and h_1 = e^{-jx} (j/x^2 - 1/x); the recurrence is stable
-// for the Hankel function as a whole because |h_l| grows with l.
-static void hankel2(int L, double xv, cdouble* h) {
-  const cdouble e = std::exp(cdouble(0.0, -xv));
-  h[0] = cdouble(0.0, 1.0) * e / xv;
-  if (L >= 1) h[1] = e * (cdouble(0.0, 1.0) / (xv * xv) - 1.0 / xv);
-  for (int l = 1; l < L; ++l) h[l + 1] = ((2.0 * l + 1.0) / xv) * h[l] - h[l - 1];
+// h_l^(2)(z), l = 0..L, by upward recurrence from the closed forms
+// h_0 = j e^{-jz}/z and h_1 = e^{-jz} (j/z^2 - 1/z); the recurrence is stable
+// for the Hankel function as a whole because |h_l| grows with l.  z is
+// complex in a lossy medium (Im z < 0, the factor e^{-jz} decays); the
+// recurrence never forms j_l and y_l separately, which there are both of
+// size e^{|Im z|} and would cancel.
+static void hankel2(int L, cdouble z, cdouble* h) {
+  const cdouble e = std::exp(cdouble(0.0, -1.0) * z);
+  h[0] = cdouble(0.0, 1.0) * e / z;
+  if (L >= 1) h[1] = e * (cdouble(0.0, 1.0) / (z * z) - 1.0 / z);
+  for (int l = 1; l < L; ++l) h[l + 1] = ((2.0 * l + 1.0) / z) * h[l] - h[l - 1];
+}
+
+int multipole_count(double a, double k0, double eps_re, double eps_im, double digits) {
+  const double kabs = k0 * std::abs(std::sqrt(cdouble(eps_re, eps_im)));
+  const double x = 2.0 * kabs * a * std::sqrt(3.0) / 2.0;
+  return (int)std::floor(x + 1.8 * std::cbrt(x) * std::pow(digits, 2.0 / 3.0));
 }
 
 static bool is_near(int dx, int dy, int dz, int rule, double kappa) {
@@ -118,10 +127,12 @@ void fft_operator(const OperatorSpec& s, const double* khat, std::vector<cdouble
   // Hankel values by |d|^2, with the (-j)^l (2l+1) coefficient folded in
   std::vector<cdouble> hc((size_t)(d2max + 1) * (L + 1));
   std::vector<char> seen(d2max + 1, 0);
+  const cdouble sq = std::sqrt(cdouble(s.eps_re, s.eps_im));
+  const cdouble k = s.k0 * sq;   // wavenumber in the medium
   cdouble pref(1.0, 0.0);
   if (s.prefactor == 1) {
-    const double eta = 376.730313668;
-    pref = cdouble(-s.k0 * s.k0 * eta / (16.0 * kPiD * kPiD), 0.0);
+    const cdouble eta = 376.730313668 / sq;
+    pref = -k * k * eta / (16.0 * kPiD * kPiD);
   }
   cdouble coef[129];
   {
@@ -139,7 +150,7 @@ void fft_operator(const OperatorSpec& s, const double* khat, std::vector<cdouble
         const int d2 = dx * dx + dy * dy + dz * dz;
         if (!seen[d2]) {
           seen[d2] = 1;
-          hankel2(L, s.k0 * s.a * std::sqrt((double)d2), h.data());
+          hankel2(L, k * (s.a * std::sqrt((double)d2)), h.data());
           for (int l = 0; l <= L; ++l) hc[(size_t)d2 * (L + 1) + l] = coef[l] * h[l];
         }
         const double inv = 1.0 / std::sqrt((double)d2);

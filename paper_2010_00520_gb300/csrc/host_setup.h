@@ -26,11 +26,18 @@ struct OperatorSpec {
   int K[3];
   int n[3];
   int L;
-  double a, k0;
+  double a, k0;        // k0: free-space wavenumber
+  double eps_re, eps_im;  // relative permittivity of the medium (Sec. III.A.5);
+                          // k = k0 sqrt(eps_r), eta = eta0 / sqrt(eps_r)
   int near_rule;      // 0 Chebyshev shell max|d_i| <= 1, 1 a|d| < kappa a sqrt(3)/2
   double kappa;
   int prefactor;      // 0 unit, 1 -k^2 eta / (16 pi^2)
 };
+
+// Multipole count of the excess-bandwidth rule (Sec. II.A):
+// L = floor(2|k|R + 1.8 digits^(2/3) (2|k|R)^(1/3)), R = a sqrt(3)/2 the radius
+// of the sphere around a box, |k| = k0 |sqrt(eps_r)|.
+int multipole_count(double a, double k0, double eps_re, double eps_im, double digits);
 
 // T~_p = FFT3(embed(T_p)) for direction khat, layout [x][y][z] (z fastest).
 void fft_operator(const OperatorSpec& s, const double* khat, std::vector<cdouble>& out);

@@ -173,3 +173,36 @@ def test_tensor_core_restore_benchmark_workload(native, cuda, prec):
             assert _rel(out[p, pol, r], ref) <= tol + 1e-5
     finally:
         F.fmmfft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("eps_r", [2 - 2j, 2 - 8j])
+@pytest.mark.parametrize("fmt,dec,prec", [("none", None, 0), ("none", None, 1), ("3d", "tucker", 2),
+                                          ("4d", "htucker", 1)])
+def test_lossy_medium_translation(native, cuda, eps_r, fmt, dec, prec):
+    """Sec. III.A.5 (Table IV): operators of a lossy medium, k = k0 sqrt(eps_r),
+    through the same kernels; against the oracle's uncompressed FP64 translation
+    (plain: <= 1e-10 in complex128, <= 2e-6 in complex64; compressed at tol
+    1e-4: <= tol + 1e-5)."""
+    F, torch = native, cuda
+    K, L, nrhs, tol = (8, 6, 10), 4, 2, 1e-4
+    plan = pl.Plan(K=K, L=L, eps_r=eps_r)
+    if fmt == "none":
+        h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, 0, 0, 0.0)
+    else:
+        h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, FMT[fmt], DEC[dec], tol)
+    try:
+        e = complex(eps_r)
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, prec)
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_EPS_R_RE, e.real)
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_EPS_R_IM, e.imag)
+        F.fmmfft_compress(h)
+        S = field_spectra(91, plan.n_dir, nrhs, K)
+        out = _run(F, torch, h, S, nrhs, c128=(prec == 0))
+        ops = pl.operators(plan)
+        ref = pl.translate_with(lambda p: ops[p], S)
+        bound = {"none": 1e-10 if prec == 0 else 2e-6}.get(fmt, tol + 1e-5)
+        assert _rel(out, ref) <= bound
+        if fmt != "none":
+            assert F.fmmfft_plan_stats(h)["saving"] > 0.0
+    finally:
+        F.fmmfft_plan_destroy(h)

@@ -143,3 +143,77 @@ def test_autotune_needs_a_compressed_plan(native):
         assert e.value.status == native.FMMFFT_ERR_NOT_COMPRESSED
     finally:
         native.fmmfft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("eps_r,pref,near", [(2 - 1j, 0, 0), (2 - 8j, 1, 1), (2.0, 1, 0)])
+def test_operator_generator_matches_oracle_in_a_lossy_medium(native, eps_r, pref, near):
+    """Sec. III.A.5: the library's FP64 operator with k = k0 sqrt(eps_r) (Hankel
+    functions by upward recurrence in complex arithmetic) against the oracle's
+    (terminating series)."""
+    K, L = (6, 5, 7), 6
+    h = native.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 0, 0, 0.0)
+    try:
+        e = complex(eps_r)
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_EPS_R_RE, e.real)
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_EPS_R_IM, e.imag)
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_PREFACTOR, pref)
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_NEAR_RULE, near)
+        plan = pl.Plan(K=K, L=L, eps_r=eps_r, prefactor="paper" if pref else "unit",
+                       near_rule="kappa" if near else "chebyshev")
+        dirs = [0, 17, plan.n_dir - 1]
+        ref = pl.operators(plan, dirs)
+        for i, p in enumerate(dirs):
+            T = native.fmmfft_operator_host(h, p)
+            assert np.linalg.norm(T - ref[i]) <= 1e-11 * np.linalg.norm(ref[i])
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+def test_medium_keys_validate(native):
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, 3, 0, 0, 0.0)
+    try:
+        for key, bad in ((native.FMMFFT_KEY_EPS_R_RE, 0.0), (native.FMMFFT_KEY_EPS_R_RE, -2.0),
+                         (native.FMMFFT_KEY_EPS_R_IM, 0.5), (native.FMMFFT_KEY_EPS_R_RE, float("nan"))):
+            with pytest.raises(native.FmmfftError) as e:
+                native.fmmfft_plan_set(h, key, bad)
+            assert e.value.status == native.FMMFFT_ERR_INVALID_ARG
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_EPS_R_IM, -8.0)
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+def _printed_counts():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "direction_counts.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            a, digits, er, ei, nd = line.split()[:5]
+            rows.append((float(a), float(digits), complex(float(er), float(ei)), int(nd)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _printed_counts())
+def test_library_multipole_count_reproduces_printed_direction_counts(native, row):
+    a, digits, eps_r, n_dir = row
+    L = native.fmmfft_multipole_count(a, 2 * np.pi, digits, eps_r)
+    assert (L + 1) * (2 * L + 1) == n_dir
+    with pytest.raises(native.FmmfftError):
+        native.fmmfft_multipole_count(a, 2 * np.pi, digits, complex(eps_r.real, 1.0))
+
+
+def test_compress_host_records_statistics(native):
+    """fmmfft_compress_host on a plan not yet compressed reports its ranks and
+    memory saving (Sec. III: 1 - compressed / original) through plan_stats."""
+    K, L = (8, 8, 8), 5
+    h = native.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 3, 1, 1e-4)
+    try:
+        r, _ = native.fmmfft_compress_host(h, restored=False)
+        st = native.fmmfft_plan_stats(h)
+        n = st["n"]
+        stored = sum(int(a) * int(b) * int(c) + n[0] * int(a) + n[1] * int(b) + n[2] * int(c) for a, b, c in r)
+        assert st["elements_compressed"] == stored
+        assert st["elements_plain"] == n[0] * n[1] * n[2] * st["n_dir"]
+        assert abs(st["saving"] - (1 - stored / st["elements_plain"])) < 1e-15
+        assert list(st["max_rank"][:3]) == list(r.max(axis=0))
+    finally:
+        native.fmmfft_plan_destroy(h)

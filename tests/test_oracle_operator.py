@@ -49,6 +49,63 @@ def test_plane_wave_expansion_reproduces_green_function(X, d):
     np.testing.assert_allclose(q, np.exp(-1j * k * R) / R, rtol=1e-8)
 
 
+@pytest.mark.parametrize("eps_r,rtol", [(2 - 1j, 1e-8), (2 - 2j, 1e-8), (2 - 8j, 1e-6)])
+def test_plane_wave_expansion_in_a_lossy_medium(eps_r, rtol):
+    """Sec. III.A.5: with the complex wavenumber k = k0 sqrt(eps_r) the same
+    quadrature reproduces the lossy Green's function e^{-jk|X+d|}/|X+d|, which
+    fixes the branch of sqrt(eps_r) (decay for Im eps_r < 0) and the complex
+    Hankel function."""
+    k0 = 2 * np.pi
+    k = op.medium_wavenumber(k0, eps_r)
+    assert k.imag < 0
+    X, d = np.array([1.0, 1.5, 0.5]), np.array([0.1, -0.15, 0.2])
+    L = 24
+    kh, w = dr.direction_grid(L, "paper")
+    Xi = (X / 0.5).round().astype(int)
+    T = np.array([op.operator_at(kh[p], Xi[0], Xi[1], Xi[2], 0.5, k0, L, near_rule="kappa", kappa=0.0,
+                                 eps_r=eps_r) for p in range(len(kh))])
+    q = (-1j * k / (4 * np.pi)) * np.sum(w * np.exp(-1j * k * (kh @ d)) * T)
+    R = np.linalg.norm(X + d)
+    ref = np.exp(-1j * k * R) / R
+    assert abs(q - ref) <= rtol * abs(ref)
+
+
+def test_paper_prefactor_in_a_medium():
+    # c = -k^2 eta / (16 pi^2) with k = k0 sqrt(eps_r), eta = eta0 / sqrt(eps_r)
+    for eps in (1.0, 2.0, 2 - 8j):
+        c = op.prefactor_value(2 * np.pi, "paper", eps)
+        ref = -(2 * np.pi) ** 2 * np.sqrt(complex(eps)) * op.ETA0 / (16 * np.pi ** 2)
+        assert abs(c - ref) <= 1e-14 * abs(ref)
+
+
+def test_direction_mode_rank_is_spherical_harmonic_count():
+    """As a function of k_p, T_p is a polynomial of degree L in k_p (the Legendre
+    terms P_l(k_p . R^), l = 0..L), so the direction-mode unfolding of T_4D has
+    rank (L+1)^2, the number of spherical harmonics of degree <= L.  Table II
+    prints r4 = r3 = 225 = 15^2 for L = 14; a sum starting at l = 1 (the printed
+    lower limit of Eq. 7) would give (L+1)^2 - 1."""
+    L, K = 5, (4, 4, 4)
+    plan = pl.Plan(K=K, L=L, nphi_rule="paper", near_rule="kappa")
+    T4 = pl.stack4d(pl.operators(plan))
+    s = np.linalg.svd(T4.reshape(-1, plan.n_dir), compute_uv=False)
+    assert plan.n_dir > (L + 1) ** 2
+    assert int(np.sum(s > 1e-10 * s[0])) == (L + 1) ** 2
+    # the l = 0 term removed: one harmonic fewer
+    kh = plan.directions()
+    ax = op.offset_axes(K)
+    dx, dy, dz = np.meshgrid(*ax, indexing="ij")
+    d = np.sqrt(dx * dx + dy * dy + dz * dz)
+    far = ~op.near_mask(dx, dy, dz, "kappa")
+    h0 = np.zeros(d.shape, dtype=np.complex128)
+    h0[far] = spherical_hankel2_all(0, plan.k0 * plan.a * d[far])[0]
+    cols = []
+    for p in range(plan.n_dir):
+        T = op.operator_grid(kh[p], K, plan.a, plan.k0, L, "kappa") - h0
+        cols.append(np.fft.fftn(op.embed(T, K, plan.n)).ravel())
+    s1 = np.linalg.svd(np.stack(cols, axis=1), compute_uv=False)
+    assert int(np.sum(s1 > 1e-10 * s1[0])) == (L + 1) ** 2 - 1
+
+
 def test_dropping_monopole_breaks_expansion():
     # a summation from l = 1 (the printed lower limit) misses the Green's function
     k, L = 2 * np.pi, 16

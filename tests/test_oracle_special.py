@@ -24,6 +24,16 @@ def test_hankel2_matches_scipy(x):
         np.testing.assert_allclose(H[l], ref, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("lmax", [0, 1, 2, 3, 5])
+def test_hankel2_small_order_matches_scipy(lmax):
+    # few orders and moderate arguments: the downward recurrence grows little
+    x = np.linspace(0.3, 40.0, 397)
+    H = sf.spherical_hankel2_all(lmax, x)
+    for l in range(lmax + 1):
+        ref = sp.spherical_jn(l, x) - 1j * sp.spherical_yn(l, x)
+        np.testing.assert_allclose(H[l], ref, rtol=1e-12, atol=0)
+
+
 def test_j_at_multiples_of_pi():
     # j_0 vanishes at m*pi; the downward recurrence must still give j_l there
     x = np.pi * np.arange(1, 12)
@@ -89,3 +99,41 @@ def test_multipole_count_reproduces_printed_direction_counts(row):
     k = 2 * np.pi * np.sqrt(eps_r)
     L = dr.multipole_count(k, a, digits)
     assert (L + 1) * dr.nphi_for(L, "paper") == n_dir
+
+
+# complex arguments of a lossy medium (Sec. III.A.5, Table IV): k = k0 sqrt(eps_r)
+_LOSSY_Z = [2 * np.pi * np.sqrt(e) * 0.5 * r for e in (2 - 1j, 2 - 2j, 2 - 8j) for r in (2.0, 3.3, 9.0, 26.0)]
+
+
+@pytest.mark.parametrize("z", _LOSSY_Z + [0.7 - 0.3j, 5.0 - 0.01j])
+def test_hankel2_series_matches_high_precision_bessel(z):
+    """The terminating series against h_l^(2) = sqrt(pi/2z) (J - iY)_{l+1/2}(z)
+    evaluated by mpmath at 160 digits: J and Y are each of size e^{|Im z|} and
+    cancel to e^{-|Im z|}, about 125 of those digits at Im z = -144."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 160
+    lmax = 28
+    H = sf.spherical_hankel2_all(lmax, np.array([z], dtype=np.complex128))[:, 0]
+    zz = mp.mpc(z.real, z.imag)
+    f = mp.sqrt(mp.pi / (2 * zz))
+    half = mp.mpf(1) / 2
+    for l in range(lmax + 1):
+        ref = complex(f * (mp.besselj(l + half, zz) - 1j * mp.bessely(l + half, zz)))
+        assert abs(H[l] - ref) <= 1e-10 * abs(ref), (l, H[l], ref)
+
+
+def test_hankel2_series_on_the_real_axis_matches_scipy():
+    x = np.array([0.4, 2.0, 7.5, 14.0, 30.0, 61.0])
+    H = sf.spherical_hankel2_all(28, x.astype(np.complex128))
+    for l in range(29):
+        ref = sp.spherical_jn(l, x) - 1j * sp.spherical_yn(l, x)
+        np.testing.assert_allclose(H[l], ref, rtol=1e-10, atol=0)
+
+
+def test_hankel2_lossy_closed_forms():
+    z = np.array(_LOSSY_Z)
+    H = sf.spherical_hankel2_all(1, z)
+    np.testing.assert_allclose(H[0], 1j * np.exp(-1j * z) / z, rtol=1e-13)
+    np.testing.assert_allclose(H[1], np.exp(-1j * z) * (1j / z ** 2 - 1 / z), rtol=1e-13)
+    # decays like e^{Im z} in a lossy medium
+    assert np.all(np.abs(H[0]) <= np.exp(z.imag) / np.abs(z) * (1 + 1e-12))
