@@ -43,7 +43,8 @@ import numpy as np
 from . import (FMMFFT_FORMAT_3D, FMMFFT_FORMAT_4D, FMMFFT_FORMAT_NONE, FMMFFT_DECOMP_HTUCKER,
                FMMFFT_DECOMP_NONE, FMMFFT_DECOMP_TT, FMMFFT_DECOMP_TUCKER, FMMFFT_KEY_EPS_R_IM,
                FMMFFT_KEY_EPS_R_RE, FMMFFT_KEY_KAPPA, FMMFFT_KEY_NEAR_RULE, FMMFFT_KEY_NPHI_RULE,
-               FMMFFT_KEY_PRECISION, FMMFFT_KEY_TRUNC_RULE, FMMFFT_PREC_C64, fmmfft_compress,
+               FMMFFT_KEY_PRECISION, FMMFFT_KEY_TRUNC_RULE, FMMFFT_PREC_C64, FMMFFT_ERR_UNSUPPORTED,
+               FmmfftError, fmmfft_compress,
                fmmfft_compress_host, fmmfft_multipole_count, fmmfft_plan_create, fmmfft_plan_destroy,
                fmmfft_plan_set, fmmfft_plan_stats, fmmfft_translate)
 
@@ -174,7 +175,13 @@ def gpu_case(c: StudyCase, row: StudyRow, nrhs=1, precision=FMMFFT_PREC_C64, ste
                           ("plain", (FMMFFT_FORMAT_NONE, FMMFFT_DECOMP_NONE), 0.0)):
         h = _plan(c, L, fd, tol, precision)
         try:
-            fmmfft_compress(h)
+            try:
+                fmmfft_compress(h)
+            except FmmfftError as e:
+                if e.status != FMMFFT_ERR_UNSUPPORTED:
+                    raise
+                row.gpu = {"unsupported": str(e)}
+                return row
             times[name] = _time_translate(torch, h, x, y, nrhs, steps, warmup)
         finally:
             fmmfft_plan_destroy(h)
@@ -248,7 +255,10 @@ def table(rows) -> str:
                 f"{r.L} | {r.n_dir} | {r.n[0]} | {tuple(r.ranks)} | {100 * r.saving:.2f} | {r.setup_s:.1f} |")
         if gpu:
             g = r.gpu
-            line += f" {g['ms_compressed']:.3f} | {g['ms_plain']:.3f} | {g['overhead']:+.2f} |"
+            if "ms_compressed" in g:
+                line += f" {g['ms_compressed']:.3f} | {g['ms_plain']:.3f} | {g['overhead']:+.2f} |"
+            else:
+                line += " - | - | - |"
         out.append(line)
     return "\n".join(out)
 
