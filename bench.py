@@ -57,6 +57,7 @@ DEFAULT_WL = "tucker3d_32cube_L8_tol1e-4_2pol_4rhs"
 WL = dict(WORKLOADS[DEFAULT_WL], name=DEFAULT_WL, a=0.5, k0=2 * math.pi)
 FORMAT_NAMES = {(3, 1): "tucker3d", (3, 2): "tt3d", (4, 1): "tucker4d", (4, 2): "tt4d", (4, 3): "htucker4d",
                 (0, 0): "none"}
+FAR_NB = 16                  # basis functions per box of the far-field steps (Eqs. 4, 6)
 CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
 # version of the yz kernel the committed DRAM-traffic figure was taken on
 YZ_KERNEL_VERSION = 4
@@ -294,6 +295,8 @@ def main():
     ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "bf16x3", "fp32"],
                     help="restore arithmetic of the compressed arm: tensor cores (3xTF32 or BF16x3) or FP32 CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-farfield", action="store_true",
+                    help="skip timing the aggregation / disaggregation steps (Eqs. 4, 6)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default schedule instead of autotuning each arm before timing")
     ap.add_argument("--workload", default=DEFAULT_WL, choices=sorted(WORKLOADS),
@@ -427,6 +430,49 @@ def main():
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PROFILE, 0)
         stage[name] = {k: v / nst for k, v in zip(("restore", "xfwd", "yz", "xinv"), acc)}
 
+    # far-field steps around the translation (Eqs. 4 and 6): synthetic patterns
+    # of FAR_NB basis functions per box, the workload's spectra as B
+    farfield = None
+    if not args.no_farfield and not c128 and world == 1:
+        nb = FAR_NB
+        g = torch.Generator(device="cuda").manual_seed(W["seed"])
+        box = (K[2], K[1], K[0])
+        Pd = torch.randn((n_dir, 2, nb) + box, dtype=tdt, device="cuda", generator=g)
+        Id = torch.randn((nrhs, nb) + box, dtype=tdt, device="cuda", generator=g)
+        Ad = torch.empty_like(x)
+        Yd = torch.empty_like(Id)
+        hf = plans[main_arm]
+
+        def t_ff(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            nf = min(args.steps, 50)
+            e0.record(stream)
+            for _ in range(nf):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / nf
+
+        ms_agg = t_ff(lambda: F.fmmfft_aggregate(hf, Pd, Id, Ad, nb, nrhs, stream))
+        ms_dis = t_ff(lambda: F.fmmfft_disaggregate(hf, Pd, x, Yd, nb, nrhs, stream))
+        pk = _peaks()[0].get("hbm_gbs", 6800.0)
+        es = x.element_size()
+        b_agg = (Pd.numel() + Id.numel() + Ad.numel()) * es
+        b_dis = (Pd.numel() + x.numel() + Yd.numel()) * es
+        farfield = {"nb": nb, "patterns_bytes": Pd.numel() * es,
+                    "aggregate": {"ms": ms_agg, "algorithmic_bytes": b_agg,
+                                  "achieved_gbs": b_agg / (ms_agg * 1e-3) / 1e9,
+                                  "frac_of_hbm": b_agg / (ms_agg * 1e-3) / 1e9 / pk},
+                    "disaggregate": {"ms": ms_dis, "algorithmic_bytes": b_dis,
+                                     "achieved_gbs": b_dis / (ms_dis * 1e-3) / 1e9,
+                                     "frac_of_hbm": b_dis / (ms_dis * 1e-3) / 1e9 / pk},
+                    "far_field_matvec_ms": ms_agg + ms[main_arm] + ms_dis}
+        del Pd, Id, Ad, Yd
+
     e2e = None
     if not args.no_e2e:
         # end to end through the host-buffer entry point (pinned memory)
@@ -504,6 +550,8 @@ def main():
                          "mean_rank": [round(v, 2) for v in st["mean_rank"]]}
     if e2e is not None:
         out["e2e"] = e2e
+    if farfield is not None:
+        out["farfield"] = farfield
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = run_cpu_baseline(CPU_SAMPLE_DIRS)
     for h in plans.values():

@@ -337,6 +337,38 @@ int fmmfft_compress_host(fmmfft_plan plan, int* ranks_out, double* restored_out)
  * elements_plain / elements_compressed / saving and setup_seconds. */
 
 /*
+ * Far-field steps around the translation (Sec. II.A), for the plan's boxes
+ * (V = Kx Ky Kz, box index v = (z Ky + y) Kx + x), directions and quadrature
+ * weights, with nb basis functions per box (empty slots: zero patterns) and
+ * nrhs right-hand sides.  Device arrays, complex64 (complex128 for plans of
+ * precision FMMFFT_PREC_C128), interleaved:
+ *   patterns  P[p][c][i][v]: theta (c = 0) and phi (c = 1) far-field patterns
+ *             P^+(k_p, b_i) of basis function i of box v (Eq. 3), n_dir * 2 *
+ *             nb * V elements; P^- is their conjugate;
+ *   currents  I[r][i][v]: coefficients of the basis functions, nrhs * nb * V;
+ *   A, B      spectra [p][c][r][v] in the layout of fmmfft_translate's S_in /
+ *             S_out, n_dir * 2 * nrhs * V;
+ *   y         [r][i][v], nrhs * nb * V.
+ *
+ * fmmfft_aggregate (Eq. 4):    A[p][c][r][v] = sum_i P[p][c][i][v] I[r][i][v]
+ * fmmfft_disaggregate (Eq. 6): y[r][i][v] = sum_p w_p sum_c conj(P[p][c][i][v]) B[p][c][r][v]
+ *
+ * So aggregate -> fmmfft_translate -> disaggregate is the far-field part of the
+ * FMM-FFT matrix-vector product (the (-jk/(4 pi)) factor of the Green's
+ * function left to the caller).  Asynchronous on `stream`; the plan need not
+ * be compressed.  The first call on a plan copies its weights to the current
+ * device (8 n_dir bytes, synchronous).  The sum over directions of
+ * fmmfft_disaggregate runs in one thread per output, in direction order.
+ * Errors: INVALID_ARG (null or misaligned pointers, nb < 1, nrhs outside
+ * [1, 4096], an output overlapping an input), UNSUPPORTED (nb > 48), OOM,
+ * CUDA (launch failure).
+ */
+int fmmfft_aggregate(fmmfft_plan plan, const void* patterns, const void* currents, void* A, int nb,
+                     int nrhs, void* stream);
+int fmmfft_disaggregate(fmmfft_plan plan, const void* patterns, const void* B, void* y, int nb,
+                        int nrhs, void* stream);
+
+/*
  * The multipole count L of the excess-bandwidth rule (Sec. II.A) for boxes of
  * edge a in a medium of relative permittivity eps_re + j eps_im:
  *   L = floor(x + 1.8 digits^(2/3) x^(1/3)),  x = 2 |k| a sqrt(3)/2,

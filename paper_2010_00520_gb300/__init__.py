@@ -57,6 +57,7 @@ EXPORTED = (
     "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
     "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy", "fmmfft_plan_save",
     "fmmfft_plan_load", "fmmfft_autotune", "fmmfft_batch_autotune", "fmmfft_multipole_count",
+    "fmmfft_aggregate", "fmmfft_disaggregate",
 )
 
 
@@ -123,6 +124,8 @@ def lib() -> ctypes.CDLL:
         "fmmfft_stage_times": [vp, ctypes.POINTER(ctypes.c_float)],
         "fmmfft_plan_ranks": [vp, ip],
         "fmmfft_multipole_count": [d, d, d, d, d, ip],
+        "fmmfft_aggregate": [vp, vp, vp, vp, i, i, vp],
+        "fmmfft_disaggregate": [vp, vp, vp, vp, i, i, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -287,6 +290,18 @@ def fmmfft_batch_destroy(batch):
 def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):
     _check(lib().fmmfft_translate(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
            "fmmfft_translate")
+
+
+def fmmfft_aggregate(plan, patterns, currents, A, nb, nrhs, stream=None):
+    """Eq. 4 on the device: A[p][c][r][v] = sum_i P[p][c][i][v] I[r][i][v]."""
+    _check(lib().fmmfft_aggregate(plan, _ptr(patterns), _ptr(currents), _ptr(A), int(nb), int(nrhs),
+                                  _stream(stream)), "fmmfft_aggregate")
+
+
+def fmmfft_disaggregate(plan, patterns, B, y, nb, nrhs, stream=None):
+    """Eq. 6 on the device: y[r][i][v] = sum_p w_p sum_c conj(P[p][c][i][v]) B[p][c][r][v]."""
+    _check(lib().fmmfft_disaggregate(plan, _ptr(patterns), _ptr(B), _ptr(y), int(nb), int(nrhs),
+                                     _stream(stream)), "fmmfft_disaggregate")
 
 
 def fmmfft_translate_noalloc(plan, S_in, S_out, nrhs, stream=None):

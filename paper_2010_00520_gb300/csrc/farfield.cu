@@ -1,0 +1,204 @@
+// Aggregation (Eq. 4) and disaggregation (Eq. 6): the far-field steps on
+// either side of the translation of Eq. 5.
+//
+//   aggregation     A[p][c][r][v] = sum_{i < nb} P[p][c][i][v] I[r][i][v]
+//   disaggregation  y[r][i][v]    = sum_p w_p sum_{c in {theta, phi}} conj(P[p][c][i][v]) B[p][c][r][v]
+//
+// P holds the theta / phi far-field patterns P^+(k_p, b) of the nb basis
+// functions of every box (Eq. 3; P^- is its conjugate, Sec. II.A), I the
+// basis-function coefficients of nrhs right-hand sides, A and B field spectra
+// in the layout of the translation ([p][c][r][v]), w_p the quadrature weights
+// of the directions.  v = (z Ky + y) Kx + x runs over the Kx Ky Kz boxes.
+//
+// Both steps stream the patterns once from HBM and do a few complex
+// multiply-adds per pattern element (about 2 flop per byte), so they are
+// HBM-bound: consecutive threads take consecutive boxes, so every pattern,
+// field and coefficient access of a warp is one coalesced transaction.
+//   * aggregation: a block takes a tile of boxes and a range of directions;
+//     the tile's coefficients for up to RT right-hand sides are staged once in
+//     shared memory and reused for every direction of the range;
+//   * disaggregation: a thread takes one box, up to IT basis functions and up
+//     to RT right-hand sides and sums over all directions in registers, so the
+//     result needs no cross-block reduction and is deterministic.  The grid
+//     runs the basis-function groups of a box tile next to each other, so the
+//     field tile they all read is fetched from HBM once and served from L2.
+#include "../../include/fmmfft.h"
+#include "fft_core.cuh"
+#include "plan_internal.h"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kAggBoxes = 128;     // boxes per aggregation block (threads)
+constexpr int kDisBoxes = 128;     // boxes per disaggregation block (threads)
+constexpr int kDisIT = 4;          // basis functions per disaggregation thread
+
+template <typename R> struct FarTile;
+template <> struct FarTile<float> { static constexpr int RT = 4; };
+template <> struct FarTile<double> { static constexpr int RT = 2; };
+
+template <typename R>
+__global__ void __launch_bounds__(kAggBoxes) aggregate_kernel(const cx<R>* __restrict__ P,
+                                                              const cx<R>* __restrict__ I,
+                                                              cx<R>* __restrict__ A, int64_t V, int nb,
+                                                              int nrhs, int n_dir, int dirs_per_block) {
+  using C = cx<R>;
+  constexpr int RT = FarTile<R>::RT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sI = reinterpret_cast<C*>(smem_raw);   // [RT][nb][kAggBoxes]
+  const int t = threadIdx.x;
+  const int64_t v = (int64_t)blockIdx.x * kAggBoxes + t;
+  const int r0 = blockIdx.z * RT;
+  const int nr = min(RT, nrhs - r0);
+  for (int r = 0; r < RT; ++r)
+    for (int i = 0; i < nb; ++i)
+      sI[(r * nb + i) * kAggBoxes + t] =
+          (r < nr && v < V) ? I[((int64_t)(r0 + r) * nb + i) * V + v] : czero<C>();
+  __syncthreads();
+  if (v >= V) return;
+  const int p0 = blockIdx.y * dirs_per_block;
+  const int p1 = min(n_dir, p0 + dirs_per_block);
+  // two directions x two polarisations (4 pattern rows) per step, four basis
+  // functions at a time: 16 independent pattern loads in flight per thread,
+  // since the staged coefficients allow only about 14 warps per SM
+  for (int p = p0; p < p1; p += 2) {
+    const int rows = p + 1 < p1 ? 4 : 2;
+    const C* Pr = P + ((int64_t)p * 2 * nb) * V + v;   // row q = 2 (p' - p) + c starts at q nb V
+    C acc[4][RT];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < RT; ++r) acc[q][r] = czero<C>();
+    for (int i = 0; i < nb; i += 4) {
+      C pv[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          pv[q][u] = (q < rows && i + u < nb) ? Pr[((int64_t)q * nb + i + u) * V] : czero<C>();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (i + u >= nb) break;
+        C iv[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) iv[r] = sI[(r * nb + i + u) * kAggBoxes + t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < RT; ++r) cfma(acc[q][r], pv[q][u], iv[r]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= rows) break;
+      C* Ac = A + ((int64_t)(p * 2 + q) * nrhs + r0) * V + v;
+#pragma unroll
+      for (int r = 0; r < RT; ++r)
+        if (r < nr) Ac[(int64_t)r * V] = acc[q][r];
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kDisBoxes) disaggregate_kernel(const cx<R>* __restrict__ P,
+                                                                 const cx<R>* __restrict__ B,
+                                                                 const double* __restrict__ w,
+                                                                 cx<R>* __restrict__ y, int64_t V, int nb,
+                                                                 int nrhs, int n_dir) {
+  using C = cx<R>;
+  constexpr int RT = FarTile<R>::RT;
+  const int groups = (nb + kDisIT - 1) / kDisIT;
+  const int g = blockIdx.x % groups;            // basis-function group (fastest)
+  const int64_t tile = blockIdx.x / groups;
+  const int64_t v = tile * kDisBoxes + threadIdx.x;
+  if (v >= V) return;
+  const int i0 = g * kDisIT;
+  const int ni = min(kDisIT, nb - i0);
+  const int r0 = blockIdx.y * RT;
+  const int nr = min(RT, nrhs - r0);
+  C acc[kDisIT][RT];
+#pragma unroll
+  for (int i = 0; i < kDisIT; ++i)
+#pragma unroll
+    for (int r = 0; r < RT; ++r) acc[i][r] = czero<C>();
+#pragma unroll 2
+  for (int p = 0; p < n_dir; ++p) {
+    const R wp = (R)w[p];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const C* Bc = B + ((int64_t)(p * 2 + c) * nrhs + r0) * V + v;
+      const C* Pc = P + ((int64_t)(p * 2 + c) * nb + i0) * V + v;
+      C b[RT], pc[kDisIT];
+#pragma unroll
+      for (int r = 0; r < RT; ++r) b[r] = r < nr ? Bc[(int64_t)r * V] : czero<C>();
+#pragma unroll
+      for (int i = 0; i < kDisIT; ++i) {
+        const C q = i < ni ? Pc[(int64_t)i * V] : czero<C>();
+        pc[i] = mk<C>(wp * q.x, -wp * q.y);    // w_p conj(P)
+      }
+#pragma unroll
+      for (int i = 0; i < kDisIT; ++i)
+#pragma unroll
+        for (int r = 0; r < RT; ++r) cfma(acc[i][r], pc[i], b[r]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kDisIT; ++i)
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+      if (i < ni && r < nr) y[((int64_t)(r0 + r) * nb + i0 + i) * V + v] = acc[i][r];
+}
+
+template <typename R>
+cudaError_t aggregate_t(const FarFieldArgs& a) {
+  constexpr int RT = FarTile<R>::RT;
+  const int64_t tiles = (a.V + kAggBoxes - 1) / kAggBoxes;
+  const int rchunks = (a.nrhs + RT - 1) / RT;
+  // enough blocks for a few waves of 152 SMs, each spanning as many directions
+  // as that leaves, so that the staged coefficients are reused
+  const int64_t want = 152 * 8;
+  int64_t split = (want + tiles * rchunks - 1) / (tiles * rchunks);
+  split = split < 1 ? 1 : (split > a.n_dir ? a.n_dir : split);
+  const int dirs = (int)((a.n_dir + split - 1) / split);
+  const int ychunks = (a.n_dir + dirs - 1) / dirs;
+  const size_t smem = (size_t)RT * a.nb * kAggBoxes * sizeof(cx<R>);
+  if (tiles > 0x7fffffff || ychunks > 65535 || rchunks > 65535) return cudaErrorInvalidValue;
+  auto kern = aggregate_kernel<R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((unsigned)tiles, ychunks, rchunks), kAggBoxes, smem, a.stream>>>(
+      (const cx<R>*)a.P, (const cx<R>*)a.in, (cx<R>*)a.out, a.V, a.nb, a.nrhs, a.n_dir, dirs);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t disaggregate_t(const FarFieldArgs& a) {
+  constexpr int RT = FarTile<R>::RT;
+  const int64_t tiles = (a.V + kDisBoxes - 1) / kDisBoxes;
+  const int groups = (a.nb + kDisIT - 1) / kDisIT;
+  const int rchunks = (a.nrhs + RT - 1) / RT;
+  if (tiles * groups > 0x7fffffff || rchunks > 65535) return cudaErrorInvalidValue;
+  disaggregate_kernel<R><<<dim3((unsigned)(tiles * groups), rchunks), kDisBoxes, 0, a.stream>>>(
+      (const cx<R>*)a.P, (const cx<R>*)a.in, a.w, (cx<R>*)a.out, a.V, a.nb, a.nrhs, a.n_dir);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t aggregate_smem_bytes(int nb, bool fp64) {
+  return fp64 ? (size_t)FarTile<double>::RT * nb * kAggBoxes * sizeof(double2)
+              : (size_t)FarTile<float>::RT * nb * kAggBoxes * sizeof(float2);
+}
+
+cudaError_t launch_aggregate(const FarFieldArgs& a) {
+  if (a.V == 0 || a.n_dir == 0) return cudaSuccess;
+  return a.fp64 ? aggregate_t<double>(a) : aggregate_t<float>(a);
+}
+
+cudaError_t launch_disaggregate(const FarFieldArgs& a) {
+  if (a.V == 0) return cudaSuccess;
+  return a.fp64 ? disaggregate_t<double>(a) : disaggregate_t<float>(a);
+}
+
+}  // namespace fmm

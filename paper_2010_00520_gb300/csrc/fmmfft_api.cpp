@@ -1,4 +1,5 @@
 // C ABI of the translation library: plan life cycle, set-up, translation.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -46,6 +47,7 @@ struct fmmfft_plan_s {
   size_t slabs_bytes = 0;
   int large_grid = 0;           // blocks of the persistent large-plane kernel
   void* d_inter = nullptr;
+  void* d_weights = nullptr;   // quadrature weights on the device (far-field steps)
   size_t inter_bytes = 0;
   void* d_io = nullptr;       // device copies for fmmfft_translate_host
   size_t io_bytes = 0;
@@ -468,6 +470,7 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
     case FMMFFT_KEY_NPHI_RULE:
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->nphi_rule = iv;
+      free_dev(p->d_weights);
       {
         const int nphi = iv == 0 ? 2 * (p->L + 1) : 2 * p->L + 1;
         p->n_dir = (p->L + 1) * nphi;
@@ -907,6 +910,79 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   return FMMFFT_OK;
 }
 
+namespace {
+
+// Shared checks of the far-field entry points; fills the launch arguments.
+int farfield_args(fmmfft_plan p, const void* P, const void* in, void* out, int nb, int nrhs, void* stream,
+                  size_t in_elems_per_box, size_t out_elems_per_box, fmm::FarFieldArgs& a) {
+  if (!p || !P || !in || !out || nb < 1 || nrhs < 1 || nrhs > 4096) return FMMFFT_ERR_INVALID_ARG;
+  if (nb > fmm::kFarFieldMaxNb) return FMMFFT_ERR_UNSUPPORTED;
+  const bool fp64 = p->precision == FMMFFT_PREC_C128;
+  const size_t es = fp64 ? 16 : 8;
+  const size_t V = (size_t)p->K[0] * p->K[1] * p->K[2];
+  if (((uintptr_t)P | (uintptr_t)in | (uintptr_t)out) % es) return FMMFFT_ERR_INVALID_ARG;
+  const char* o0 = (const char*)out;
+  const size_t ob = out_elems_per_box * V * es;
+  const void* srcs[2] = {P, in};
+  const size_t sb[2] = {(size_t)p->n_dir * 2 * nb * V * es, in_elems_per_box * V * es};
+  for (int k = 0; k < 2; ++k) {
+    const char* s0 = (const char*)srcs[k];
+    if (s0 < o0 + ob && o0 < s0 + sb[k]) return FMMFFT_ERR_INVALID_ARG;   // output aliases an input
+  }
+  if (!p->d_weights) {
+    void* w = nullptr;
+    int st = dev_alloc(&w, sizeof(double) * (size_t)std::max(p->n_dir, 1));
+    if (st != FMMFFT_OK) return st;
+    if (cudaMemcpy(w, p->weights.data(), sizeof(double) * p->n_dir, cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_dev(w);
+      cudaGetLastError();
+      return FMMFFT_ERR_CUDA;
+    }
+    p->d_weights = w;
+  }
+  a.P = P;
+  a.in = in;
+  a.out = out;
+  a.w = (const double*)p->d_weights;
+  a.V = (int64_t)V;
+  a.nb = nb;
+  a.nrhs = nrhs;
+  a.n_dir = p->n_dir;
+  a.fp64 = fp64;
+  a.stream = (cudaStream_t)stream;
+  return FMMFFT_OK;
+}
+
+}  // namespace
+
+int fmmfft_aggregate(fmmfft_plan p, const void* patterns, const void* currents, void* A, int nb, int nrhs,
+                     void* stream) {
+  fmm::FarFieldArgs a;
+  int st = farfield_args(p, patterns, currents, A, nb, nrhs, stream, (size_t)nb * (nrhs > 0 ? nrhs : 0),
+                         (size_t)(p ? p->n_dir : 0) * 2 * (nrhs > 0 ? nrhs : 0), a);
+  if (st != FMMFFT_OK) return st;
+  cudaError_t e = fmm::launch_aggregate(a);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
+int fmmfft_disaggregate(fmmfft_plan p, const void* patterns, const void* B, void* y, int nb, int nrhs,
+                        void* stream) {
+  fmm::FarFieldArgs a;
+  int st = farfield_args(p, patterns, B, y, nb, nrhs, stream, (size_t)(p ? p->n_dir : 0) * 2 * (nrhs > 0 ? nrhs : 0),
+                         (size_t)nb * (nrhs > 0 ? nrhs : 0), a);
+  if (st != FMMFFT_OK) return st;
+  cudaError_t e = fmm::launch_disaggregate(a);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
 int fmmfft_multipole_count(double a, double k0, double eps_re, double eps_im, double digits, int* L_out) {
   if (!L_out || !(a > 0) || !(k0 > 0) || !(eps_re > 0) || !(eps_im <= 0) || !(digits > 0) ||
       !std::isfinite(a * k0 * eps_re * eps_im * digits))
@@ -1313,6 +1389,7 @@ int fmmfft_plan_destroy(fmmfft_plan p) {
   release_operator(p);
   free_dev(p->d_inter);
   free_dev(p->d_io);
+  free_dev(p->d_weights);
   for (auto& ev : p->events)
     if (ev) cudaEventDestroy(ev);
   if (p->side) {

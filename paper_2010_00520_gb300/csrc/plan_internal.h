@@ -120,4 +120,24 @@ int plan_intermediate(fmmfft_plan p, int nrhs, void* stream, void** inter, size_
 // Stream that fmmfft_poll_status synchronises for this plan.
 void plan_set_last_stream(fmmfft_plan p, void* stream);
 
+// Aggregation (Eq. 4) and disaggregation (Eq. 6), farfield.cu.  P: patterns
+// [n_dir][2][nb][V]; aggregation reads `in` = coefficients [nrhs][nb][V] and
+// writes `out` = spectra [n_dir][2][nrhs][V]; disaggregation reads `in` =
+// spectra and the weights w (n_dir doubles) and writes `out` = [nrhs][nb][V].
+// Complex64 (float2) or, with fp64, complex128 (double2) elements.
+struct FarFieldArgs {
+  const void* P = nullptr;
+  const void* in = nullptr;
+  void* out = nullptr;
+  const double* w = nullptr;
+  int64_t V = 0;
+  int nb = 0, nrhs = 0, n_dir = 0;
+  bool fp64 = false;
+  cudaStream_t stream = nullptr;
+};
+constexpr int kFarFieldMaxNb = 48;   // basis functions per box
+size_t aggregate_smem_bytes(int nb, bool fp64);
+cudaError_t launch_aggregate(const FarFieldArgs& a);
+cudaError_t launch_disaggregate(const FarFieldArgs& a);
+
 }  // namespace fmm
