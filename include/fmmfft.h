@@ -357,8 +357,9 @@ int fmmfft_compress_host(fmmfft_plan plan, int* ranks_out, double* restored_out)
  * FMM-FFT matrix-vector product (the (-jk/(4 pi)) factor of the Green's
  * function left to the caller).  Asynchronous on `stream`; the plan need not
  * be compressed.  The first call on a plan copies its weights to the current
- * device (8 n_dir bytes, synchronous).  The sum over directions of
- * fmmfft_disaggregate runs in one thread per output, in direction order.
+ * device (8 n_dir bytes, synchronous).  fmmfft_disaggregate sums each
+ * output over four consecutive quarters of the directions and adds the four
+ * partial sums in a fixed order: results are reproducible bit for bit.
  * Errors: INVALID_ARG (null or misaligned pointers, nb < 1, nrhs outside
  * [1, 4096], an output overlapping an input), UNSUPPORTED (nb > 48), OOM,
  * CUDA (launch failure).

@@ -18,28 +18,40 @@
 //     the tile's coefficients for up to RT right-hand sides are staged once in
 //     shared memory and reused for every direction of the range;
 //   * disaggregation: a thread takes one box, up to IT basis functions and up
-//     to RT right-hand sides and sums over all directions in registers, so the
-//     result needs no cross-block reduction and is deterministic.  The grid
-//     runs the basis-function groups of a box tile next to each other, so the
-//     field tile they all read is fetched from HBM once and served from L2.
+//     to RT right-hand sides and sums a quarter of the directions in
+//     registers; the four CTAs of a thread-block cluster take the four
+//     quarters of the same outputs and add their partial sums through
+//     distributed shared memory in a fixed order (deterministic, no scratch
+//     in HBM, and four times the blocks of one sum per thread, which left
+//     the last wave of SMs two-thirds full).  The four warps of a block take
+//     four basis-function groups of the same 32 boxes, so the spectra they
+//     all read come from HBM once and from L1 after that.
+#include <cooperative_groups.h>
+
 #include "../../include/fmmfft.h"
 #include "fft_core.cuh"
 #include "plan_internal.h"
 
 namespace fmm {
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int kAggBoxes = 128;     // boxes per aggregation block (threads)
-constexpr int kDisBoxes = 128;     // boxes per disaggregation block (threads)
+constexpr int kDisBoxes = 128;     // threads per disaggregation block
+constexpr int kDisWarps = kDisBoxes / 32;   // basis-function groups per block
 constexpr int kDisIT = 4;          // basis functions per disaggregation thread
+constexpr int kDisSplit = 4;       // CTAs per cluster, each summing a quarter of the directions
 
 template <typename R> struct FarTile;
-template <> struct FarTile<float> { static constexpr int RT = 4; };
-template <> struct FarTile<double> { static constexpr int RT = 2; };
+// RT right-hand sides per thread; QR pattern rows (direction x polarisation)
+// per aggregation step
+template <> struct FarTile<float> { static constexpr int RT = 4, QR = 4; };
+template <> struct FarTile<double> { static constexpr int RT = 2, QR = 4; };
 
 template <typename R>
-__global__ void __launch_bounds__(kAggBoxes) aggregate_kernel(const cx<R>* __restrict__ P,
+__global__ void __launch_bounds__(kAggBoxes, 3) aggregate_kernel(const cx<R>* __restrict__ P,
                                                               const cx<R>* __restrict__ I,
                                                               cx<R>* __restrict__ A, int64_t V, int nb,
                                                               int nrhs, int n_dir, int dirs_per_block) {
@@ -61,19 +73,21 @@ __global__ void __launch_bounds__(kAggBoxes) aggregate_kernel(const cx<R>* __res
   const int p1 = min(n_dir, p0 + dirs_per_block);
   // two directions x two polarisations (4 pattern rows) per step, four basis
   // functions at a time: 16 independent pattern loads in flight per thread,
-  // since the staged coefficients allow only about 14 warps per SM
-  for (int p = p0; p < p1; p += 2) {
-    const int rows = p + 1 < p1 ? 4 : 2;
+  // since the staged coefficients allow only about 12 warps per SM (8 rows
+  // per step measured slower: 0.369 against 0.334 ms at 16 basis functions)
+  constexpr int QR = FarTile<R>::QR;
+  for (int p = p0; p < p1; p += QR / 2) {
+    const int rows = min(QR, 2 * (p1 - p));
     const C* Pr = P + ((int64_t)p * 2 * nb) * V + v;   // row q = 2 (p' - p) + c starts at q nb V
-    C acc[4][RT];
+    C acc[QR][RT];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < QR; ++q)
 #pragma unroll
       for (int r = 0; r < RT; ++r) acc[q][r] = czero<C>();
     for (int i = 0; i < nb; i += 4) {
-      C pv[4][4];
+      C pv[QR][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < QR; ++q)
 #pragma unroll
         for (int u = 0; u < 4; ++u)
           pv[q][u] = (q < rows && i + u < nb) ? Pr[((int64_t)q * nb + i + u) * V] : czero<C>();
@@ -84,13 +98,13 @@ __global__ void __launch_bounds__(kAggBoxes) aggregate_kernel(const cx<R>* __res
 #pragma unroll
         for (int r = 0; r < RT; ++r) iv[r] = sI[(r * nb + i + u) * kAggBoxes + t];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < QR; ++q)
 #pragma unroll
           for (int r = 0; r < RT; ++r) cfma(acc[q][r], pv[q][u], iv[r]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < QR; ++q) {
       if (q >= rows) break;
       C* Ac = A + ((int64_t)(p * 2 + q) * nrhs + r0) * V + v;
 #pragma unroll
@@ -101,53 +115,98 @@ __global__ void __launch_bounds__(kAggBoxes) aggregate_kernel(const cx<R>* __res
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kDisBoxes) disaggregate_kernel(const cx<R>* __restrict__ P,
-                                                                 const cx<R>* __restrict__ B,
-                                                                 const double* __restrict__ w,
-                                                                 cx<R>* __restrict__ y, int64_t V, int nb,
-                                                                 int nrhs, int n_dir) {
+__global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kDisBoxes)
+    disaggregate_kernel(const cx<R>* __restrict__ P, const cx<R>* __restrict__ B, const double* __restrict__ w,
+                        cx<R>* __restrict__ y, int64_t V, int nb, int nrhs, int n_dir) {
   using C = cx<R>;
   constexpr int RT = FarTile<R>::RT;
+  constexpr int NC = kDisIT * RT;               // outputs per thread
+  __shared__ C part[NC][kDisBoxes];             // this CTA's partial sums
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = (int)cluster.block_rank();      // which quarter of the directions
+  // warp j of the block takes basis-function group gs * kDisWarps + j for the
+  // same 32 boxes (one per lane): the warps of a block read the same spectra,
+  // which the first one brings into this SM's L1
   const int groups = (nb + kDisIT - 1) / kDisIT;
-  const int g = blockIdx.x % groups;            // basis-function group (fastest)
-  const int64_t tile = blockIdx.x / groups;
-  const int64_t v = tile * kDisBoxes + threadIdx.x;
-  if (v >= V) return;
+  const int gsets = (groups + kDisWarps - 1) / kDisWarps;
+  const int64_t unit = blockIdx.x / kDisSplit;
+  const int gs = (int)(unit % gsets);
+  const int64_t tile = unit / gsets;
+  const int t = threadIdx.x;
+  const int g = gs * kDisWarps + (t >> 5);
+  const int64_t v = tile * 32 + (t & 31);
   const int i0 = g * kDisIT;
   const int ni = min(kDisIT, nb - i0);
+  const bool live = v < V && ni > 0;
   const int r0 = blockIdx.y * RT;
   const int nr = min(RT, nrhs - r0);
+  const int per = (n_dir + kDisSplit - 1) / kDisSplit;
+  const int pa = s * per, pb = min(n_dir, pa + per);
   C acc[kDisIT][RT];
 #pragma unroll
   for (int i = 0; i < kDisIT; ++i)
 #pragma unroll
     for (int r = 0; r < RT; ++r) acc[i][r] = czero<C>();
-#pragma unroll 2
-  for (int p = 0; p < n_dir; ++p) {
-    const R wp = (R)w[p];
+  if (live && pa < pb) {
+    // the next direction's patterns and spectra are loaded while the current
+    // one is summed: 16 loads per thread in flight behind the arithmetic
+    C pn[2][kDisIT], bn[2][RT];
+    auto load = [&](int p) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const C* Bc = B + ((int64_t)(p * 2 + c) * nrhs + r0) * V + v;
-      const C* Pc = P + ((int64_t)(p * 2 + c) * nb + i0) * V + v;
-      C b[RT], pc[kDisIT];
+      for (int c = 0; c < 2; ++c) {
+        const C* Bc = B + ((int64_t)(p * 2 + c) * nrhs + r0) * V + v;
+        const C* Pc = P + ((int64_t)(p * 2 + c) * nb + i0) * V + v;
 #pragma unroll
-      for (int r = 0; r < RT; ++r) b[r] = r < nr ? Bc[(int64_t)r * V] : czero<C>();
+        for (int r = 0; r < RT; ++r) bn[c][r] = r < nr ? Bc[(int64_t)r * V] : czero<C>();
 #pragma unroll
-      for (int i = 0; i < kDisIT; ++i) {
-        const C q = i < ni ? Pc[(int64_t)i * V] : czero<C>();
-        pc[i] = mk<C>(wp * q.x, -wp * q.y);    // w_p conj(P)
+        for (int i = 0; i < kDisIT; ++i) pn[c][i] = i < ni ? Pc[(int64_t)i * V] : czero<C>();
       }
+    };
+    load(pa);
+    for (int p = pa; p < pb; ++p) {
+      C pc[2][kDisIT], b[2][RT];
 #pragma unroll
-      for (int i = 0; i < kDisIT; ++i)
+      for (int c = 0; c < 2; ++c) {
 #pragma unroll
-        for (int r = 0; r < RT; ++r) cfma(acc[i][r], pc[i], b[r]);
+        for (int i = 0; i < kDisIT; ++i) pc[c][i] = pn[c][i];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) b[c][r] = bn[c][r];
+      }
+      if (p + 1 < pb) load(p + 1);
+      const R wp = (R)w[p];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < kDisIT; ++i) {
+          const C q = mk<C>(wp * pc[c][i].x, -wp * pc[c][i].y);   // w_p conj(P)
+#pragma unroll
+          for (int r = 0; r < RT; ++r) cfma(acc[i][r], q, b[c][r]);
+        }
     }
   }
 #pragma unroll
   for (int i = 0; i < kDisIT; ++i)
 #pragma unroll
-    for (int r = 0; r < RT; ++r)
-      if (i < ni && r < nr) y[((int64_t)(r0 + r) * nb + i0 + i) * V + v] = acc[i][r];
+    for (int r = 0; r < RT; ++r) part[i * RT + r][t] = acc[i][r];
+  cluster.sync();
+  // CTA s of the cluster finishes the outputs k = s, s + kDisSplit, ...: the
+  // partial sums of the cluster's CTAs, read through distributed shared
+  // memory and added in CTA order (deterministic)
+  if (live) {
+    for (int k = s; k < NC; k += kDisSplit) {
+      const int i = k / RT, r = k % RT;
+      if (i >= ni || r >= nr) continue;
+      C sum = czero<C>();
+#pragma unroll
+      for (int q = 0; q < kDisSplit; ++q) {
+        const C* rp = cluster.map_shared_rank(&part[k][t], q);
+        sum = cadd(sum, *rp);
+      }
+      y[((int64_t)(r0 + r) * nb + i0 + i) * V + v] = sum;
+    }
+  }
+  // no CTA may leave while another still reads its shared memory
+  cluster.sync();
 }
 
 template <typename R>
@@ -175,11 +234,12 @@ cudaError_t aggregate_t(const FarFieldArgs& a) {
 template <typename R>
 cudaError_t disaggregate_t(const FarFieldArgs& a) {
   constexpr int RT = FarTile<R>::RT;
-  const int64_t tiles = (a.V + kDisBoxes - 1) / kDisBoxes;
+  const int64_t tiles = (a.V + 31) / 32;
   const int groups = (a.nb + kDisIT - 1) / kDisIT;
+  const int gsets = (groups + kDisWarps - 1) / kDisWarps;
   const int rchunks = (a.nrhs + RT - 1) / RT;
-  if (tiles * groups > 0x7fffffff || rchunks > 65535) return cudaErrorInvalidValue;
-  disaggregate_kernel<R><<<dim3((unsigned)(tiles * groups), rchunks), kDisBoxes, 0, a.stream>>>(
+  if (tiles * gsets * kDisSplit > 0x7fffffff || rchunks > 65535) return cudaErrorInvalidValue;
+  disaggregate_kernel<R><<<dim3((unsigned)(tiles * gsets * kDisSplit), rchunks), kDisBoxes, 0, a.stream>>>(
       (const cx<R>*)a.P, (const cx<R>*)a.in, a.w, (cx<R>*)a.out, a.V, a.nb, a.nrhs, a.n_dir);
   return cudaGetLastError();
 }
