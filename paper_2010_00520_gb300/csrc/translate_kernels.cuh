@@ -349,6 +349,8 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
 // that at most four blocks share an SM and its 512 TMEM columns.
 // ---------------------------------------------------------------------------
 constexpr size_t kTcGemmSmem = 56 * 1024;
+// contraction chunk of the CUDA-core TT-like slab restore (slab_tt_chunked)
+constexpr int kRestoreKC = 64;
 
 template <bool BF16>   // BF16: BF16x3 products, else 3xTF32
 __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDesc* __restrict__ descs,
@@ -384,10 +386,15 @@ struct YZLayout {
   static constexpr size_t fixed_elems = (size_t)N3 * PY + N2 + N3;   // Tt + twiddles
   static constexpr int G = 2;                                          // fields per round
   static constexpr size_t plane_elems = (size_t)G * (N3 / 2) * PY + kWarps * XW;
-  // restore work space: Gt (rb x N2) plus, before stage B, Ht (rb x ra) and
-  // U2t (ra x N2) [FMT 1] or nothing [FMT 2]; then U3 (N3 x rb)
+  // restore work space.  FMT 1: Gt (rb x N2) plus, before stage B, Ht
+  // (rb x ra) and U2t (ra x N2), then U3 (N3 x rb).  FMT 2: one chunk of the
+  // contraction over rb, T1[x] (kRestoreKC x (N2 + 1)) and U3 (N3 x kRestoreKC)
   static size_t restore_elems(int fmt, int ra, int rb) {
-    const size_t a = (fmt == 1) ? (size_t)rb * ra + (size_t)ra * N2 : 0, b = (size_t)N3 * rb;
+    if (fmt == 2) {
+      const size_t kc = rb < kRestoreKC ? (size_t)rb : (size_t)kRestoreKC;
+      return kc * (N2 + 1) + (size_t)N3 * kc;
+    }
+    const size_t a = (size_t)rb * ra + (size_t)ra * N2, b = (size_t)N3 * rb;
     return (size_t)rb * N2 + (a > b ? a : b);
   }
   // tensor-core restore: operand chunks + mbarrier, then G (rb x (N2 + 1), FMT 1)
@@ -403,6 +410,91 @@ struct YZLayout {
     return sizeof(cx<R>) * fixed_elems + work;
   }
 };
+
+// Row tile of the CUDA-core slab products (N3 rows x N2 columns, 32 TN columns
+// per warp item): as many rows as give every warp of the block an item.
+template <int N2, int N3>
+struct SlabTile {
+  static constexpr int TN = N2 >= 64 ? 2 : 1;
+  static constexpr int NCB = (N2 + 32 * TN - 1) / (32 * TN);
+  static constexpr int TM0 = N3 * NCB / kWarps;
+  static constexpr int TM = TM0 < 1 ? 1 : (TM0 > 8 ? 8 : TM0);
+};
+
+// TT-like slab on the CUDA cores, the contraction over rb in chunks of
+// kRestoreKC staged in shared memory (any rb fits):
+//   Tt[z * PY + y] = scale * sum_b U3[z * rb + b] H[y * rb + b]
+// Every warp keeps its output tiles in registers across the chunks.
+template <int N2, int N3, typename C>
+__device__ __forceinline__ void slab_tt_chunked(int rb, const C* __restrict__ H, const C* __restrict__ U3,
+                                                C* work, C* Tt, int PY, typename real_of<C>::type scale) {
+  using T = SlabTile<N2, N3>;
+  constexpr int TM = T::TM, TN = T::TN, NCB = T::NCB;
+  constexpr int KC = kRestoreKC, GP = N2 + 1;
+  constexpr int ITEMS = ((N3 + TM - 1) / TM) * NCB;
+  constexpr int IPW = (ITEMS + kWarps - 1) / kWarps;
+  const int kcap = rb < KC ? rb : KC;
+  C* Gc = work;                  // chunk of T1[x]: Gc[b * GP + y] = H[y * rb + k0 + b]
+  C* Uc = Gc + kcap * GP;        // chunk of U3:    Uc[z * kcap + b] = U3[z * rb + k0 + b]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  C acc[IPW][TM][TN];
+#pragma unroll
+  for (int it = 0; it < IPW; ++it)
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[it][i][j] = czero<C>();
+  for (int k0 = 0; k0 < rb; k0 += KC) {
+    const int kc = rb - k0 < KC ? rb - k0 : KC;
+    __syncthreads();                               // previous chunk consumed
+    for (int i = tid; i < N2 * kc; i += kThreads) {
+      const int y = i / kc, b = i - y * kc;
+      Gc[b * GP + y] = H[(size_t)y * rb + k0 + b];
+    }
+    for (int i = tid; i < N3 * kc; i += kThreads) {
+      const int z = i / kc, b = i - z * kc;
+      Uc[z * kcap + b] = U3[(size_t)z * rb + k0 + b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IPW; ++it) {
+      const int item = w + it * kWarps;
+      if (item >= ITEMS) break;
+      const int m0 = (item / NCB) * TM, n0 = (item % NCB) * (32 * TN);
+      for (int k = 0; k < kc; ++k) {
+        C b[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const int n = n0 + lane + 32 * j;
+          b[j] = n < N2 ? Gc[k * GP + n] : czero<C>();
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          const int m = m0 + i;
+          const C a = m < N3 ? Uc[m * kcap + k] : czero<C>();
+#pragma unroll
+          for (int j = 0; j < TN; ++j) cfma(acc[it][i][j], a, b[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < IPW; ++it) {
+    const int item = w + it * kWarps;
+    if (item >= ITEMS) break;
+    const int m0 = (item / NCB) * TM, n0 = (item % NCB) * (32 * TN);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + i;
+      if (m >= N3) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + lane + 32 * j;
+        if (n < N2) Tt[m * PY + n] = mk<C>(acc[it][i][j].x * scale, acc[it][i][j].y * scale);
+      }
+    }
+  }
+}
 
 template <typename R, int N2, int N3, int FMT, int TC>   // TC: 0 CUDA cores, 1 3xTF32, 2 BF16x3
 __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
@@ -462,10 +554,12 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
       tc_teardown(tc);
     } else {
-      // CUDA cores
-      C* Gt = work;                              // rb x N2
-      C* U3s = Gt + rb * N2;                     // N3 x rb (stage B)
+      // CUDA cores; row tiles sized so that every warp has an output tile
+      using ST = SlabTile<N2, N3>;
+      const C* U3 = reinterpret_cast<const C*>(d.u3);
       if constexpr (FMT == 1) {
+        C* Gt = work;                            // rb x N2
+        C* U3s = Gt + rb * N2;                   // N3 x rb (stage B)
         C* Ht = Gt + rb * N2;                    // rb x ra
         C* U2t = Ht + rb * ra;                   // ra x N2
         const C* U2 = reinterpret_cast<const C*>(d.u2);
@@ -478,18 +572,14 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
           U2t[b * N2 + y] = U2[i];
         }
         __syncthreads();
-        block_cgemm<8, (N2 >= 64 ? 2 : 1)>(rb, N2, ra, Ht, ra, U2t, N2, Gt, N2, (R)1);
+        block_cgemm<(N2 >= 64 ? 8 : 4), ST::TN>(rb, N2, ra, Ht, ra, U2t, N2, Gt, N2, (R)1);
+        __syncthreads();
+        for (int i = tid; i < N3 * rb; i += kThreads) U3s[i] = U3[i];
+        __syncthreads();
+        block_cgemm<ST::TM, ST::TN>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
       } else {
-        for (int i = tid; i < N2 * rb; i += kThreads) {
-          const int y = i / rb, b = i - y * rb;
-          Gt[b * N2 + y] = H[i];
-        }
+        slab_tt_chunked<N2, N3>(rb, H, U3, work, Tt, PY, (R)P.scale);
       }
-      __syncthreads();
-      const C* U3 = reinterpret_cast<const C*>(d.u3);
-      for (int i = tid; i < N3 * rb; i += kThreads) U3s[i] = U3[i];
-      __syncthreads();
-      block_cgemm<8, (N2 >= 64 ? 2 : 1)>(N3, N2, rb, U3s, rb, Gt, N2, Tt, PY, (R)P.scale);
     }
   }
   yz_fields<R, N2, N3, LY::G>(P, x, p, plane, xs, tw2, tw3, Tt, PY);
