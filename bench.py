@@ -339,6 +339,7 @@ def main():
     if wl_name != DEFAULT_WL:
         args.no_e2e = True
         args.no_cpu_baseline = True
+        args.no_farfield = True
     K, L, nrhs = W["K"], W["L"], (args.nrhs or W["nrhs"])
     c128 = W.get("c128", False)
     fmt_c, dec_c = W["fmt"], W["dec"]
