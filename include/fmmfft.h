@@ -112,9 +112,13 @@ enum {
                                     part (> 0, default 1): k = k0 sqrt(eps_r),
                                     eta = eta0 / sqrt(eps_r) in Eq. 7 (Sec. III.A.5,
                                     Table IV)                                   */
-  FMMFFT_KEY_EPS_R_IM = 9        /* imaginary part (<= 0, default 0; a lossy
+  FMMFFT_KEY_EPS_R_IM = 9,       /* imaginary part (<= 0, default 0; a lossy
                                     medium under the e^{j omega t} convention,
                                     eps_r = eps' - j sigma / (omega eps0))      */
+  FMMFFT_KEY_HOST_BLOCKS = 10    /* direction blocks of fmmfft_translate_host's
+                                    copy / compute pipeline (0: default 12; 1:
+                                    copy in, translate, copy out in sequence;
+                                    at most 64); may be changed at any time   */
 };
 
 /* Stages of one translation, in launch order (fmmfft_stage_times). */
@@ -298,8 +302,15 @@ int fmmfft_translate_noalloc(fmmfft_plan plan, const void* S_in, void* S_out, in
 
 /*
  * As fmmfft_translate with HOST field buffers: copies S_in to the device,
- * translates and copies the result back, all on `stream`, and waits for the
- * stream before returning.  Page-locked host buffers give full copy speed.
+ * translates and copies the result back, and waits for `stream` before
+ * returning.  The directions are taken in FMMFFT_KEY_HOST_BLOCKS blocks
+ * (default 12): every block's copy-in is queued on a plan-owned copy stream,
+ * block k translates on `stream` once its copy-in is done, and its copy-out
+ * runs on a second plan-owned copy stream while block k + 1 translates, so
+ * the copies overlap the kernels.  Results equal fmmfft_translate's bit for
+ * bit.  Page-locked host buffers are needed for the overlap (pageable ones
+ * work, with each copy staged synchronously).  The first pipelined call
+ * creates the two copy streams and their events.
  */
 int fmmfft_translate_host(fmmfft_plan plan, const void* S_in_host, void* S_out_host,
                           int nrhs, void* stream);

@@ -19,6 +19,9 @@
 
 using fmm::cdouble;
 
+constexpr int kHostBlocksMax = 64;     // direction blocks of the host pipeline
+constexpr int kHostBlocksDefault = 12;
+
 struct fmmfft_plan_s {
   int K[3] = {0, 0, 0};
   int n[3] = {0, 0, 0};
@@ -55,6 +58,11 @@ struct fmmfft_plan_s {
   cudaStream_t last_stream = nullptr;
   cudaStream_t side = nullptr;  // restore pre-pass, overlapped with the x pass
   cudaEvent_t fork = nullptr, join = nullptr;
+  // copy/compute pipeline of fmmfft_translate_host: copy streams, events
+  // (start, done, then one in / out pair per direction block) and block count
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t hev[2 + 2 * kHostBlocksMax] = {};
+  int host_blocks = 0;          // FMMFFT_KEY_HOST_BLOCKS, 0: default
   fmm::Schedule sched;          // fmmfft_autotune's choices
   bool profile = false;
   bool profiled_run = false;
@@ -190,6 +198,9 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   a.side = p->side;
   a.fork = p->fork;
   a.join = p->join;
+  a.p0 = 0;
+  a.nw = 0;
+  a.prepass = true;
   return a;
 }
 
@@ -460,7 +471,7 @@ int fmmfft_plan_create(fmmfft_plan* out, int Nx, int Ny, int Nz, double a, doubl
 }
 
 int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
-  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE)) return FMMFFT_ERR_INVALID_ARG;
+  if (!p || (p->ready && key != FMMFFT_KEY_PROFILE && key != FMMFFT_KEY_HOST_BLOCKS)) return FMMFFT_ERR_INVALID_ARG;
   const int iv = (int)v;
   switch (key) {
     case FMMFFT_KEY_PRECISION:
@@ -496,6 +507,10 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
     case FMMFFT_KEY_PROFILE:
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->profile = iv == 1;
+      return FMMFFT_OK;
+    case FMMFFT_KEY_HOST_BLOCKS:
+      if (iv < 0 || iv > kHostBlocksMax || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->host_blocks = iv;
       return FMMFFT_OK;
     case FMMFFT_KEY_EPS_R_RE:
       if (!(v > 0) || !std::isfinite(v)) return FMMFFT_ERR_INVALID_ARG;
@@ -817,7 +832,8 @@ int fmmfft_translate_host(fmmfft_plan p, const void* S_in_host, void* S_out_host
   if (!p) return FMMFFT_ERR_INVALID_ARG;
   if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
   if (!S_in_host || !S_out_host || nrhs < 1 || nrhs > 4096) return FMMFFT_ERR_INVALID_ARG;
-  const size_t bytes = (size_t)p->n_dir * 2 * nrhs * p->K[0] * p->K[1] * p->K[2] * elem_bytes(p);
+  const size_t per_dir = (size_t)2 * nrhs * p->K[0] * p->K[1] * p->K[2] * elem_bytes(p);
+  const size_t bytes = (size_t)p->n_dir * per_dir;
   cudaStream_t s = (cudaStream_t)stream;
   if (2 * bytes > p->io_bytes) {
     if (p->d_io) {
@@ -831,12 +847,70 @@ int fmmfft_translate_host(fmmfft_plan p, const void* S_in_host, void* S_out_host
   }
   char* din = (char*)p->d_io;
   char* dout = din + bytes;
-  if (cudaMemcpyAsync(din, S_in_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FMMFFT_ERR_CUDA;
-  int st = fmmfft_translate(p, din, dout, nrhs, stream);
+  const int want = p->host_blocks > 0 ? p->host_blocks : kHostBlocksDefault;
+  const int blocks = p->profile ? 1 : std::min(want, p->n_dir);
+  if (blocks <= 1) {
+    if (cudaMemcpyAsync(din, S_in_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    int st = fmmfft_translate(p, din, dout, nrhs, stream);
+    if (st != FMMFFT_OK) return st;
+    if (cudaMemcpyAsync(S_out_host, dout, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? FMMFFT_OK : FMMFFT_ERR_CUDA;
+  }
+  // Pipeline over blocks of directions: the copy-in of every block is queued
+  // on one copy stream, the translation of block k waits for its copy-in, and
+  // its copy-out runs on a second copy stream while block k + 1 translates.
+  void* inter = nullptr;
+  size_t ib = 0;
+  int st = fmm::plan_intermediate(p, nrhs, stream, &inter, &ib);
   if (st != FMMFFT_OK) return st;
-  if (cudaMemcpyAsync(S_out_host, dout, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FMMFFT_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return FMMFFT_ERR_CUDA;
-  return FMMFFT_OK;
+  if (!p->h2d) {
+    if (cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking) != cudaSuccess)
+      return FMMFFT_ERR_CUDA;
+    for (auto& ev : p->hev)
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  }
+  cudaEvent_t ev_start = p->hev[0], ev_done = p->hev[1];
+  cudaEvent_t* ev_in = p->hev + 2;
+  cudaEvent_t* ev_out = ev_in + kHostBlocksMax;
+  const int per = (p->n_dir + blocks - 1) / blocks;
+  const char* hin = (const char*)S_in_host;
+  char* hout = (char*)S_out_host;
+  // the copies must follow earlier work of `stream` on these buffers
+  if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaStreamWaitEvent(p->h2d, ev_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(p->d2h, ev_start, 0) != cudaSuccess)
+    return FMMFFT_ERR_CUDA;
+  for (int k = 0, p0 = 0; p0 < p->n_dir; ++k, p0 += per) {
+    const size_t off = (size_t)p0 * per_dir, len = (size_t)std::min(per, p->n_dir - p0) * per_dir;
+    if (cudaMemcpyAsync(din + off, hin + off, len, cudaMemcpyHostToDevice, p->h2d) != cudaSuccess ||
+        cudaEventRecord(ev_in[k], p->h2d) != cudaSuccess)
+      return FMMFFT_ERR_CUDA;
+  }
+  p->last_stream = s;
+  for (int k = 0, p0 = 0; p0 < p->n_dir; ++k, p0 += per) {
+    const int nw = std::min(per, p->n_dir - p0);
+    const size_t off = (size_t)p0 * per_dir, len = (size_t)nw * per_dir;
+    if (cudaStreamWaitEvent(s, ev_in[k], 0) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    fmm::TranslateArgs a = base_args(p);
+    a.nrhs = nrhs;
+    a.s_in = din;
+    a.s_out = dout;
+    a.inter = inter;
+    a.stream = s;
+    a.p0 = p0;
+    a.nw = nw;
+    a.prepass = k == 0;
+    if (fmm::launch_translate(a) != cudaSuccess) {
+      cudaGetLastError();
+      return FMMFFT_ERR_CUDA;
+    }
+    if (cudaEventRecord(ev_out[k], s) != cudaSuccess || cudaStreamWaitEvent(p->d2h, ev_out[k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(hout + off, dout + off, len, cudaMemcpyDeviceToHost, p->d2h) != cudaSuccess)
+      return FMMFFT_ERR_CUDA;
+  }
+  if (cudaEventRecord(ev_done, p->d2h) != cudaSuccess || cudaStreamWaitEvent(s, ev_done, 0) != cudaSuccess)
+    return FMMFFT_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? FMMFFT_OK : FMMFFT_ERR_CUDA;
 }
 
 int fmmfft_operator_host(fmmfft_plan p, int d, double* out) {
@@ -1398,6 +1472,14 @@ int fmmfft_plan_destroy(fmmfft_plan p) {
   }
   if (p->fork) cudaEventDestroy(p->fork);
   if (p->join) cudaEventDestroy(p->join);
+  if (p->h2d) {
+    cudaStreamSynchronize(p->h2d);
+    cudaStreamSynchronize(p->d2h);
+    cudaStreamDestroy(p->h2d);
+    cudaStreamDestroy(p->d2h);
+  }
+  for (auto& ev : p->hev)
+    if (ev) cudaEventDestroy(ev);
   void* s = p->d_status;
   free_dev(s);
   delete p;

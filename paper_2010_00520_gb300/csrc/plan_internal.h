@@ -81,6 +81,11 @@ struct TranslateArgs {
                                      // lines one block iteration covers (1, 2, 4)
   int no_overlap;                    // 1: pre-pass in line with the x pass
   int tc_gemm;                       // pre-pass products on the tensor cores: 1 3xTF32, 2 BF16x3
+  // direction block of this launch: directions p0 .. p0 + nw - 1 (nw = 0: all),
+  // fields and intermediate addressed at their place in the full arrays; the
+  // restore pre-pass runs only when `prepass` is set (it covers every direction)
+  int p0 = 0, nw = 0;
+  bool prepass = true;
 };
 
 // A translation schedule: the choices fmmfft_autotune makes for a plan.

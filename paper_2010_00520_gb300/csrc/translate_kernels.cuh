@@ -56,7 +56,8 @@ struct YZParams {
   int rmax_a, rmax_b;  // shared-memory capacity of the launch (ranks)
   int* status;
   int tc;              // restore on the tensor cores (TcRestore): 1 3xTF32, 2 BF16x3
-  int n_dir;
+  int n_dir;           // directions of this launch: p0 .. p0 + n_dir - 1
+  int p0;
   void* slab_scratch;  // large planes: one slot of slot_elems per block
   long long slot_elems;
 };
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
   C* work = tw3 + N3;
   C* plane = work;                          // LY::G planes of N3/2 x PY, field [z][y]
   C* xs = plane + LY::G * (N3 / 2) * PY;
-  const int x = blockIdx.x, p = blockIdx.y;
+  const int x = blockIdx.x, p = P.p0 + blockIdx.y;
   const int tid = threadIdx.x;
   for (int i = tid; i < N2; i += kThreads) tw2[i] = reinterpret_cast<const C*>(P.tw2)[i];
   for (int i = tid; i < N3; i += kThreads) tw3[i] = reinterpret_cast<const C*>(P.tw3)[i];
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
   if constexpr (TC != 0) tc = tc_setup(plane, &tc_bar, &tmem_slot);
   const int items = P.n1 * P.n_dir;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
-    const int x = it % P.n1, p = it / P.n1;
+    const int x = it % P.n1, p = P.p0 + it / P.n1;
     const C* op;
     if constexpr (FMT == 0) {
       op = reinterpret_cast<const C*>(P.op) + ((size_t)p * P.n1 + x) * (N3 * N2);

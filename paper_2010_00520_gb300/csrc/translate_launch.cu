@@ -203,8 +203,12 @@ static cudaError_t launch_yz(const TranslateArgs& a, const YZParams& Y, dim3 gri
 
 template <typename R>
 static cudaError_t launch_all(const TranslateArgs& a) {
-  const int F = a.n_dir * 2 * a.nrhs;
+  const int nw = a.nw > 0 ? a.nw : a.n_dir;
+  if (a.p0 < 0 || a.p0 + nw > a.n_dir) return cudaErrorInvalidValue;
+  const int F = nw * 2 * a.nrhs;
+  const size_t f0 = (size_t)a.p0 * 2 * a.nrhs;     // first field of the block
   const int rows = a.K[1] * a.K[2];
+  const size_t es = sizeof(cx<R>);
   cudaError_t e;
   auto mark = [&](int i) {
     if (a.events) cudaEventRecord(a.events[i], a.stream);
@@ -212,7 +216,8 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   mark(0);
   // the pre-pass needs only the stored factors: overlap it with the forward
   // x pass on the side stream (serially when stage times are recorded)
-  const bool overlap = a.n_stages > 0 && a.side && a.fork && a.join && !a.events && !a.no_overlap;
+  const int n_stages = a.prepass ? a.n_stages : 0;
+  const bool overlap = n_stages > 0 && a.side && a.fork && a.join && !a.events && !a.no_overlap;
   cudaStream_t ps = a.stream;
   if (overlap) {
     if ((e = cudaEventRecord(a.fork, a.stream)) != cudaSuccess) return e;
@@ -233,7 +238,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
       configured = true;
     }
   }
-  for (int i = 0; i < a.n_stages; ++i) {
+  for (int i = 0; i < n_stages; ++i) {
     const GemmStage& g = a.stages[i];
     dim3 grid((g.max_n + kGemmT - 1) / kGemmT, (g.max_m + kGemmT - 1) / kGemmT, g.batch);
     if (tc_gemm && sizeof(R) == 4 && a.tc_gemm == 2)
@@ -246,8 +251,8 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   if (overlap && (e = cudaEventRecord(a.join, a.side)) != cudaSuccess) return e;
   mark(1);
   XPassParams X;
-  X.src = a.s_in;
-  X.dst = a.inter;
+  X.src = (const char*)a.s_in + f0 * a.K[0] * rows * es;
+  X.dst = (char*)a.inter + f0 * a.n[0] * rows * es;
   X.tw = a.tw[0];
   X.Kx = a.K[0];
   X.rows = rows;
@@ -271,18 +276,19 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   Y.rmax_b = a.rmax_b;
   Y.status = a.status;
   Y.tc = a.tc;
-  Y.n_dir = a.n_dir;
+  Y.n_dir = nw;
+  Y.p0 = a.p0;
   Y.slab_scratch = a.slab_scratch;
   Y.slot_elems = a.slot_elems;
   const size_t smem = yz_smem_bytes(a);
   if (a.large && a.yz_fmt != 0 && !a.slab_scratch) return cudaErrorInvalidValue;
-  const int items = a.n[0] * a.n_dir;
-  dim3 grid = a.large ? dim3((unsigned)(items < a.large_grid ? items : a.large_grid)) : dim3(a.n[0], a.n_dir);
+  const int items = a.n[0] * nw;
+  dim3 grid = a.large ? dim3((unsigned)(items < a.large_grid ? items : a.large_grid)) : dim3(a.n[0], nw);
   if ((e = launch_yz(a, Y, grid, smem)) != cudaSuccess) return e;
   mark(3);
 
-  X.src = a.inter;
-  X.dst = a.s_out;
+  X.src = (const char*)a.inter + f0 * a.n[0] * rows * es;
+  X.dst = (char*)a.s_out + f0 * a.K[0] * rows * es;
   e = launch_x<R>(false, a.n[0], X, F, a.stream);
   mark(4);
   return e;
