@@ -295,6 +295,9 @@ def main():
     ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "bf16x3", "fp32"],
                     help="restore arithmetic of the compressed arm: tensor cores (3xTF32 or BF16x3) or FP32 CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "directions"],
+                    help="N > 1: independent problems per GPU (weak scaling) or the directions of one "
+                         "problem split into contiguous blocks, one shard plan per GPU (strong scaling)")
     ap.add_argument("--no-farfield", action="store_true",
                     help="skip timing the aggregation / disaggregation steps (Eqs. 4, 6)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -322,7 +325,8 @@ def main():
     import paper_2010_00520_gb300 as F
     from seeded_inputs import field_spectra
 
-    from paper_2010_00520_gb300.replicas import job_throughput, max_over_ranks, ranks_from_env, replica_seed
+    from paper_2010_00520_gb300.replicas import (direction_block, job_throughput, max_over_ranks, ranks_from_env,
+                                                 replica_seed)
     R_ = ranks_from_env()
     world, rank, local = R_.world, R_.rank, R_.local
     torch.cuda.set_device(local)
@@ -341,6 +345,10 @@ def main():
         args.no_cpu_baseline = True
         args.no_farfield = True
     K, L, nrhs = W["K"], W["L"], (args.nrhs or W["nrhs"])
+    shard = args.shard == "directions" and world > 1
+    n_dir_grid = 2 * (L + 1) ** 2
+    first, count = direction_block(n_dir_grid, world, rank) if shard else (0, n_dir_grid)
+    seed = W["seed"] if shard else replica_seed(W["seed"], rank)   # shards split one problem
     c128 = W.get("c128", False)
     fmt_c, dec_c = W["fmt"], W["dec"]
     plans = {}
@@ -360,6 +368,9 @@ def main():
         else:
             prec = F.FMMFFT_PREC_C64
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, prec)
+        if shard:
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_DIR_FIRST, first)
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_DIR_COUNT, count)
         t0 = time.perf_counter()
         F.fmmfft_compress(h)
         t_setup[name] = time.perf_counter() - t0
@@ -375,15 +386,17 @@ def main():
     stream = torch.cuda.current_stream()
     S_host = None
     if wl_name == DEFAULT_WL:
-        S_host = field_spectra(replica_seed(W["seed"], rank), n_dir, nrhs, K).astype(cdt)
-        x = torch.from_numpy(S_host).to("cuda")
+        # a shard's fields are its block of the whole problem's
+        S_host = field_spectra(seed, n_dir_grid, nrhs, K)[first:first + count].astype(cdt)
+        x = torch.from_numpy(np.ascontiguousarray(S_host)).to("cuda")
     else:
         # generated one direction at a time straight into device memory
         from seeded_inputs import field_spectra_rows
         x = torch.empty((n_dir, 2, nrhs, K[2], K[1], K[0]), dtype=tdt, device="cuda")
         nf = 2 * nrhs
         for p in range(n_dir):
-            rows = field_spectra_rows(replica_seed(W["seed"], rank), n_dir, nrhs, K, np.arange(p * nf, (p + 1) * nf))
+            q = first + p
+            rows = field_spectra_rows(seed, n_dir_grid, nrhs, K, np.arange(q * nf, (q + 1) * nf))
             x[p] = torch.from_numpy(rows.astype(cdt).reshape(2, nrhs, K[2], K[1], K[0])).to("cuda")
     y = torch.empty_like(x)
     io_bytes = x.numel() * x.element_size()
@@ -410,13 +423,19 @@ def main():
         return max_over_ranks(ms, dist, "cuda")
 
     units = _units(n, n_dir, nrhs)
+    # throughput of the job: replicas count every rank's problem, shards one
+    # problem, in both cases timed by the slowest rank
+    def job_value(seconds):
+        if shard:
+            return _units(n, n_dir_grid, nrhs) / seconds
+        return job_throughput(units, world, seconds)
     clocks = ClockSampler(local)
     clocks.start()
     ms = {name: timed(h, args.steps) for name, h in plans.items()}
     clk = clocks.stop()
     for h in plans.values():
         assert F.fmmfft_poll_status(h) == 0
-    value = {name: job_throughput(units, world, t * 1e-3) / 1e9 for name, t in ms.items()}
+    value = {name: job_value(t * 1e-3) / 1e9 for name, t in ms.items()}
 
     # per-stage device times (CUDA events on the launch stream, between kernels)
     stage = {}
@@ -487,7 +506,7 @@ def main():
         for _ in range(ne):
             F.fmmfft_translate_host(plans[main_arm], hin, hout, nrhs, stream)
         e2e_s = max_over_ranks((time.perf_counter() - t0) / ne, dist, "cuda")
-        e2e = {"value": job_throughput(units, world, e2e_s) / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+        e2e = {"value": job_value(e2e_s) / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                "d2h_bytes_per_step": io_bytes}
 
     peaks, peak_src = _peaks()
@@ -508,10 +527,13 @@ def main():
     step_bytes = 2 * io_bytes + st["device_bytes_operator"]
     out = {
         "metric": METRIC, "value": value[main_arm], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms[main_arm], "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms[main_arm], "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "c128 (fp64)" if c128 else "c64 (fp32)", "data": "synthetic",
         "config": {"workload": wl_name if nrhs == W["nrhs"] else wl_name.replace(f"{W['nrhs']}rhs", f"{nrhs}rhs"),
-                   "K": list(K), "n": list(n), "L": L, "n_dir": n_dir,
+                   "K": list(K), "n": list(n), "L": L, "n_dir": n_dir_grid,
+                   "parallelism": (f"direction shards over {world} GPUs (rank 0: directions {first}..{first + count - 1})"
+                                   if shard else (f"{world} replicas" if world > 1 else "1 GPU")),
                    "nrhs": nrhs, "fields": n_dir * 2 * nrhs,
                    "format": FORMAT_NAMES[(fmt_c, dec_c)] if main_arm == "compressed" else "none",
                    "tol": W["tol"],

@@ -115,10 +115,24 @@ enum {
   FMMFFT_KEY_EPS_R_IM = 9,       /* imaginary part (<= 0, default 0; a lossy
                                     medium under the e^{j omega t} convention,
                                     eps_r = eps' - j sigma / (omega eps0))      */
-  FMMFFT_KEY_HOST_BLOCKS = 10    /* direction blocks of fmmfft_translate_host's
+  FMMFFT_KEY_HOST_BLOCKS = 10,   /* direction blocks of fmmfft_translate_host's
                                     copy / compute pipeline (0: default 12; 1:
                                     copy in, translate, copy out in sequence;
                                     at most 64); may be changed at any time   */
+  FMMFFT_KEY_DIR_FIRST = 11,     /* shard plans: first direction of the block  */
+  FMMFFT_KEY_DIR_COUNT = 12      /* ... and its length (0, default: through the
+                                    last direction of the grid).  A shard plan
+                                    holds, compresses and translates only the
+                                    directions [first, first + count) of the
+                                    grid (Sec. II.A order): n_dir, the
+                                    directions, weights and field layouts are
+                                    those of the block, so the fields of a
+                                    shard are a contiguous block of the whole
+                                    problem's.  3D formats and the plain
+                                    operator give per direction exactly what
+                                    the whole plan gives; 4D formats decompose
+                                    the block's own 4D tensor.  Block outside
+                                    the grid: INVALID_ARG                     */
 };
 
 /* Stages of one translation, in launch order (fmmfft_stage_times). */

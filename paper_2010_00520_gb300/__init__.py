@@ -45,6 +45,8 @@ FMMFFT_KEY_PROFILE = 7
 FMMFFT_KEY_EPS_R_RE = 8
 FMMFFT_KEY_EPS_R_IM = 9
 FMMFFT_KEY_HOST_BLOCKS = 10
+FMMFFT_KEY_DIR_FIRST = 11
+FMMFFT_KEY_DIR_COUNT = 12
 FMMFFT_STAGE_RESTORE, FMMFFT_STAGE_XFWD, FMMFFT_STAGE_YZ, FMMFFT_STAGE_XINV = 0, 1, 2, 3
 FMMFFT_NUM_STAGES = 4
 
@@ -395,7 +397,8 @@ class Plan:
                 "near_rule": FMMFFT_KEY_NEAR_RULE, "kappa": FMMFFT_KEY_KAPPA,
                 "prefactor": FMMFFT_KEY_PREFACTOR, "trunc_rule": FMMFFT_KEY_TRUNC_RULE,
                 "profile": FMMFFT_KEY_PROFILE, "eps_r_re": FMMFFT_KEY_EPS_R_RE,
-                "eps_r_im": FMMFFT_KEY_EPS_R_IM, "host_blocks": FMMFFT_KEY_HOST_BLOCKS}
+                "eps_r_im": FMMFFT_KEY_EPS_R_IM, "host_blocks": FMMFFT_KEY_HOST_BLOCKS,
+                "dir_first": FMMFFT_KEY_DIR_FIRST, "dir_count": FMMFFT_KEY_DIR_COUNT}
         for k, v in opts.items():
             fmmfft_plan_set(self.handle, keys[k], v)
 

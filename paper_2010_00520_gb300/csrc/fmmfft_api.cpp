@@ -32,7 +32,9 @@ struct fmmfft_plan_s {
   int nphi_rule = 0, near_rule = 0, prefactor = 0, trunc_rule = 0;
   double kappa = 4.0;
   double eps_re = 1.0, eps_im = 0.0;   // relative permittivity of the medium
-  int n_dir = 0;
+  int dir_first = 0, dir_count = 0;    // direction block of a shard plan (count 0: to the end)
+  int n_dir_grid = 0;                  // directions of the whole grid
+  int n_dir = 0;                       // directions of this plan
   std::vector<double> khat, weights;
   bool ready = false;
   // device state
@@ -167,6 +169,25 @@ int ensure_common(fmmfft_plan_s* p) {
     p->d_status = (int*)s;
     if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FMMFFT_ERR_CUDA;
   }
+  return FMMFFT_OK;
+}
+
+// The plan's directions: the grid of Sec. II.A for its L and N_phi rule, cut
+// to the block [dir_first, dir_first + dir_count) for a shard plan.
+int set_directions(fmmfft_plan_s* p, int nphi_rule, int first, int count) {
+  const int nphi = nphi_rule == 0 ? 2 * (p->L + 1) : 2 * p->L + 1;
+  const int grid = (p->L + 1) * nphi;
+  const int cnt = count == 0 ? grid - first : count;
+  if (first < 0 || count < 0 || first >= grid || cnt < 1 || first + cnt > grid) return FMMFFT_ERR_INVALID_ARG;
+  std::vector<double> kh, w;
+  fmm::direction_grid(p->L, nphi, kh, w);
+  p->khat.assign(kh.begin() + 3 * (size_t)first, kh.begin() + 3 * (size_t)(first + cnt));
+  p->weights.assign(w.begin() + first, w.begin() + first + cnt);
+  p->nphi_rule = nphi_rule;
+  p->dir_first = first;
+  p->dir_count = count;
+  p->n_dir_grid = grid;
+  p->n_dir = cnt;
   return FMMFFT_OK;
 }
 
@@ -464,8 +485,7 @@ int fmmfft_plan_create(fmmfft_plan* out, int Nx, int Ny, int Nz, double a, doubl
   p->format = format;
   p->decomp = decomp;
   p->tol = tol;
-  p->n_dir = (L + 1) * 2 * (L + 1);
-  fmm::direction_grid(L, 2 * (L + 1), p->khat, p->weights);
+  set_directions(p, 0, 0, 0);
   *out = p;
   return FMMFFT_OK;
 }
@@ -480,14 +500,18 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
       return FMMFFT_OK;
     case FMMFFT_KEY_NPHI_RULE:
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
-      p->nphi_rule = iv;
       free_dev(p->d_weights);
-      {
-        const int nphi = iv == 0 ? 2 * (p->L + 1) : 2 * p->L + 1;
-        p->n_dir = (p->L + 1) * nphi;
-        fmm::direction_grid(p->L, nphi, p->khat, p->weights);
-      }
+      // a shard block that no longer fits the new grid falls back to the whole grid
+      if (set_directions(p, iv, p->dir_first, p->dir_count) != FMMFFT_OK) set_directions(p, iv, 0, 0);
       return FMMFFT_OK;
+    case FMMFFT_KEY_DIR_FIRST:
+      if (iv != v) return FMMFFT_ERR_INVALID_ARG;
+      free_dev(p->d_weights);
+      return set_directions(p, p->nphi_rule, iv, p->dir_count);
+    case FMMFFT_KEY_DIR_COUNT:
+      if (iv != v) return FMMFFT_ERR_INVALID_ARG;
+      free_dev(p->d_weights);
+      return set_directions(p, p->nphi_rule, p->dir_first, iv);
     case FMMFFT_KEY_NEAR_RULE:
       if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->near_rule = iv;
@@ -1106,7 +1130,7 @@ int fmmfft_poll_status(fmmfft_plan p, int* device_status) {
 namespace {
 
 const char kMagic[8] = {'F', 'M', 'M', 'F', 'F', 'T', 'P', '1'};
-const uint32_t kFileVersion = 2;   // 2: medium permittivity after trunc_rule
+const uint32_t kFileVersion = 3;   // 2: medium permittivity after trunc_rule; 3: direction block
 
 struct Writer {
   FILE* f;
@@ -1169,6 +1193,8 @@ int fmmfft_plan_save(fmmfft_plan p, const char* path) {
   w.put<int32_t>(p->trunc_rule);
   w.put<double>(p->eps_re);
   w.put<double>(p->eps_im);
+  w.put<int32_t>(p->dir_first);
+  w.put<int32_t>(p->dir_count);
   w.put<int32_t>(p->n_dir);
   if (p->format != FMMFFT_FORMAT_NONE) {
     const fmm::Layout& L = p->layout;
@@ -1228,13 +1254,15 @@ int fmmfft_plan_load(fmmfft_plan* out, const char* path) {
   const double kappa = r.get<double>();
   const int prefactor = r.get<int32_t>(), trunc_rule = r.get<int32_t>();
   const double eps_re = r.get<double>(), eps_im = r.get<double>();
+  const int dir_first = r.get<int32_t>(), dir_count = r.get<int32_t>();
   const int n_dir = r.get<int32_t>();
   fmmfft_plan p = nullptr;
   int st = r.ok ? fmmfft_plan_create(&p, K[0], K[1], K[2], a, k0, L, format, decomp, tol) : FMMFFT_ERR_IO;
   const std::pair<int, double> opts[] = {{FMMFFT_KEY_PRECISION, precision}, {FMMFFT_KEY_NPHI_RULE, nphi_rule},
                                          {FMMFFT_KEY_NEAR_RULE, near_rule},  {FMMFFT_KEY_KAPPA, kappa},
                                          {FMMFFT_KEY_PREFACTOR, prefactor},  {FMMFFT_KEY_TRUNC_RULE, trunc_rule},
-                                         {FMMFFT_KEY_EPS_R_RE, eps_re},      {FMMFFT_KEY_EPS_R_IM, eps_im}};
+                                         {FMMFFT_KEY_EPS_R_RE, eps_re},      {FMMFFT_KEY_EPS_R_IM, eps_im},
+                                         {FMMFFT_KEY_DIR_COUNT, dir_count},  {FMMFFT_KEY_DIR_FIRST, dir_first}};
   for (const auto& o : opts)
     if (st == FMMFFT_OK) st = fmmfft_plan_set(p, o.first, o.second);
   if (st == FMMFFT_OK && p->n_dir != n_dir) st = FMMFFT_ERR_INVALID_ARG;

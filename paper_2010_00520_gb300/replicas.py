@@ -2,10 +2,14 @@
 
 The translation stage has no exchange step between directions, fields or
 independent problems (Sec. II.C: restore and translation per direction need
-no communication), so a run on N GPUs is N independent replicas, one process
-per GPU: each rank translates its own problem, the only collectives are a
-barrier around the timed region and the maximum of the per-rank times, and
-the throughput counts the work of all ranks (weak scaling).
+no communication), so a run on N GPUs needs no data-path collective.  Two
+ways to use N GPUs, one process each:
+  * replicas (weak scaling): each rank translates its own problem;
+  * direction shards (strong scaling): the ranks split the directions of one
+    problem into contiguous blocks (`direction_block`) and each translates
+    its block with a shard plan (FMMFFT_KEY_DIR_FIRST / _COUNT).
+Either way the only collectives are a barrier around the timed region and the
+maximum of the per-rank times.
 """
 from __future__ import annotations
 
@@ -38,6 +42,16 @@ def ranks_from_env(env=None) -> Ranks:
 def replica_seed(seed: int, rank: int) -> int:
     """Seed of rank `rank`'s problem: rank 0 keeps the workload's own seed."""
     return seed + 7919 * rank
+
+
+def direction_block(n_dir: int, world: int, rank: int) -> tuple[int, int]:
+    """(first, count) of rank `rank`'s contiguous block of n_dir directions:
+    sizes differ by at most one, larger blocks first, every direction once."""
+    if world < 1 or not 0 <= rank < world or n_dir < world:
+        raise ValueError(f"cannot split {n_dir} directions over {world} ranks")
+    base, extra = divmod(n_dir, world)
+    first = rank * base + min(rank, extra)
+    return first, base + (1 if rank < extra else 0)
 
 
 def max_over_ranks(value: float, dist=None, device=None) -> float:

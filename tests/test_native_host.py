@@ -217,3 +217,28 @@ def test_compress_host_records_statistics(native):
         assert list(st["max_rank"][:3]) == list(r.max(axis=0))
     finally:
         native.fmmfft_plan_destroy(h)
+
+
+def test_shard_plan_directions_are_a_block_of_the_grid(native):
+    L = 4
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, L, 0, 0, 0.0)
+    try:
+        kh, w = native.fmmfft_plan_directions(h)
+        n = len(w)
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_DIR_FIRST, 7)
+        assert native.fmmfft_plan_stats(h)["n_dir"] == n - 7           # count 0: to the end
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_DIR_COUNT, 11)
+        kh2, w2 = native.fmmfft_plan_directions(h)
+        assert native.fmmfft_plan_stats(h)["n_dir"] == 11
+        assert np.array_equal(kh2, kh[7:18]) and np.array_equal(w2, w[7:18])
+        for key, bad in ((native.FMMFFT_KEY_DIR_COUNT, n), (native.FMMFFT_KEY_DIR_FIRST, n),
+                         (native.FMMFFT_KEY_DIR_FIRST, -1), (native.FMMFFT_KEY_DIR_COUNT, 2.5)):
+            with pytest.raises(native.FmmfftError):
+                native.fmmfft_plan_set(h, key, bad)
+        assert native.fmmfft_plan_stats(h)["n_dir"] == 11                # unchanged by the rejects
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_NPHI_RULE, 1)       # the block of the new grid
+        kh3, _ = native.fmmfft_plan_directions(h)
+        ref, _ = dr.direction_grid(L, "paper")
+        assert np.allclose(kh3, ref[7:18], atol=1e-14)
+    finally:
+        native.fmmfft_plan_destroy(h)

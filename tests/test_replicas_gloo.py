@@ -57,3 +57,63 @@ def test_ranks_from_env_alone_and_invalid():
     with pytest.raises(ValueError):
         ranks_from_env({"WORLD_SIZE": "2", "RANK": "2"})
     assert max_over_ranks(3.0) == 3.0
+
+
+def test_direction_blocks_partition_the_grid():
+    from paper_2010_00520_gb300.replicas import direction_block
+    for n_dir, world in ((162, 1), (162, 2), (162, 4), (162, 8), (98, 8), (8, 8), (435, 3)):
+        blocks = [direction_block(n_dir, world, r) for r in range(world)]
+        assert blocks[0][0] == 0 and sum(c for _, c in blocks) == n_dir
+        for (f0, c0), (f1, _) in zip(blocks, blocks[1:]):
+            assert f1 == f0 + c0                       # contiguous, in rank order
+        assert max(c for _, c in blocks) - min(c for _, c in blocks) <= 1
+    with pytest.raises(ValueError):
+        direction_block(3, 4, 0)
+
+
+def _shard_worker(rank, world, port, out):
+    """Each rank compresses only its block of directions (host FP64 set-up,
+    Tucker-3D) with a shard plan; rank 0 gathers the restored operators."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import numpy as np
+        import paper_2010_00520_gb300 as F
+        from paper_2010_00520_gb300.replicas import direction_block
+        K, L = (6, 5, 7), 3
+        n_dir = 2 * (L + 1) ** 2
+        first, count = direction_block(n_dir, world, rank)
+        h = F.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 3, 1, 1e-4)
+        try:
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_DIR_FIRST, first)
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_DIR_COUNT, count)
+            assert F.fmmfft_plan_stats(h)["n_dir"] == count
+            ranks, restored = F.fmmfft_compress_host(h)
+        finally:
+            F.fmmfft_plan_destroy(h)
+        parts = [None] * world
+        dist.all_gather_object(parts, (first, ranks, restored))
+        if rank == 0:
+            out["parts"] = parts
+    finally:
+        dist.destroy_process_group()
+
+
+def test_direction_shards_on_gloo_ranks_equal_the_whole_plan():
+    import numpy as np
+    import paper_2010_00520_gb300 as F
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        parts = out["parts"]
+    K, L = (6, 5, 7), 3
+    h = F.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 3, 1, 1e-4)
+    try:
+        ranks, restored = F.fmmfft_compress_host(h)
+    finally:
+        F.fmmfft_plan_destroy(h)
+    parts = sorted(parts, key=lambda t: t[0])
+    assert np.array_equal(np.concatenate([p[1] for p in parts]), ranks)
+    assert np.array_equal(np.concatenate([p[2] for p in parts]), restored)
