@@ -346,3 +346,47 @@ def test_direction_shards_translate_their_block(native, cuda, fmt, dec, prec):
         ops = pl.operators(plan)
         ref = pl.translate_with(lambda p: ops[p], S.astype(np.complex128))
         assert np.linalg.norm(sharded - ref) / np.linalg.norm(ref) <= tol + 1e-5
+
+
+@pytest.mark.parametrize("fmt,dec,prec,bound", [(0, 0, 1, 2e-6), (3, 1, 2, 1e-4 + 1e-5)])
+def test_maximum_extents_degenerate_L0(native, cuda, fmt, dec, prec, bound):
+    """The largest grid the kernels take, 128 x 128 x 64 boxes (n = 256 x 256 x
+    128, persistent large-plane kernel), at the degenerate L = 0: the operator
+    is the isotropic monopole term for both directions of the grid.  Sampled
+    fields against the oracle's FP64 translation."""
+    F, torch = native, cuda
+    K, L, nrhs = (128, 128, 64), 0, 1
+    h = _plan(F, K, L, fmt, dec, 1e-4 if fmt else 0.0, prec)
+    try:
+        F.fmmfft_compress(h)
+        st = F.fmmfft_plan_stats(h)
+        assert st["n_dir"] == 2 and list(st["n"]) == [256, 256, 128] and st["large_planes"] == 1
+        errs = _sampled_fields(F, torch, h, K, L, nrhs, 31, [0] if fmt == 0 else [3])
+        assert max(errs) <= bound, errs
+    finally:
+        F.fmmfft_plan_destroy(h)
+
+
+def test_smallest_grid(native, cuda):
+    """K = 2 per axis (n = 4), every offset near except the far corners under the
+    Chebyshev shell: only |d_i| <= 1, so the whole operator is zero; with the
+    kappa = 0 rule (only d = 0 near) the far interactions are all there."""
+    F, torch = native, cuda
+    K, L, nrhs = (2, 2, 2), 1, 2
+    for near, kappa in ((0, 4.0), (1, 0.0)):
+        h = _plan(F, K, L, 0, 0, 0.0, 0)
+        try:
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_NEAR_RULE, near)
+            F.fmmfft_plan_set(h, F.FMMFFT_KEY_KAPPA, kappa)
+            F.fmmfft_compress(h)
+            plan = pl.Plan(K=K, L=L, near_rule="chebyshev" if near == 0 else "kappa", kappa=kappa)
+            S = field_spectra(5, plan.n_dir, nrhs, K)
+            out = _gpu_translate(F, torch, h, S, nrhs, c128=True)
+            ops = pl.operators(plan)
+            ref = pl.translate_with(lambda p: ops[p], S)
+            if near == 0:
+                assert np.abs(out).max() == 0.0 and np.abs(ref).max() == 0.0
+            else:
+                assert _rel(out, ref) <= 1e-10
+        finally:
+            F.fmmfft_plan_destroy(h)
