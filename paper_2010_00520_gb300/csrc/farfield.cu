@@ -223,8 +223,9 @@ cudaError_t aggregate_t(const FarFieldArgs& a) {
   const int ychunks = (a.n_dir + dirs - 1) / dirs;
   const size_t smem = (size_t)RT * a.nb * kAggBoxes * sizeof(cx<R>);
   if (tiles > 0x7fffffff || ychunks > 65535 || rchunks > 65535) return cudaErrorInvalidValue;
+  static std::atomic<int> optin[kMaxDevices];
   auto kern = aggregate_kernel<R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_optin((const void*)kern, optin);
   if (e != cudaSuccess) return e;
   kern<<<dim3((unsigned)tiles, ychunks, rchunks), kAggBoxes, smem, a.stream>>>(
       (const cx<R>*)a.P, (const cx<R>*)a.in, (cx<R>*)a.out, a.V, a.nb, a.nrhs, a.n_dir, dirs);

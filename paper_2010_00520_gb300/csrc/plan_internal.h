@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <complex>
 #include <vector>
 
@@ -12,6 +13,29 @@
 namespace fmm {
 
 using cdouble = std::complex<double>;
+
+// Devices a process may drive (per-device launch state below).
+constexpr int kMaxDevices = 64;
+
+// Let `func` take up to the device's opt-in maximum of dynamic shared memory
+// (less its static shared memory), once per device: `done` is the caller's
+// per-kernel array of kMaxDevices flags (static storage, zero-initialised).
+// The attribute is a per-device upper bound, so one setting serves every
+// later launch size; setting it twice (two threads) is harmless.
+inline cudaError_t smem_optin(const void* func, std::atomic<int>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cache = dev >= 0 && dev < kMaxDevices;
+  if (cache && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && cache) done[dev].store(1, std::memory_order_release);
+  return e;
+}
 
 // Per-direction restore descriptor of the yz kernel (device pointers).
 //   Tucker-like (yz format 1): h = H_p, row x at h + x * hx (ra x rb, [b][c]);

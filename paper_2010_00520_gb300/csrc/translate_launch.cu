@@ -35,23 +35,17 @@ static int xpass_rows_per_block(int rows, int mult) {
 
 template <typename R, int N1>
 static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s) {
-  static size_t configured_f = 0, configured_i = 0;
+  static std::atomic<int> optin_f[kMaxDevices], optin_i[kMaxDevices];
   P.rows_per_block = xpass_rows_per_block<R, N1>(P.rows, P.rows_per_block);
   const size_t smem = xpass_smem<R, N1>(P.rows_per_block);
   dim3 grid((unsigned)(((P.rows + P.rows_per_block - 1) / P.rows_per_block) * (size_t)F));
   if (fwd) {
-    if (smem > configured_f) {
-      cudaError_t e = cudaFuncSetAttribute(xfwd_kernel<R, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      configured_f = smem;
-    }
+    cudaError_t e = smem_optin((const void*)xfwd_kernel<R, N1>, optin_f);
+    if (e != cudaSuccess) return e;
     xfwd_kernel<R, N1><<<grid, kThreads, smem, s>>>(P);
   } else {
-    if (smem > configured_i) {
-      cudaError_t e = cudaFuncSetAttribute(xinv_kernel<R, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      configured_i = smem;
-    }
+    cudaError_t e = smem_optin((const void*)xinv_kernel<R, N1>, optin_i);
+    if (e != cudaSuccess) return e;
     xinv_kernel<R, N1><<<grid, kThreads, smem, s>>>(P);
   }
   return cudaGetLastError();
@@ -227,16 +221,10 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   // 3xTF32 plans run the pre-pass products on the tensor cores too
   const bool tc_gemm = a.tc_gemm != 0;
   if (tc_gemm) {
-    static bool configured = false;
-    if (!configured) {
-      e = cudaFuncSetAttribute(cgemm_batched_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kTcGemmSmem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cgemm_batched_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kTcGemmSmem);
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
+    static std::atomic<int> optin_t[kMaxDevices], optin_b[kMaxDevices];
+    e = smem_optin((const void*)cgemm_batched_tc_kernel<false>, optin_t);
+    if (e == cudaSuccess) e = smem_optin((const void*)cgemm_batched_tc_kernel<true>, optin_b);
+    if (e != cudaSuccess) return e;
   }
   for (int i = 0; i < n_stages; ++i) {
     const GemmStage& g = a.stages[i];

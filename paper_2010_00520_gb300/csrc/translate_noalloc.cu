@@ -18,9 +18,8 @@ static __device__ __align__(256) unsigned char g_translate_scratch[FMMFFT_NOALLO
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_addr[fmm::kMaxDevices] = {};
 
 // Device address of g_translate_scratch on the current device.  In host code
 // the array's name stands for a host-side shadow, not device memory, so the
@@ -31,7 +30,7 @@ int scratch_address(void** out) {
     cudaGetLastError();
     return FMMFFT_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return FMMFFT_ERR_UNSUPPORTED;
+  if (dev < 0 || dev >= fmm::kMaxDevices) return FMMFFT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
     void* ptr = nullptr;

@@ -9,13 +9,10 @@ namespace fmm {
 
 template <typename R, int N2, int N3, int FMT, int TC>
 cudaError_t launch_yz_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
-  static size_t configured = 0;
+  static std::atomic<int> optin[kMaxDevices];
   auto kern = yz_kernel<R, N2, N3, FMT, TC>;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = smem_optin((const void*)kern, optin);
+  if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
@@ -57,13 +54,10 @@ cudaError_t launch_yz_fmt(const YZParams& P, int n2, int n3, dim3 grid, size_t s
 
 template <typename R, int N2, int N3, int FMT, int TC>
 cudaError_t launch_yzl_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s) {
-  static size_t configured = 0;
+  static std::atomic<int> optin[kMaxDevices];
   auto kern = yzl_kernel<R, N2, N3, FMT, TC>;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = smem_optin((const void*)kern, optin);
+  if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
