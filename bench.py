@@ -138,11 +138,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, one thread, on a bounded sample
 # ---------------------------------------------------------------------------
-def cpu_baseline_child(ndirs: int):
+def cpu_baseline_child(ndirs: int, out_path: str = ""):
     """Runs in a subprocess with one BLAS/OpenMP thread.  Times the oracle's
     compressed translation (Tucker-3D restore of each sampled direction, Fig.
     3(a), then Eq. 5 for its 8 fields); the oracle's HOSVD set-up is not
-    timed, as the GPU arm's set-up is not."""
+    timed, as the GPU arm's set-up is not.  Afterwards (untimed) it translates
+    the same fields with the uncompressed FP64 operators and, given out_path,
+    saves both results there (.npz) so that the GPU outputs of these fields
+    can be checked against them."""
     import numpy as np
     from oracle import decomp as D
     from oracle import pipeline as pl
@@ -157,24 +160,30 @@ def cpu_baseline_child(ndirs: int):
     nf = 2 * nrhs
     fields = np.array([p * nf + j for p in dirs for j in range(nf)])
     A = field_spectra_rows(seed, plan.n_dir, nrhs, K, fields)
+    comp = []
     t0 = time.perf_counter()
     i = 0
     for tk in tks:
         That = D.tucker3d_restore_steps(tk.core, *tk.factors)
         for _ in range(nf):
-            tr.translate_field_fft(That, A[i])
+            comp.append(tr.translate_field_fft(That, A[i]))
             i += 1
     dt = time.perf_counter() - t0
     n = plan.n
     units = n[0] * n[1] * n[2] * len(fields)
+    if out_path:
+        exact = [tr.translate_field_fft(ops[k], A[k * nf + j]) for k in range(len(dirs)) for j in range(nf)]
+        np.savez(out_path, dirs=np.array(dirs), compressed=np.stack(comp), exact=np.stack(exact))
     print(json.dumps({"seconds": dt, "units": units, "fields": int(len(fields)), "dirs": len(dirs)}))
 
 
-def run_cpu_baseline(ndirs: int):
+def run_cpu_baseline(ndirs: int, out_path: str = ""):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", str(ndirs)],
-                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, timeout=900)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", str(ndirs)]
+    if out_path:
+        cmd += ["--cpu-baseline-out", out_path]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
@@ -306,10 +315,11 @@ def main():
                     help="workload (default: the headline Tucker-3D one); others print their own line "
                          "without CPU baseline and end-to-end arms")
     ap.add_argument("--cpu-baseline-child", type=int, default=0)
+    ap.add_argument("--cpu-baseline-out", default="")
     ap.add_argument("--reference-child", type=int, nargs=2, default=None)
     args = ap.parse_args()
     if args.cpu_baseline_child:
-        cpu_baseline_child(args.cpu_baseline_child)
+        cpu_baseline_child(args.cpu_baseline_child, args.cpu_baseline_out)
         return
     if args.reference_child:
         reference_child(*args.reference_child)
@@ -576,7 +586,25 @@ def main():
     if farfield is not None:
         out["farfield"] = farfield
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = run_cpu_baseline(CPU_SAMPLE_DIRS)
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            ref_path = os.path.join(td, "oracle_fields.npz")
+            out["cpu_baseline"] = run_cpu_baseline(CPU_SAMPLE_DIRS, ref_path)
+            if os.path.exists(ref_path) and wl_name == DEFAULT_WL and nrhs == W["nrhs"]:
+                # accuracy of the timed outputs on the oracle's sample of fields:
+                # the GPU translation against the uncompressed FP64 one
+                ref = np.load(ref_path)
+                dirs = [int(d) for d in ref["dirs"]]
+                acc = {"fields": int(ref["exact"].shape[0]), "directions": dirs}
+                exact = ref["exact"]
+                for name, h in plans.items():
+                    F.fmmfft_translate(h, x, y, nrhs, stream)
+                    torch.cuda.synchronize()
+                    got = y[dirs].cpu().numpy().astype(np.complex128).reshape(exact.shape)
+                    acc[f"{name}_rel_l2_vs_fp64"] = float(np.linalg.norm(got - exact) / np.linalg.norm(exact))
+                acc["oracle_compressed_rel_l2_vs_fp64"] = float(np.linalg.norm(ref["compressed"] - exact)
+                                                                / np.linalg.norm(exact))
+                out["accuracy"] = acc
     for h in plans.values():
         F.fmmfft_plan_destroy(h)
     if rank == 0:
