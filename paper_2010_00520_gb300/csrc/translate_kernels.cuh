@@ -66,7 +66,11 @@ struct YZParams {
 // planes, and for the Tucker-like format at most 64 columns of H_p[x].
 template <typename R, int N2, int N3, int FMT>
 struct TcRestore {
-  static constexpr bool available = sizeof(R) == 4 && N2 % 64 == 0 && N3 % 64 == 0 && FMT != 0;
+  // 64-multiples (tiled over larger planes), or planes of 32 and 64 that one
+  // partly filled 64 x 64 tile covers
+  static constexpr bool available = sizeof(R) == 4 && FMT != 0 &&
+                                    ((N2 % 64 == 0 && N3 % 64 == 0) ||
+                                     (N2 % 32 == 0 && N3 % 32 == 0 && N2 <= 64 && N3 <= 64));
 };
 
 // ---------------------------------------------------------------------------

@@ -98,7 +98,9 @@ int tc_kind(int precision) {
 }
 
 bool tc_restore_applies(const TranslateArgs& a) {
-  return tc_kind(a.precision) != 0 && a.yz_fmt != 0 && a.n[1] % 64 == 0 && a.n[2] % 64 == 0 &&
+  const bool tiles = (a.n[1] % 64 == 0 && a.n[2] % 64 == 0) ||
+                     (a.n[1] % 32 == 0 && a.n[2] % 32 == 0 && a.n[1] <= 64 && a.n[2] <= 64);
+  return tc_kind(a.precision) != 0 && a.yz_fmt != 0 && tiles &&
          (a.yz_fmt == 2 || a.rmax_b <= 64);
 }
 

@@ -229,12 +229,12 @@ def loss(formats, eps=(2.0, 2 - 1j, 2 - 2j, 2 - 8j), diameter=8, **kw):
 SWEEPS = {"size": structure_size, "tol": tolerance, "box": box_size, "digits": accuracy, "loss": loss}
 
 
-def run(cases, gpu=False, nrhs=1, log=None):
+def run(cases, gpu=False, nrhs=1, log=None, precision=FMMFFT_PREC_C64):
     rows = []
     for c in cases:
         row = host_case(c)
         if gpu:
-            gpu_case(c, row, nrhs=nrhs)
+            gpu_case(c, row, nrhs=nrhs, precision=precision)
         rows.append(row)
         if log:
             log(row)
@@ -276,6 +276,8 @@ def main(argv=None):
     ap.add_argument("--trunc-rule", type=int, default=0)
     ap.add_argument("--gpu", action="store_true", help="also time compressed and plain translations")
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=FMMFFT_PREC_C64,
+                    help="FMMFFT_PREC_*: 1 complex64 with FP32 restores (default), 2 3xTF32, 3 BF16x3")
     ap.add_argument("--json", help="write the rows to this file")
     a = ap.parse_args(argv)
     fmts = list(FORMATS) if a.formats == ["all"] else a.formats
@@ -286,7 +288,7 @@ def main(argv=None):
         cases = tolerance(fmts, diameter=a.diameter, **kw)
     else:
         cases = SWEEPS[a.sweep](fmts, diameter=a.diameter, tol=a.tol, **kw)
-    rows = run(cases, gpu=a.gpu, nrhs=a.nrhs,
+    rows = run(cases, gpu=a.gpu, nrhs=a.nrhs, precision=a.precision,
                log=lambda r: print(json.dumps(asdict(r)), flush=True))
     print(table(rows))
     if a.json:
