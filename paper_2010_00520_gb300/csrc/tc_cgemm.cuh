@@ -56,10 +56,17 @@ __device__ __forceinline__ int tc_off(int row, int k) {
   return (((row >> 3) * (kTcKC / 4) + (k >> 2)) << 5) + ((row & 7) << 2) + (k & 3);
 }
 
+// bytes of operand staging for chunks of KC complex K (A big/small, B big/small)
+template <int KC>
+constexpr size_t tc_smem_bytes() {
+  return 4 * 128 * (size_t)KC * sizeof(float);
+}
+
 // shared-memory matrix descriptor: no swizzle, LBO 128 B (K direction), SBO
-// between 8-row groups, descriptor version 1
+// between 8-row groups (KC / 4 core matrices of 128 B each), version 1
+template <int KC = kTcKC>
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  const uint64_t lbo = 128, sbo = (kTcKC / 4) * 128;
+  const uint64_t lbo = 128, sbo = (KC / 4) * 128;
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
@@ -394,7 +401,10 @@ __device__ __forceinline__ void tc_cgemm64_bf16(TcState& s, int M, int N, int K,
 // thread of the 256-thread block calls it.  C_GLOBAL: C is in global memory,
 // so the epilogue combines the quadrants in shared memory and writes C once,
 // coalesced; otherwise C (shared memory) is written directly, one row per lane.
-template <bool C_GLOBAL, bool BF16 = false, typename FA, typename FB>
+// KC: complex K per staged chunk (3xTF32 path); `s.buf` must hold
+// tc_smem_bytes<KC>().  Larger chunks halve the round trips of long
+// contractions at the price of registers and shared memory.
+template <bool C_GLOBAL, bool BF16 = false, int KC = kTcKC, typename FA, typename FB>
 __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a_of, FB b_of, float2* C,
                                            int ldc, float scale) {
   if constexpr (BF16) {
@@ -403,24 +413,25 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
   }
   const int tid = threadIdx.x;
   uint32_t* Ab = reinterpret_cast<uint32_t*>(s.buf);
-  uint32_t* As = Ab + kTcTileFloats;
-  uint32_t* Bb = As + kTcTileFloats;
-  uint32_t* Bs = Bb + kTcTileFloats;
+  constexpr int kTile = 128 * KC;
+  uint32_t* As = Ab + kTile;
+  uint32_t* Bb = As + kTile;
+  uint32_t* Bs = Bb + kTile;
   constexpr uint32_t idesc = tc_idesc_tf32_128x128();
-  const int nchunks = (K + kTcKC - 1) / kTcKC;
+  const int nchunks = (K + KC - 1) / KC;
   // Element i of the first 64 rows of a chunk sits at float i of the tile:
   // core matrix i / 32 (row group, K group), row (i % 32) / 4, column i % 4;
   // the second 64 rows follow 1024 floats later.  Each thread owns i = tid +
   // 256 j (j < 4); consecutive threads write consecutive words.
-  constexpr int kPer = 64 * kTcKC / 256;
+  constexpr int kPer = 64 * KC / 256;
   float2 va[kPer], vb[kPer];
   auto gather = [&](int k0) {
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
       const int i = tid + 256 * j;
       const int cm = i >> 5, w = i & 31;
-      const int m = (cm / (kTcKC / 4)) * 8 + (w >> 2);
-      const int gk = k0 + (cm % (kTcKC / 4)) * 4 + (w & 3);
+      const int m = (cm / (KC / 4)) * 8 + (w >> 2);
+      const int gk = k0 + (cm % (KC / 4)) * 4 + (w & 3);
       va[j] = (gk < K && m < M) ? a_of(m, gk) : make_float2(0.f, 0.f);
       vb[j] = (gk < K && m < N) ? b_of(gk, m) : make_float2(0.f, 0.f);
     }
@@ -431,7 +442,7 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
     // (real) and 64 + n (imaginary), K contiguous
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
-      const int o0 = tid + 256 * j, o1 = o0 + 64 * kTcKC;
+      const int o0 = tid + 256 * j, o1 = o0 + 64 * KC;
       const float2 a = va[j], b = vb[j];
       const uint32_t arb = to_tf32(a.x), aib = to_tf32(a.y);
       const uint32_t brb = to_tf32(b.x), bib = to_tf32(b.y);
@@ -450,17 +461,17 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
       tc_fence_after();
       const uint32_t ab = smem_u32(Ab), as = smem_u32(As), bb = smem_u32(Bb), bs = smem_u32(Bs);
 #pragma unroll
-      for (int ks = 0; ks < kTcKC / 8; ++ks) {
+      for (int ks = 0; ks < KC / 8; ++ks) {
         const uint32_t step = ks * 2 * 128;        // two core matrices along K
         const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
-        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bb + step), idesc, acc0);
-        tc_mma(s.tmem, tc_desc(as + step), tc_desc(bb + step), idesc, 1u);
-        tc_mma(s.tmem, tc_desc(ab + step), tc_desc(bs + step), idesc, 1u);
+        tc_mma(s.tmem, tc_desc<KC>(ab + step), tc_desc<KC>(bb + step), idesc, acc0);
+        tc_mma(s.tmem, tc_desc<KC>(as + step), tc_desc<KC>(bb + step), idesc, 1u);
+        tc_mma(s.tmem, tc_desc<KC>(ab + step), tc_desc<KC>(bs + step), idesc, 1u);
       }
       tc_commit(s.mbar);
     }
     // the next chunk's loads overlap the MMAs of this one
-    if (ch + 1 < nchunks) gather((ch + 1) * kTcKC);
+    if (ch + 1 < nchunks) gather((ch + 1) * KC);
     // warp 0 polls the mbarrier (each poll is a shared-memory operation);
     // the other warps sleep in the barrier, which also shares the outcome
     bool timeout = false;

@@ -356,6 +356,11 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
 constexpr size_t kTcGemmSmem = 56 * 1024;
 // contraction chunk of the CUDA-core TT-like slab restore (slab_tt_chunked)
 constexpr int kRestoreKC = 64;
+// complex K per staged tensor-core chunk in the large-plane kernel: its field
+// plane already takes more shared memory than the 64 KB of staging, so the
+// longer chunk (half the round trips of the fused kernel's 16) costs no
+// occupancy
+constexpr int kTcKCLarge = 32;
 
 template <bool BF16>   // BF16: BF16x3 products, else 3xTF32
 __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDesc* __restrict__ descs,
@@ -607,7 +612,7 @@ struct YZLLayout {
   static constexpr size_t plane_elems = (size_t)(N3 / 2) * PY + kWarps * XW;
   static size_t smem_bytes(int fmt, bool tc) {
     size_t work = sizeof(cx<R>) * plane_elems;
-    if (fmt != 0 && tc && kTcSmemBytes > work) work = kTcSmemBytes;
+    if (fmt != 0 && tc && tc_smem_bytes<kTcKCLarge>() > work) work = tc_smem_bytes<kTcKCLarge>();
     return sizeof(cx<R>) * (N2 + N3) + work;
   }
   // global scratch per block: the slab, then G (rb x N2) of the Tucker-like
@@ -664,17 +669,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
         float2* Sf = reinterpret_cast<float2*>(slot);
         if constexpr (FMT == 1) {
           for (int y0 = 0; y0 < N2; y0 += 64)
-            tc_cgemm64<true, TC == 2>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
+            tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
                        [&](int b, int y) { return U2f[(y0 + y) * ra + b]; }, Gf + y0, N2, 1.0f);
           for (int z0 = 0; z0 < N3; z0 += 64)
             for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64<true, TC == 2>(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
+              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
                          [&](int c, int y) { return Gf[c * N2 + y0 + y]; }, Sf + (size_t)z0 * N2 + y0, N2,
                          (float)P.scale);
         } else {
           for (int z0 = 0; z0 < N3; z0 += 64)
             for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64<true, TC == 2>(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
+              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
                          [&](int b, int y) { return Hf[(y0 + y) * rb + b]; }, Sf + (size_t)z0 * N2 + y0, N2,
                          (float)P.scale);
         }
