@@ -162,8 +162,9 @@ typedef struct fmmfft_stats {
   int64_t device_bytes_scratch;  /* device bytes of scratch buffers currently held */
   double setup_seconds;          /* wall time of the last fmmfft_compress    */
   int restore_on_tensor_cores;   /* slab restores on the tensor cores (y-z
-                                    planes with n2, n3 multiples of 64): 1 in
-                                    3xTF32, 2 in BF16x3; 0 CUDA cores         */
+                                    planes of 32 or 64 per side, or multiples
+                                    of 64): 1 in 3xTF32, 2 in BF16x3; 0 CUDA
+                                    cores                                     */
   int kernel_launches;           /* kernels one fmmfft_translate launches    */
   int large_planes;              /* 1 when the y-z pass keeps restored slabs
                                     in global scratch (planes too large for

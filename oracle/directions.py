@@ -6,7 +6,7 @@ The paper samples directions as the Cartesian product of quadrature points in
 theta and phi and gives the number of multipoles L as a function of the box
 radius and the desired number of accurate digits.  Readings taken here:
   * theta nodes: Gauss-Legendre in x = cos(theta), L + 1 of them;
-  * phi nodes: uniform, N_phi = 2(L + 1) by default ("baseline" rule), or
+  * phi nodes: uniform, N_phi = 2(L + 1) by default ("benchmark" rule), or
     N_phi = 2L + 1 ("paper" rule, N_dir = (L+1)(2L+1) as printed in Sec. II.A);
   * ordering: theta-major, p = i * N_phi + j with x_i ascending and
     phi_j = 2 pi j / N_phi;
@@ -50,15 +50,15 @@ def gauss_legendre(n: int) -> tuple[np.ndarray, np.ndarray]:
     return nodes[order], weights[order]
 
 
-def nphi_for(L: int, rule: str = "baseline") -> int:
-    if rule == "baseline":
+def nphi_for(L: int, rule: str = "benchmark") -> int:
+    if rule == "benchmark":
         return 2 * (L + 1)
     if rule == "paper":
         return 2 * L + 1
     raise ValueError(f"unknown nphi rule {rule!r}")
 
 
-def direction_grid(L: int, rule: str = "baseline"):
+def direction_grid(L: int, rule: str = "benchmark"):
     """Unit directions k_p (N_dir x 3) and quadrature weights w_p (Sec. II.A, Eq. 6).
 
     Weights integrate over the unit sphere: sum_p w_p = 4 pi.

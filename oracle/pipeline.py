@@ -38,7 +38,7 @@ class Plan:
     a: float = 0.5        # box edge (wavelengths when k0 = 2 pi)
     k0: float = 2 * np.pi
     L: int = 5
-    nphi_rule: str = "baseline"
+    nphi_rule: str = "benchmark"
     near_rule: str = "chebyshev"
     prefactor: str = "unit"
     kappa: float = 4.0

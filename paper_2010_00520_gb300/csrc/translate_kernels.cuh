@@ -62,8 +62,9 @@ struct YZParams {
   long long slot_elems;
 };
 
-// Plans whose restore runs on the tensor cores (3xTF32): complex64, 64 x 64
-// planes, and for the Tucker-like format at most 64 columns of H_p[x].
+// Plans whose restore can run on the tensor cores (3xTF32 or BF16x3):
+// complex64, planes of 32 or 64 per side or multiples of 64, and (checked on
+// the host) for the Tucker-like format at most 64 columns of H_p[x].
 template <typename R, int N2, int N3, int FMT>
 struct TcRestore {
   // 64-multiples (tiled over larger planes), or planes of 32 and 64 that one

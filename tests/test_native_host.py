@@ -73,7 +73,7 @@ def test_directions_match_oracle(native, L, rule):
     try:
         native.fmmfft_plan_set(h, native.FMMFFT_KEY_NPHI_RULE, rule)
         kh, w = native.fmmfft_plan_directions(h)
-        kh2, w2 = dr.direction_grid(L, "baseline" if rule == 0 else "paper")
+        kh2, w2 = dr.direction_grid(L, "benchmark" if rule == 0 else "paper")
         np.testing.assert_allclose(kh, kh2, atol=1e-14)
         np.testing.assert_allclose(w, w2, atol=1e-14)
         assert abs(w.sum() - 4 * np.pi) < 1e-12
