@@ -301,7 +301,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=0, help="override the RHS count (profiling cases)")
     ap.add_argument("--only", default="both", choices=["both", "compressed", "plain"])
-    ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "bf16x3", "fp32"],
+    ap.add_argument("--restore", default="3xtf32", choices=["3xtf32", "bf16x3", "tf32", "fp32"],
                     help="restore arithmetic of the compressed arm: tensor cores (3xTF32 or BF16x3) or FP32 CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "directions"],
@@ -375,6 +375,8 @@ def main():
             prec = F.FMMFFT_PREC_C64_3XTF32
         elif name == "compressed" and args.restore == "bf16x3":
             prec = F.FMMFFT_PREC_C64_BF16X3
+        elif name == "compressed" and args.restore == "tf32":
+            prec = F.FMMFFT_PREC_C64_TF32
         else:
             prec = F.FMMFFT_PREC_C64
         F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, prec)
@@ -551,7 +553,9 @@ def main():
                                  "FP32 FFTs, 3xTF32 restores on the tensor cores (tcgen05, FP32 accumulate)"
                                  if st.get("restore_on_tensor_cores") == 1 else
                                  "FP32 FFTs, BF16x3 restores on the tensor cores (tcgen05, FP32 accumulate)"
-                                 if st.get("restore_on_tensor_cores") == 2 else "FP32 FFTs and FP32 restores"),
+                                 if st.get("restore_on_tensor_cores") == 2 else
+                                 "FP32 FFTs, single-TF32 restores on the tensor cores (ablation)"
+                                 if st.get("restore_on_tensor_cores") == 3 else "FP32 FFTs and FP32 restores"),
                    "large_planes": bool(st.get("large_planes")),
                    "schedule": {name: dict(zip(("xrows", "tc_slab", "tc_gemm", "serial_prepass"),
                                                [int(v) for v in F.fmmfft_plan_stats(h)["schedule"]]))

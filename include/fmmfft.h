@@ -88,11 +88,15 @@ enum {
   FMMFFT_PREC_C64_3XTF32 = 2,    /* FP32 fields and FFTs, restores on the tensor
                                     cores as three TF32 products (big x big,
                                     big x small, small x big), FP32 accumulate;
-                                    y-z planes whose sides are not multiples of
-                                    64 restore on the CUDA cores in FP32     */
-  FMMFFT_PREC_C64_BF16X3 = 3     /* as above with bf16 hi/lo splits (hi x hi +
+                                    y-z planes of other sides than 32, 64 or
+                                    multiples of 64 restore on the CUDA cores */
+  FMMFFT_PREC_C64_BF16X3 = 3,    /* as above with bf16 hi/lo splits (hi x hi +
                                     lo x hi + hi x lo, kind::f16 products),
                                     relative error near 2^-16 per product    */
+  FMMFFT_PREC_C64_TF32 = 4       /* as 3XTF32 with one TF32 product (operands
+                                    rounded to TF32, no split): relative error
+                                    near 2^-11 per product, an ablation of the
+                                    split modes, coarser than a 1e-4 tolerance */
 };
 
 /* ---- keys of fmmfft_plan_set (all before fmmfft_compress) -------------- */
@@ -163,8 +167,8 @@ typedef struct fmmfft_stats {
   double setup_seconds;          /* wall time of the last fmmfft_compress    */
   int restore_on_tensor_cores;   /* slab restores on the tensor cores (y-z
                                     planes of 32 or 64 per side, or multiples
-                                    of 64): 1 in 3xTF32, 2 in BF16x3; 0 CUDA
-                                    cores                                     */
+                                    of 64): 1 in 3xTF32, 2 in BF16x3, 3 in
+                                    single TF32; 0 CUDA cores                 */
   int kernel_launches;           /* kernels one fmmfft_translate launches    */
   int large_planes;              /* 1 when the y-z pass keeps restored slabs
                                     in global scratch (planes too large for

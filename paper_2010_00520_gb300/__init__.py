@@ -35,6 +35,7 @@ FMMFFT_NOALLOC_SCRATCH_BYTES = 32 << 20
 FMMFFT_FORMAT_NONE, FMMFFT_FORMAT_3D, FMMFFT_FORMAT_4D = 0, 3, 4
 FMMFFT_DECOMP_NONE, FMMFFT_DECOMP_TUCKER, FMMFFT_DECOMP_TT, FMMFFT_DECOMP_HTUCKER = 0, 1, 2, 3
 FMMFFT_PREC_C128, FMMFFT_PREC_C64, FMMFFT_PREC_C64_3XTF32, FMMFFT_PREC_C64_BF16X3 = 0, 1, 2, 3
+FMMFFT_PREC_C64_TF32 = 4
 FMMFFT_KEY_PRECISION = 1
 FMMFFT_KEY_NPHI_RULE = 2
 FMMFFT_KEY_NEAR_RULE = 3

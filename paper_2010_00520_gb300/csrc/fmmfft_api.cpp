@@ -210,6 +210,7 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   for (int i = 0; i < p->n_stages; ++i) a.stages[i] = p->stages[i];
   a.status = p->d_status;
   a.tc = fmm::tc_restore_applies(a) && p->sched.tc_slab != 0 ? fmm::tc_kind(p->precision) : 0;
+  a.tc_single = p->precision == FMMFFT_PREC_C64_TF32 ? 1 : 0;
   a.tc_gemm = p->sched.tc_gemm != 0 ? fmm::tc_kind(p->precision) : 0;
   a.xrows = p->sched.xrows;
   a.no_overlap = p->sched.no_overlap;
@@ -356,7 +357,8 @@ fmm::OperatorSpec spec_of(const fmmfft_plan_s* p) {
 
 bool precision_supported(const fmmfft_plan_s* p) {
   return p->precision == FMMFFT_PREC_C128 || p->precision == FMMFFT_PREC_C64 ||
-         p->precision == FMMFFT_PREC_C64_3XTF32 || p->precision == FMMFFT_PREC_C64_BF16X3;
+         p->precision == FMMFFT_PREC_C64_3XTF32 || p->precision == FMMFFT_PREC_C64_BF16X3 ||
+         p->precision == FMMFFT_PREC_C64_TF32;
 }
 
 bool check_supported(fmmfft_plan_s* p) {
@@ -495,7 +497,7 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
   const int iv = (int)v;
   switch (key) {
     case FMMFFT_KEY_PRECISION:
-      if (iv < FMMFFT_PREC_C128 || iv > FMMFFT_PREC_C64_BF16X3 || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      if (iv < FMMFFT_PREC_C128 || iv > FMMFFT_PREC_C64_TF32 || iv != v) return FMMFFT_ERR_INVALID_ARG;
       p->precision = iv;
       return FMMFFT_OK;
     case FMMFFT_KEY_NPHI_RULE:
@@ -997,7 +999,7 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   o->setup_seconds = p->setup_seconds;
   if (p->ready) {
     const fmm::TranslateArgs a = base_args(p);
-    o->restore_on_tensor_cores = a.tc;
+    o->restore_on_tensor_cores = a.tc == 1 && a.tc_single ? 3 : a.tc;
     o->kernel_launches = a.n_stages + 3;
     o->large_planes = a.large;
     o->schedule[0] = p->sched.xrows;

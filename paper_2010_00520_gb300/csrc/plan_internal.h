@@ -86,6 +86,7 @@ struct TranslateArgs {
   const SlabDesc* slab;              // device, n_dir entries
   int rmax_a, rmax_b;                // largest ra, rb over directions
   int tc;                            // slab restores on the tensor cores: 1 3xTF32, 2 BF16x3
+  int tc_single;                     // 1: single TF32 products instead of 3xTF32 (tc == 1, pre-pass)
   // large y-z planes (persistent yz kernel, slabs in global scratch)
   int large;                         // set by plan_yz
   long long slot_elems;              // scratch elements per block (set by plan_yz)

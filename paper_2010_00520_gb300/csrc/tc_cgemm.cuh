@@ -192,6 +192,7 @@ struct TcState {
   uint32_t tmem;       // TMEM base address of D
   uint32_t phase;      // parity of the next mbarrier phase
   bool ok;             // false once a wait ran out (results invalid)
+  bool single;         // 3xTF32 path: one TF32 product (big x big) only
 };
 
 // Block-wide set-up: `buf` (kTcSmemBytes, 16-byte aligned) holds the operand
@@ -213,6 +214,7 @@ __device__ __forceinline__ TcState tc_setup(void* buf, uint64_t* bar, uint32_t* 
   s.tmem = *slot;
   s.phase = 0;
   s.ok = true;
+  s.single = false;
   return s;
 }
 
@@ -448,12 +450,14 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
       const uint32_t brb = to_tf32(b.x), bib = to_tf32(b.y);
       Ab[o0] = arb;
       Ab[o1] = aib;
-      As[o0] = to_tf32(a.x - __uint_as_float(arb));
-      As[o1] = to_tf32(a.y - __uint_as_float(aib));
       Bb[o0] = brb;
       Bb[o1] = bib;
-      Bs[o0] = to_tf32(b.x - __uint_as_float(brb));
-      Bs[o1] = to_tf32(b.y - __uint_as_float(bib));
+      if (!s.single) {
+        As[o0] = to_tf32(a.x - __uint_as_float(arb));
+        As[o1] = to_tf32(a.y - __uint_as_float(aib));
+        Bs[o0] = to_tf32(b.x - __uint_as_float(brb));
+        Bs[o1] = to_tf32(b.y - __uint_as_float(bib));
+      }
     }
     fence_async_smem();
     __syncthreads();
@@ -465,8 +469,10 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
         const uint32_t step = ks * 2 * 128;        // two core matrices along K
         const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
         tc_mma(s.tmem, tc_desc<KC>(ab + step), tc_desc<KC>(bb + step), idesc, acc0);
-        tc_mma(s.tmem, tc_desc<KC>(as + step), tc_desc<KC>(bb + step), idesc, 1u);
-        tc_mma(s.tmem, tc_desc<KC>(ab + step), tc_desc<KC>(bs + step), idesc, 1u);
+        if (!s.single) {
+          tc_mma(s.tmem, tc_desc<KC>(as + step), tc_desc<KC>(bb + step), idesc, 1u);
+          tc_mma(s.tmem, tc_desc<KC>(ab + step), tc_desc<KC>(bs + step), idesc, 1u);
+        }
       }
       tc_commit(s.mbar);
     }

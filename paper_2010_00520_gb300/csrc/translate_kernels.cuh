@@ -56,6 +56,7 @@ struct YZParams {
   int rmax_a, rmax_b;  // shared-memory capacity of the launch (ranks)
   int* status;
   int tc;              // restore on the tensor cores (TcRestore): 1 3xTF32, 2 BF16x3
+  int tc_single;       // with tc == 1: one TF32 product instead of three
   int n_dir;           // directions of this launch: p0 .. p0 + n_dir - 1
   int p0;
   void* slab_scratch;  // large planes: one slot of slot_elems per block
@@ -363,9 +364,9 @@ constexpr int kRestoreKC = 64;
 // occupancy
 constexpr int kTcKCLarge = 32;
 
-template <bool BF16>   // BF16: BF16x3 products, else 3xTF32
+template <bool BF16>   // BF16: BF16x3 products, else 3xTF32 (single TF32 with `single`)
 __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDesc* __restrict__ descs,
-                                                                    int* status) {
+                                                                    int* status, int single) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
   __shared__ uint64_t tc_bar;
@@ -377,6 +378,7 @@ __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDe
   float2* Cm = reinterpret_cast<float2*>(d.C) + (size_t)m0 * d.N + n0;
   const int K = d.K, N = d.N;
   TcState tc = tc_setup(smem_raw, &tc_bar, &tmem_slot);
+  tc.single = single != 0;
   tc_cgemm64<true, BF16>(tc, min(64, d.M - m0), min(64, d.N - n0), K, [&](int m, int k) { return A[(size_t)m * K + k]; },
                    [&](int k, int n) { return B[(size_t)k * N + n]; }, Cm, N, 1.0f);
   if (!tc.ok && threadIdx.x == 0) atomicOr(status, kStatusTcTimeout);
@@ -543,6 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       __shared__ uint32_t tmem_slot;
       __shared__ uint64_t tc_bar;
       TcState tc = tc_setup(work, &tc_bar, &tmem_slot);
+      tc.single = P.tc_single != 0;
       const float2* U3 = reinterpret_cast<const float2*>(d.u3);
       const float2* Hf = reinterpret_cast<const float2*>(H);
       if constexpr (FMT == 1) {
@@ -643,7 +646,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
   __shared__ uint32_t tmem_slot;
   __shared__ uint64_t tc_bar;
   TcState tc;
-  if constexpr (TC != 0) tc = tc_setup(plane, &tc_bar, &tmem_slot);
+  if constexpr (TC != 0) {
+    tc = tc_setup(plane, &tc_bar, &tmem_slot);
+    tc.single = P.tc_single != 0;
+  }
   const int items = P.n1 * P.n_dir;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int x = it % P.n1, p = P.p0 + it / P.n1;

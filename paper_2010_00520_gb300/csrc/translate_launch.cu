@@ -94,7 +94,9 @@ static size_t yz_smem_any(int n2, int n3, int fmt, int ra, int rb, bool tc) {
 }
 
 int tc_kind(int precision) {
-  return precision == FMMFFT_PREC_C64_3XTF32 ? 1 : (precision == FMMFFT_PREC_C64_BF16X3 ? 2 : 0);
+  return (precision == FMMFFT_PREC_C64_3XTF32 || precision == FMMFFT_PREC_C64_TF32)
+             ? 1
+             : (precision == FMMFFT_PREC_C64_BF16X3 ? 2 : 0);
 }
 
 bool tc_restore_applies(const TranslateArgs& a) {
@@ -232,9 +234,9 @@ static cudaError_t launch_all(const TranslateArgs& a) {
     const GemmStage& g = a.stages[i];
     dim3 grid((g.max_n + kGemmT - 1) / kGemmT, (g.max_m + kGemmT - 1) / kGemmT, g.batch);
     if (tc_gemm && sizeof(R) == 4 && a.tc_gemm == 2)
-      cgemm_batched_tc_kernel<true><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status);
+      cgemm_batched_tc_kernel<true><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status, 0);
     else if (tc_gemm && sizeof(R) == 4)
-      cgemm_batched_tc_kernel<false><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status);
+      cgemm_batched_tc_kernel<false><<<grid, kThreads, kTcGemmSmem, ps>>>(g.desc, a.status, a.tc_single);
     else cgemm_batched_kernel<R><<<grid, kThreads, 0, ps>>>(g.desc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -266,6 +268,7 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   Y.rmax_b = a.rmax_b;
   Y.status = a.status;
   Y.tc = a.tc;
+  Y.tc_single = a.tc_single;
   Y.n_dir = nw;
   Y.p0 = a.p0;
   Y.slab_scratch = a.slab_scratch;
