@@ -60,7 +60,7 @@ FORMAT_NAMES = {(3, 1): "tucker3d", (3, 2): "tt3d", (4, 1): "tucker4d", (4, 2): 
 FAR_NB = 16                  # basis functions per box of the far-field steps (Eqs. 4, 6)
 CPU_SAMPLE_DIRS = 8          # directions (x 8 fields) the CPU baseline translates
 # version of the yz kernel the committed DRAM-traffic figure was taken on
-YZ_KERNEL_VERSION = 4
+YZ_KERNEL_VERSION = 5
 
 
 def _units(n, n_dir, nrhs):
