@@ -117,3 +117,36 @@ def test_far_field_argument_errors(native, cuda):
         assert e.value.status == F.FMMFFT_ERR_INVALID_ARG
     finally:
         F.fmmfft_plan_destroy(h)
+
+
+def test_single_direction_and_many_rhs(native, cuda):
+    """Degenerate grid: L = 0 with N_phi = 2L + 1 gives one direction (three of
+    the four direction quarters of the disaggregation cluster are empty); 37
+    right-hand sides exercise the RHS tiles' ragged tail.  The chain against
+    the oracle's."""
+    F, torch = native, cuda
+    K, L, nb, nrhs = (5, 6, 7), 0, 3, 37
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, 0, 0, 0.0)
+    try:
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_NPHI_RULE, 1)
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C128)
+        F.fmmfft_compress(h)
+        assert F.fmmfft_plan_stats(h)["n_dir"] == 1
+        _, w = F.fmmfft_plan_directions(h)
+        box = (K[2], K[1], K[0])
+        P = _cg(61, (1, 2, nb) + box)
+        I = _cg(62, (nrhs, nb) + box)
+        dP, dI = _dev(torch, P, True), _dev(torch, I, True)
+        dA = torch.empty((1, 2, nrhs) + box, dtype=dP.dtype, device="cuda")
+        dB, dy = torch.empty_like(dA), torch.empty_like(dI)
+        s = torch.cuda.current_stream()
+        F.fmmfft_aggregate(h, dP, dI, dA, nb, nrhs, s)
+        F.fmmfft_translate(h, dA, dB, nrhs, s)
+        F.fmmfft_disaggregate(h, dP, dB, dy, nb, nrhs, s)
+        torch.cuda.synchronize()
+        plan = pl.Plan(K=K, L=L, nphi_rule="paper")
+        ops = pl.operators(plan)
+        ref = ff.disaggregate(P, w, pl.translate_with(lambda p: ops[p], ff.aggregate(P, I)))
+        assert _rel(dy.cpu().numpy(), ref) <= 1e-10
+    finally:
+        F.fmmfft_plan_destroy(h)
