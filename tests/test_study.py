@@ -85,3 +85,20 @@ def test_study_row_matches_library_statistics(study, native):
     finally:
         native.fmmfft_plan_destroy(h)
     assert "| htucker | 4 |" in study.table([row])
+
+
+def test_study_command_line_writes_rows(study, tmp_path, capsys):
+    """`python -m paper_2010_00520_gb300.study`: a host-only sweep of the
+    structure size (a 1-lambda sphere: 2 x 2 x 2 boxes of 0.5 lambda) writes
+    one row per case, as JSON lines, a table and a JSON file."""
+    import json
+    out = tmp_path / "rows.json"
+    study.main(["size", "--diameters", "1", "1.5", "--formats", "tucker3d", "tt3d", "--tol", "1e-4",
+                "--json", str(out)])
+    rows = json.loads(out.read_text())
+    assert [r["case"]["fmt"] for r in rows] == ["tucker3d", "tt3d", "tucker3d", "tt3d"]
+    assert [r["case"]["K"] for r in rows] == [2, 2, 3, 3]
+    assert all(r["n_dir"] == 435 and r["L"] == 14 for r in rows)
+    assert all(0.0 <= r["saving"] < 1.0 and r["gpu"] == {} for r in rows)
+    printed = capsys.readouterr().out
+    assert printed.count('{"case"') == 4 and "| tucker3d | 2 |" in printed
