@@ -242,3 +242,50 @@ def test_shard_plan_directions_are_a_block_of_the_grid(native):
         assert np.allclose(kh3, ref[7:18], atol=1e-14)
     finally:
         native.fmmfft_plan_destroy(h)
+
+
+def test_far_field_arguments_are_checked_before_any_launch(native):
+    """fmmfft_aggregate / fmmfft_disaggregate reject bad arguments on the host,
+    before touching a device (addresses below are never dereferenced)."""
+    K, L = (4, 4, 4), 1
+    h = native.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 0, 0, 0.0)
+    try:
+        nd = native.fmmfft_plan_stats(h)["n_dir"]
+        V, nb, nrhs = 64, 2, 1
+        base = 1 << 40                                    # 256-byte aligned fake addresses
+        P, I, A = base, base + (1 << 30), base + (2 << 30)
+        cases = [
+            (native.fmmfft_aggregate, (h, P, I, A, 0, nrhs), native.FMMFFT_ERR_INVALID_ARG),     # nb < 1
+            (native.fmmfft_aggregate, (h, P, I, A, 49, nrhs), native.FMMFFT_ERR_UNSUPPORTED),    # nb > 48
+            (native.fmmfft_aggregate, (h, P, I, A, nb, 0), native.FMMFFT_ERR_INVALID_ARG),       # nrhs < 1
+            (native.fmmfft_aggregate, (h, P, I, A, nb, 5000), native.FMMFFT_ERR_INVALID_ARG),
+            (native.fmmfft_aggregate, (h, 0, I, A, nb, nrhs), native.FMMFFT_ERR_INVALID_ARG),    # null
+            (native.fmmfft_aggregate, (h, P + 4, I, A, nb, nrhs), native.FMMFFT_ERR_INVALID_ARG),  # misaligned
+            # output overlapping the patterns / the coefficients
+            (native.fmmfft_aggregate, (h, P, I, P + 8 * (nd * 2 * nb * V - 1), nb, nrhs),
+             native.FMMFFT_ERR_INVALID_ARG),
+            (native.fmmfft_aggregate, (h, P, I, I - 8, nb, nrhs), native.FMMFFT_ERR_INVALID_ARG),
+            (native.fmmfft_disaggregate, (h, P, A, P, nb, nrhs), native.FMMFFT_ERR_INVALID_ARG),
+            (native.fmmfft_disaggregate, (h, P, A, A + 8, nb, nrhs), native.FMMFFT_ERR_INVALID_ARG),
+        ]
+        for fn, args, status in cases:
+            with pytest.raises(native.FmmfftError) as e:
+                fn(*args)
+            assert e.value.status == status, (fn.__name__, args[4:])
+        with pytest.raises(native.FmmfftError) as e:
+            native.fmmfft_aggregate(0, P, I, A, nb, nrhs)
+        assert e.value.status == native.FMMFFT_ERR_INVALID_ARG
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+def test_host_blocks_key(native):
+    h = native.fmmfft_plan_create(4, 4, 4, 0.5, 2 * np.pi, 1, 0, 0, 0.0)
+    try:
+        for ok in (0, 1, 12, 64):
+            native.fmmfft_plan_set(h, native.FMMFFT_KEY_HOST_BLOCKS, ok)
+        for bad in (-1, 65, 2.5):
+            with pytest.raises(native.FmmfftError):
+                native.fmmfft_plan_set(h, native.FMMFFT_KEY_HOST_BLOCKS, bad)
+    finally:
+        native.fmmfft_plan_destroy(h)
