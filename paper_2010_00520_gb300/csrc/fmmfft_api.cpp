@@ -899,24 +899,34 @@ int fmmfft_translate_host(fmmfft_plan p, const void* S_in_host, void* S_out_host
   cudaEvent_t ev_start = p->hev[0], ev_done = p->hev[1];
   cudaEvent_t* ev_in = p->hev + 2;
   cudaEvent_t* ev_out = ev_in + kHostBlocksMax;
+  // on a failure part-way, let the copies already queued finish before
+  // returning: they read and write the caller's host buffers
+  auto fail = [&]() {
+    cudaGetLastError();
+    cudaStreamSynchronize(p->h2d);
+    cudaStreamSynchronize(p->d2h);
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  };
   const int per = (p->n_dir + blocks - 1) / blocks;
   const char* hin = (const char*)S_in_host;
   char* hout = (char*)S_out_host;
   // the copies must follow earlier work of `stream` on these buffers
   if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaStreamWaitEvent(p->h2d, ev_start, 0) != cudaSuccess ||
       cudaStreamWaitEvent(p->d2h, ev_start, 0) != cudaSuccess)
-    return FMMFFT_ERR_CUDA;
+    return fail();
   for (int k = 0, p0 = 0; p0 < p->n_dir; ++k, p0 += per) {
     const size_t off = (size_t)p0 * per_dir, len = (size_t)std::min(per, p->n_dir - p0) * per_dir;
     if (cudaMemcpyAsync(din + off, hin + off, len, cudaMemcpyHostToDevice, p->h2d) != cudaSuccess ||
         cudaEventRecord(ev_in[k], p->h2d) != cudaSuccess)
-      return FMMFFT_ERR_CUDA;
+      return fail();
   }
   p->last_stream = s;
   for (int k = 0, p0 = 0; p0 < p->n_dir; ++k, p0 += per) {
     const int nw = std::min(per, p->n_dir - p0);
     const size_t off = (size_t)p0 * per_dir, len = (size_t)nw * per_dir;
-    if (cudaStreamWaitEvent(s, ev_in[k], 0) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, ev_in[k], 0) != cudaSuccess) return fail();
     fmm::TranslateArgs a = base_args(p);
     a.nrhs = nrhs;
     a.s_in = din;
@@ -926,16 +936,13 @@ int fmmfft_translate_host(fmmfft_plan p, const void* S_in_host, void* S_out_host
     a.p0 = p0;
     a.nw = nw;
     a.prepass = k == 0;
-    if (fmm::launch_translate(a) != cudaSuccess) {
-      cudaGetLastError();
-      return FMMFFT_ERR_CUDA;
-    }
+    if (fmm::launch_translate(a) != cudaSuccess) return fail();
     if (cudaEventRecord(ev_out[k], s) != cudaSuccess || cudaStreamWaitEvent(p->d2h, ev_out[k], 0) != cudaSuccess ||
         cudaMemcpyAsync(hout + off, dout + off, len, cudaMemcpyDeviceToHost, p->d2h) != cudaSuccess)
-      return FMMFFT_ERR_CUDA;
+      return fail();
   }
   if (cudaEventRecord(ev_done, p->d2h) != cudaSuccess || cudaStreamWaitEvent(s, ev_done, 0) != cudaSuccess)
-    return FMMFFT_ERR_CUDA;
+    return fail();
   return cudaStreamSynchronize(s) == cudaSuccess ? FMMFFT_OK : FMMFFT_ERR_CUDA;
 }
 
