@@ -345,8 +345,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if not os.path.exists(F.LIB_PATH):
-        from paper_2010_00520_gb300 import build as _b
-        _b.build()
+        # one builder per node; the other ranks wait for it
+        if local == 0:
+            from paper_2010_00520_gb300 import build as _b
+            _b.build()
+        if dist is not None:
+            dist.barrier()
 
     wl_name = args.workload
     W = dict(WORKLOADS[wl_name], a=0.5, k0=2 * math.pi)
