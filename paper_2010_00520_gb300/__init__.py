@@ -7,6 +7,14 @@ tensors (their data_ptr() is used) or as integer addresses; streams as torch
 streams, integer handles or None (the current torch stream when torch is
 loaded, else the legacy default stream).
 
+A C pointer carries neither its memory space nor its length, so for tensors
+and NumPy arrays the binding checks what the library cannot: the buffer is
+contiguous, lives where the entry point expects it (device memory for the
+device entry points, host memory for fmmfft_translate_host) and holds at
+least the bytes the plan's extents address.  A failed check raises
+FmmfftError(FMMFFT_ERR_INVALID_ARG) before anything is launched.  Integer
+addresses are passed through as given, unchecked.
+
 Importing the package does not load the library; the first call does, and it
 raises if libfmmfft.so is missing (build it with
 ``python -m paper_2010_00520_gb300.build``).  There is no fallback path.
@@ -156,6 +164,68 @@ def _ptr(x) -> int:
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
+def _extents(plan):
+    """(directions, boxes per field, bytes per complex element) of `plan`."""
+    s = _Stats()
+    _check(lib().fmmfft_plan_stats(plan, ctypes.byref(s)), "fmmfft_plan_stats")
+    return s.n_dir, s.K[0] * s.K[1] * s.K[2], 16 if s.precision == FMMFFT_PREC_C128 else 8
+
+
+def _sized(*bufs) -> bool:
+    """True when any buffer is an object whose size the binding can check."""
+    return any(b is not None and not isinstance(b, int) for b in bufs)
+
+
+def _buffer(x, device: bool, need, where: str, what: str) -> int:
+    """Address of one field, pattern or coefficient buffer after the checks a
+    bare pointer cannot carry.  A torch tensor or NumPy array must be
+    contiguous, in device memory for a device entry point (a kernel given a
+    host address faults, or on a GPU that reaches host memory reads the wrong
+    data) or in host memory for the host entry point, and hold at least
+    `need` bytes (None: not checked) -- the kernels address the full extents
+    of the plan.  None and integer addresses pass through unchecked."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if isinstance(x, np.ndarray):
+        on_device, contiguous, nbytes = False, bool(x.flags.c_contiguous), int(x.nbytes)
+    elif hasattr(x, "is_cuda") and hasattr(x, "numel") and hasattr(x, "element_size"):
+        on_device = bool(x.is_cuda)
+        contiguous = bool(x.is_contiguous())
+        nbytes = int(x.numel()) * int(x.element_size())
+    else:
+        return _ptr(x)
+    if on_device != device:
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG,
+                          f"{where}: {what} is in {'device' if on_device else 'host'} memory, "
+                          f"this entry point takes {'device' if device else 'host'} memory")
+    if not contiguous:
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG, f"{where}: {what} is not contiguous")
+    if need is not None and nbytes < need:
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG,
+                          f"{where}: {what} holds {nbytes} bytes, the plan's extents need {need}")
+    return _ptr(x)
+
+
+def _fields(plan, S_in, S_out, nrhs, device: bool, where: str):
+    """Checked addresses of the input and output fields [n_dir][2][nrhs][Kz][Ky][Kx]."""
+    need = None
+    if nrhs >= 1 and _sized(S_in, S_out):
+        nd, V, es = _extents(plan)
+        need = nd * 2 * nrhs * V * es
+    return (_buffer(S_in, device, need, where, "S_in"), _buffer(S_out, device, need, where, "S_out"))
+
+
+def _far_field(plan, patterns, per_box, spectra, nb, nrhs, where: str, names):
+    """Checked addresses of the far-field buffers: patterns [n_dir][2][nb][V],
+    the per-box coefficients or results [nrhs][nb][V] and the spectra
+    [n_dir][2][nrhs][V]."""
+    need = (None, None, None)
+    if nb >= 1 and nrhs >= 1 and _sized(patterns, per_box, spectra):
+        nd, V, es = _extents(plan)
+        need = (nd * 2 * nb * V * es, nrhs * nb * V * es, nd * 2 * nrhs * V * es)
+    return tuple(_buffer(b, True, n, where, w) for b, n, w in zip((patterns, per_box, spectra), need, names))
+
+
 def _stream(s) -> int:
     if s is None:
         import sys
@@ -281,8 +351,10 @@ def fmmfft_batch_create(plans) -> int:
 
 def fmmfft_batch_translate(batch, S_in, S_out, nrhs, stream=None):
     n = len(S_in)
-    ins = (ctypes.c_void_p * n)(*[_ptr(x) for x in S_in])
-    outs = (ctypes.c_void_p * n)(*[_ptr(x) for x in S_out])
+    ins = (ctypes.c_void_p * n)(*[_buffer(x, True, None, "fmmfft_batch_translate", f"S_in[{i}]")
+                                  for i, x in enumerate(S_in)])
+    outs = (ctypes.c_void_p * n)(*[_buffer(x, True, None, "fmmfft_batch_translate", f"S_out[{i}]")
+                                   for i, x in enumerate(S_out)])
     r, rp = _ints(nrhs)
     _check(lib().fmmfft_batch_translate(batch, ins, outs, rp, _stream(stream)), "fmmfft_batch_translate")
 
@@ -292,20 +364,22 @@ def fmmfft_batch_destroy(batch):
 
 
 def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):
-    _check(lib().fmmfft_translate(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
-           "fmmfft_translate")
+    i, o = _fields(plan, S_in, S_out, int(nrhs), True, "fmmfft_translate")
+    _check(lib().fmmfft_translate(plan, i, o, int(nrhs), _stream(stream)), "fmmfft_translate")
 
 
 def fmmfft_aggregate(plan, patterns, currents, A, nb, nrhs, stream=None):
     """Eq. 4 on the device: A[p][c][r][v] = sum_i P[p][c][i][v] I[r][i][v]."""
-    _check(lib().fmmfft_aggregate(plan, _ptr(patterns), _ptr(currents), _ptr(A), int(nb), int(nrhs),
-                                  _stream(stream)), "fmmfft_aggregate")
+    p, c, a = _far_field(plan, patterns, currents, A, int(nb), int(nrhs), "fmmfft_aggregate",
+                         ("patterns", "currents", "A"))
+    _check(lib().fmmfft_aggregate(plan, p, c, a, int(nb), int(nrhs), _stream(stream)), "fmmfft_aggregate")
 
 
 def fmmfft_disaggregate(plan, patterns, B, y, nb, nrhs, stream=None):
     """Eq. 6 on the device: y[r][i][v] = sum_p w_p sum_c conj(P[p][c][i][v]) B[p][c][r][v]."""
-    _check(lib().fmmfft_disaggregate(plan, _ptr(patterns), _ptr(B), _ptr(y), int(nb), int(nrhs),
-                                     _stream(stream)), "fmmfft_disaggregate")
+    p, o, b = _far_field(plan, patterns, y, B, int(nb), int(nrhs), "fmmfft_disaggregate",
+                         ("patterns", "y", "B"))
+    _check(lib().fmmfft_disaggregate(plan, p, b, o, int(nb), int(nrhs), _stream(stream)), "fmmfft_disaggregate")
 
 
 def fmmfft_translate_noalloc(plan, S_in, S_out, nrhs, stream=None):
@@ -313,13 +387,13 @@ def fmmfft_translate_noalloc(plan, S_in, S_out, nrhs, stream=None):
     in the library's fixed 32 MiB device array (shared by every call; order
     calls on one stream).  Raises FmmfftError(FMMFFT_ERR_TOO_LARGE) when the
     workload's intermediate does not fit."""
-    _check(lib().fmmfft_translate_noalloc(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
-           "fmmfft_translate_noalloc")
+    i, o = _fields(plan, S_in, S_out, int(nrhs), True, "fmmfft_translate_noalloc")
+    _check(lib().fmmfft_translate_noalloc(plan, i, o, int(nrhs), _stream(stream)), "fmmfft_translate_noalloc")
 
 
 def fmmfft_translate_host(plan, S_in, S_out, nrhs, stream=None):
-    _check(lib().fmmfft_translate_host(plan, _ptr(S_in), _ptr(S_out), int(nrhs), _stream(stream)),
-           "fmmfft_translate_host")
+    i, o = _fields(plan, S_in, S_out, int(nrhs), False, "fmmfft_translate_host")
+    _check(lib().fmmfft_translate_host(plan, i, o, int(nrhs), _stream(stream)), "fmmfft_translate_host")
 
 
 def fmmfft_plan_stats(plan) -> dict:

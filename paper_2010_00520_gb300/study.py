@@ -43,7 +43,8 @@ import numpy as np
 from . import (FMMFFT_FORMAT_3D, FMMFFT_FORMAT_4D, FMMFFT_FORMAT_NONE, FMMFFT_DECOMP_HTUCKER,
                FMMFFT_DECOMP_NONE, FMMFFT_DECOMP_TT, FMMFFT_DECOMP_TUCKER, FMMFFT_KEY_EPS_R_IM,
                FMMFFT_KEY_EPS_R_RE, FMMFFT_KEY_KAPPA, FMMFFT_KEY_NEAR_RULE, FMMFFT_KEY_NPHI_RULE,
-               FMMFFT_KEY_PRECISION, FMMFFT_KEY_TRUNC_RULE, FMMFFT_PREC_C64, FMMFFT_ERR_UNSUPPORTED,
+               FMMFFT_KEY_PRECISION, FMMFFT_KEY_TRUNC_RULE, FMMFFT_PREC_C64, FMMFFT_PREC_C128,
+               FMMFFT_ERR_UNSUPPORTED,
                FmmfftError, fmmfft_compress,
                fmmfft_compress_host, fmmfft_multipole_count, fmmfft_plan_create, fmmfft_plan_destroy,
                fmmfft_plan_set, fmmfft_plan_stats, fmmfft_translate)
@@ -167,8 +168,10 @@ def gpu_case(c: StudyCase, row: StudyRow, nrhs=1, precision=FMMFFT_PREC_C64, ste
     nd = row.n_dir
     g = torch.Generator(device="cuda").manual_seed(seed)
     shape = (nd, 2, nrhs, c.K, c.K, c.K)
+    # fields in the plans' precision: complex128 for FMMFFT_PREC_C128
+    cdt = torch.complex128 if precision == FMMFFT_PREC_C128 else torch.complex64
     x = torch.complex(torch.randn(shape, generator=g, device="cuda"),
-                      torch.randn(shape, generator=g, device="cuda")).to(torch.complex64)
+                      torch.randn(shape, generator=g, device="cuda")).to(cdt)
     y = torch.empty_like(x)
     times = {}
     for name, fd, tol in (("compressed", FORMATS[c.fmt], c.tol),
@@ -277,7 +280,8 @@ def main(argv=None):
     ap.add_argument("--gpu", action="store_true", help="also time compressed and plain translations")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--precision", type=int, default=FMMFFT_PREC_C64,
-                    help="FMMFFT_PREC_*: 1 complex64 with FP32 restores (default), 2 3xTF32, 3 BF16x3")
+                    help="FMMFFT_PREC_*: 0 complex128, 1 complex64 with FP32 restores (default), 2 3xTF32, "
+                         "3 BF16x3")
     ap.add_argument("--json", help="write the rows to this file")
     a = ap.parse_args(argv)
     fmts = list(FORMATS) if a.formats == ["all"] else a.formats
