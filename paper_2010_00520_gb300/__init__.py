@@ -268,16 +268,47 @@ def fmmfft_compress(plan):
     _check(lib().fmmfft_compress(plan), "fmmfft_compress")
 
 
+def _import_ranks(plan, ranks, per_dir: int, count: int, where: str):
+    """Rank array of an import (int32, contiguous) and the plan's (n, n_dir).
+    The library reads `count` ranks (per direction for the 3D formats) and,
+    from them, the lengths of the factor arrays; a short rank array would be
+    read past its end, so it is refused here."""
+    st = fmmfft_plan_stats(plan)
+    r = np.ascontiguousarray(ranks, dtype=np.int32).ravel()
+    need = count * (st["n_dir"] if per_dir else 1)
+    if r.size < need:
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG, f"{where}: {r.size} ranks given, the plan needs {need}")
+    return r, tuple(st["n"]), st["n_dir"]
+
+
+def _import_arrays(where: str, ranks, named_arrays, needs):
+    """Contiguous complex128 copies of the factor arrays, each checked to hold
+    at least the complex values its ranks imply (the library reads exactly
+    that many).  Ranks below 1 are left to the library to refuse."""
+    arrs = [_cplx(x) for _, x in named_arrays]
+    if np.all(np.asarray(ranks) >= 1):
+        for (name, _), a, n in zip(named_arrays, arrs, needs):
+            if a.size < n:
+                raise FmmfftError(FMMFFT_ERR_INVALID_ARG,
+                                  f"{where}: {name} holds {a.size} complex values, the ranks need {n}")
+    return arrs
+
+
 def fmmfft_import_plain(plan, That):
-    T = _cplx(That)
+    st = fmmfft_plan_stats(plan)
+    n = st["n"]
+    T, = _import_arrays("fmmfft_import_plain", [1], [("That", That)], [st["n_dir"] * n[0] * n[1] * n[2]])
     _check(lib().fmmfft_import_plain(plan, _dptr(T)), "fmmfft_import_plain")
 
 
 def fmmfft_import_tucker3d(plan, ranks, core, U1, U2, U3):
-    r = np.ascontiguousarray(ranks, dtype=np.int32)
-    arrs = [_cplx(x) for x in (core, U1, U2, U3)]
+    where = "fmmfft_import_tucker3d"
+    r, n, nd = _import_ranks(plan, ranks, True, 3, where)
+    rd = r[:3 * nd].reshape(nd, 3).astype(np.int64)
+    needs = [int(np.prod(rd, axis=1).sum())] + [n[i] * int(rd[:, i].sum()) for i in range(3)]
+    arrs = _import_arrays(where, rd, [("core", core), ("U1", U1), ("U2", U2), ("U3", U3)], needs)
     _check(lib().fmmfft_import_tucker3d(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                        *[_dptr(x) for x in arrs]), "fmmfft_import_tucker3d")
+                                        *[_dptr(x) for x in arrs]), where)
 
 
 def _ints(x):
@@ -286,27 +317,46 @@ def _ints(x):
 
 
 def fmmfft_import_tt3d(plan, ranks, U1, C1, U3):
-    r, rp = _ints(ranks)
-    arrs = [_cplx(x) for x in (U1, C1, U3)]
-    _check(lib().fmmfft_import_tt3d(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_tt3d")
+    where = "fmmfft_import_tt3d"
+    r, n, nd = _import_ranks(plan, ranks, True, 2, where)
+    rd = r[:2 * nd].reshape(nd, 2).astype(np.int64)
+    needs = [n[0] * int(rd[:, 0].sum()), n[1] * int((rd[:, 0] * rd[:, 1]).sum()), n[2] * int(rd[:, 1].sum())]
+    arrs = _import_arrays(where, rd, [("U1", U1), ("C1", C1), ("U3", U3)], needs)
+    _check(lib().fmmfft_import_tt3d(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                    *[_dptr(x) for x in arrs]), where)
 
 
 def fmmfft_import_tucker4d(plan, ranks, core, U1, U2, U3, U4):
-    r, rp = _ints(ranks)
-    arrs = [_cplx(x) for x in (core, U1, U2, U3, U4)]
-    _check(lib().fmmfft_import_tucker4d(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_tucker4d")
+    where = "fmmfft_import_tucker4d"
+    r, n, nd = _import_ranks(plan, ranks, False, 4, where)
+    q = [int(v) for v in r[:4]]
+    dims = (n[0], n[1], n[2], nd)
+    needs = [q[0] * q[1] * q[2] * q[3]] + [dims[i] * q[i] for i in range(4)]
+    arrs = _import_arrays(where, q, [("core", core), ("U1", U1), ("U2", U2), ("U3", U3), ("U4", U4)], needs)
+    _check(lib().fmmfft_import_tucker4d(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        *[_dptr(x) for x in arrs]), where)
 
 
 def fmmfft_import_htucker(plan, ranks, U1, U2, U3, U4, C12, C34, B):
-    r, rp = _ints(ranks)
-    arrs = [_cplx(x) for x in (U1, U2, U3, U4, C12, C34, B)]
-    _check(lib().fmmfft_import_htucker(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_htucker")
+    where = "fmmfft_import_htucker"
+    r, n, nd = _import_ranks(plan, ranks, False, 6, where)
+    q = [int(v) for v in r[:6]]
+    dims = (n[0], n[1], n[2], nd)
+    needs = [dims[i] * q[i] for i in range(4)] + [q[0] * q[1] * q[4], q[2] * q[3] * q[5], q[4] * q[5]]
+    named = [("U1", U1), ("U2", U2), ("U3", U3), ("U4", U4), ("C12", C12), ("C34", C34), ("B", B)]
+    arrs = _import_arrays(where, q, named, needs)
+    _check(lib().fmmfft_import_htucker(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       *[_dptr(x) for x in arrs]), where)
 
 
 def fmmfft_import_tt4d(plan, ranks, U1, C1, C2, U3):
-    r, rp = _ints(ranks)
-    arrs = [_cplx(x) for x in (U1, C1, C2, U3)]
-    _check(lib().fmmfft_import_tt4d(plan, rp, *[_dptr(x) for x in arrs]), "fmmfft_import_tt4d")
+    where = "fmmfft_import_tt4d"
+    r, n, nd = _import_ranks(plan, ranks, False, 3, where)
+    q = [int(v) for v in r[:3]]
+    needs = [n[0] * q[0], q[0] * n[1] * q[1], q[1] * n[2] * q[2], nd * q[2]]
+    arrs = _import_arrays(where, q, [("U1", U1), ("C1", C1), ("C2", C2), ("U3", U3)], needs)
+    _check(lib().fmmfft_import_tt4d(plan, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                    *[_dptr(x) for x in arrs]), where)
 
 
 def fmmfft_compress_host(plan, restored=True):

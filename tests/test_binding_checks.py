@@ -143,3 +143,90 @@ def test_batch_takes_device_buffers(native):
     with pytest.raises(F.FmmfftError) as e:
         F.fmmfft_batch_translate(0, [DeviceBuffer(64)], [DeviceBuffer(64, addr=2 << 40)], [1], 0)
     assert e.value.status == F.FMMFFT_ERR_INVALID_ARG and "memory" not in str(e.value)
+
+
+def _oracle_parts(K, L, fmt, dec, tol):
+    from oracle import pipeline as pl
+    plan = pl.Plan(K=K, L=L)
+    ops = pl.operators(plan)
+    return ops, pl.compress(ops, fmt, dec, tol).parts
+
+
+def _import_args(F, fmt, dec, P, short=None):
+    """The import call of one format with the oracle's factors, laid out as
+    the library's header states; `short` names one array to cut by one value."""
+    cat = lambda xs: np.concatenate([np.ravel(x) for x in xs])
+    if fmt == "3d" and dec == "tucker":
+        fn, ranks = F.fmmfft_import_tucker3d, np.array([t.ranks for t in P], dtype=np.int32)
+        named = [("core", cat([t.core for t in P]))] + \
+                [(f"U{i + 1}", cat([t.factors[i] for t in P])) for i in range(3)]
+    elif fmt == "3d":
+        fn, ranks = F.fmmfft_import_tt3d, np.array([t.ranks for t in P], dtype=np.int32)
+        named = [("U1", cat([t.U1 for t in P])), ("C1", cat([t.cores[0] for t in P])),
+                 ("U3", cat([t.Ud for t in P]))]
+    elif dec == "tucker":
+        fn, ranks = F.fmmfft_import_tucker4d, np.array(P.ranks, dtype=np.int32)
+        named = [("core", P.core)] + [(f"U{i + 1}", u) for i, u in enumerate(P.factors)]
+    elif dec == "htucker":
+        fn, ranks = F.fmmfft_import_htucker, np.array(P.ranks, dtype=np.int32)
+        named = [(f"U{i + 1}", u) for i, u in enumerate(P.U)] + [("C12", P.C12), ("C34", P.C34), ("B", P.B)]
+    else:
+        fn, ranks = F.fmmfft_import_tt4d, np.array(P.ranks, dtype=np.int32)
+        named = [("U1", P.U1), ("C1", P.cores[0]), ("C2", P.cores[1]), ("U3", P.Ud)]
+    arrays = [np.ravel(a)[:-1] if name == short else a for name, a in named]
+    return fn, ranks, arrays, [name for name, _ in named]
+
+
+def _import_status(fn, h, *args):
+    """0 when the import succeeds (a machine with a device), else its status."""
+    import paper_2010_00520_gb300 as F
+    try:
+        fn(h, *args)
+        return 0
+    except F.FmmfftError as e:
+        return e.status
+
+
+FORMATS = [("3d", "tucker", 3, 1), ("3d", "tt", 3, 2), ("4d", "tucker", 4, 1), ("4d", "htucker", 4, 3),
+           ("4d", "tt", 4, 2)]
+
+
+@pytest.mark.parametrize("fmt,dec,cfmt,cdec", FORMATS)
+def test_imports_take_the_oracles_factors_and_refuse_short_arrays(native, fmt, dec, cfmt, cdec):
+    """The oracle's factors pass the binding's length checks and reach the
+    library, whose host-side checks accept them too (on a machine without a
+    device the upload then fails with a status other than
+    FMMFFT_ERR_INVALID_ARG); every factor array one value short, and a short
+    rank array, is refused before the library reads it."""
+    F = native
+    K, L, tol = (6, 5, 7), 2, 1e-3
+    _, P = _oracle_parts(K, L, fmt, dec, tol)
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, cfmt, cdec, tol)
+    try:
+        fn, ranks, arrays, names = _import_args(F, fmt, dec, P)
+        assert _import_status(fn, h, ranks, *arrays) != F.FMMFFT_ERR_INVALID_ARG
+        for name in names:
+            fn, ranks, arrays, _ = _import_args(F, fmt, dec, P, short=name)
+            with pytest.raises(F.FmmfftError) as e:
+                fn(h, ranks, *arrays)
+            assert e.value.status == F.FMMFFT_ERR_INVALID_ARG and f"{name} holds" in str(e.value), name
+        fn, ranks, arrays, _ = _import_args(F, fmt, dec, P)
+        with pytest.raises(F.FmmfftError) as e:
+            fn(h, np.ravel(ranks)[:-1], *arrays)
+        assert e.value.status == F.FMMFFT_ERR_INVALID_ARG and "ranks given" in str(e.value)
+    finally:
+        F.fmmfft_plan_destroy(h)
+
+
+def test_plain_import_takes_the_whole_operator(native):
+    F = native
+    K, L = (6, 5, 7), 2
+    ops, _ = _oracle_parts(K, L, "3d", "tucker", 1e-3)
+    h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, L, 0, 0, 0.0)
+    try:
+        assert _import_status(F.fmmfft_import_plain, h, np.stack(ops)) != F.FMMFFT_ERR_INVALID_ARG
+        with pytest.raises(F.FmmfftError) as e:
+            F.fmmfft_import_plain(h, np.stack(ops[:-1]))
+        assert e.value.status == F.FMMFFT_ERR_INVALID_ARG and "That holds" in str(e.value)
+    finally:
+        F.fmmfft_plan_destroy(h)
