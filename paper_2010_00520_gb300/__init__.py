@@ -206,13 +206,14 @@ def _buffer(x, device: bool, need, where: str, what: str) -> int:
     return _ptr(x)
 
 
-def _fields(plan, S_in, S_out, nrhs, device: bool, where: str):
-    """Checked addresses of the input and output fields [n_dir][2][nrhs][Kz][Ky][Kx]."""
+def _fields(plan, S_in, S_out, nrhs, device: bool, where: str, tag: str = ""):
+    """Checked addresses of the input and output fields [n_dir][2][nrhs][Kz][Ky][Kx]
+    (plan None: memory space and layout only)."""
     need = None
-    if nrhs >= 1 and _sized(S_in, S_out):
+    if plan is not None and nrhs >= 1 and _sized(S_in, S_out):
         nd, V, es = _extents(plan)
         need = nd * 2 * nrhs * V * es
-    return (_buffer(S_in, device, need, where, "S_in"), _buffer(S_out, device, need, where, "S_out"))
+    return (_buffer(S_in, device, need, where, "S_in" + tag), _buffer(S_out, device, need, where, "S_out" + tag))
 
 
 def _far_field(plan, patterns, per_box, spectra, nb, nrhs, where: str, names):
@@ -379,6 +380,10 @@ def fmmfft_autotune(plan, nrhs, budget_ms=2000.0):
 
 def fmmfft_batch_autotune(batch, nrhs, budget_ms=2000.0):
     r, rp = _ints(nrhs)
+    plans = _BATCH_PLANS.get(batch)
+    if plans is not None and r.size != len(plans):
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG,
+                          f"fmmfft_batch_autotune: {r.size} RHS counts for a batch of {len(plans)} plans")
     _check(lib().fmmfft_batch_autotune(batch, rp, float(budget_ms)), "fmmfft_batch_autotune")
 
 
@@ -392,25 +397,41 @@ def fmmfft_plan_load(path) -> int:
     return h.value
 
 
+# The plans of each batch made through this binding.  The library reads one
+# entry of S_in, S_out and nrhs per plan of the batch, from C arrays that
+# carry no length, so the lists' lengths (and each instance's buffers) are
+# checked against these.
+_BATCH_PLANS: dict = {}
+
+
 def fmmfft_batch_create(plans) -> int:
+    plans = list(plans)
     arr = (ctypes.c_void_p * len(plans))(*plans)
     h = ctypes.c_void_p()
     _check(lib().fmmfft_batch_create(ctypes.byref(h), arr, len(plans)), "fmmfft_batch_create")
+    _BATCH_PLANS[h.value] = plans
     return h.value
 
 
 def fmmfft_batch_translate(batch, S_in, S_out, nrhs, stream=None):
-    n = len(S_in)
-    ins = (ctypes.c_void_p * n)(*[_buffer(x, True, None, "fmmfft_batch_translate", f"S_in[{i}]")
-                                  for i, x in enumerate(S_in)])
-    outs = (ctypes.c_void_p * n)(*[_buffer(x, True, None, "fmmfft_batch_translate", f"S_out[{i}]")
-                                   for i, x in enumerate(S_out)])
+    where = "fmmfft_batch_translate"
     r, rp = _ints(nrhs)
-    _check(lib().fmmfft_batch_translate(batch, ins, outs, rp, _stream(stream)), "fmmfft_batch_translate")
+    plans = _BATCH_PLANS.get(batch)
+    n = len(S_in)
+    if not (len(S_out) == r.size == n) or (plans is not None and n != len(plans)):
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG,
+                          f"{where}: {n} inputs, {len(S_out)} outputs and {r.size} RHS counts"
+                          + (f" for a batch of {len(plans)} plans" if plans is not None else ""))
+    pairs = [_fields(plans[i] if plans is not None else None, S_in[i], S_out[i], int(r.flat[i]), True,
+                     where, f"[{i}]") for i in range(n)]
+    ins = (ctypes.c_void_p * n)(*[a for a, _ in pairs])
+    outs = (ctypes.c_void_p * n)(*[b for _, b in pairs])
+    _check(lib().fmmfft_batch_translate(batch, ins, outs, rp, _stream(stream)), where)
 
 
 def fmmfft_batch_destroy(batch):
     _check(lib().fmmfft_batch_destroy(batch), "fmmfft_batch_destroy")
+    _BATCH_PLANS.pop(batch, None)
 
 
 def fmmfft_translate(plan, S_in, S_out, nrhs, stream=None):

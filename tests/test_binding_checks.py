@@ -230,3 +230,32 @@ def test_plain_import_takes_the_whole_operator(native):
         assert e.value.status == F.FMMFFT_ERR_INVALID_ARG and "That holds" in str(e.value)
     finally:
         F.fmmfft_plan_destroy(h)
+
+
+def test_batch_lists_match_the_batch(native, plan):
+    """The library reads one S_in, S_out and nrhs entry per plan of the batch;
+    the binding checks the lists against the plans it recorded at batch
+    creation and each instance's buffers against its plan.  A batch needs
+    compressed plans, so the recorded plans are set here for the null handle,
+    which the library itself refuses once the binding lets a call through."""
+    F, h, nd, V = plan
+    need = nd * 2 * 2 * V * 8
+    ok = [DeviceBuffer(need)], [DeviceBuffer(need, addr=2 << 40)]
+
+    def message(ins, outs, nrhs):
+        with pytest.raises(F.FmmfftError) as e:
+            F.fmmfft_batch_translate(0, ins, outs, nrhs, 0)
+        assert e.value.status == F.FMMFFT_ERR_INVALID_ARG
+        return str(e.value)
+
+    assert "2 inputs, 1 outputs" in message(ok[0] * 2, ok[1], [2, 2])
+    F._BATCH_PLANS[0] = [h]
+    try:
+        assert "for a batch of 1 plans" in message(ok[0] * 2, ok[1] * 2, [2, 2])
+        assert "S_in[0] holds" in message([DeviceBuffer(need - 8)], ok[1], [2])
+        assert "holds" not in message(ok[0], ok[1], [2])           # reaches the library
+        with pytest.raises(F.FmmfftError) as e:
+            F.fmmfft_batch_autotune(0, [1, 2], 10.0)
+        assert "2 RHS counts for a batch of 1 plans" in str(e.value)
+    finally:
+        F._BATCH_PLANS.pop(0, None)
