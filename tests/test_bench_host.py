@@ -55,3 +55,41 @@ def test_workload_table():
     for name, w in W.items():
         assert (w["fmt"] == 0) == (w["dec"] == 0), name
         assert 2 * (w["L"] + 1) ** 2 >= 1
+
+
+def _bench(args, env_extra=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, cwd=root, env=env,
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    """bench.py --impl reference times the FP64 oracle on the host (one field
+    of the benchmark workload per step) and prints one JSON line in the same
+    metric and unit as the GPU arm, with its CPU-baseline and end-to-end
+    objects (no host-device copies)."""
+    out = _bench(["--impl", "reference", "--steps", "2", "--warmup", "1"])
+    assert len(out) == 1
+    line = out[0]
+    assert line["impl"] == "reference" and "unavailable" not in line
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["config"]["workload"] == bench.WL["name"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    # the metric's units: one field is 64^3 padded voxels of one direction
+    assert math.isclose(line["value"], 64 ** 3 / (line["ms_per_step"] * 1e-3) / 1e9, rel_tol=1e-9)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    assert _bench(["--impl", "reference", "--steps", "1", "--warmup", "1"], {"RANK": "1"}) == []
