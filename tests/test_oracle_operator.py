@@ -5,7 +5,10 @@
   e^{-jk|X+d|}/|X+d| (this fixes the l = 0 term, the (-j)^l phase and the
   Hankel kind of Eq. 7);
 * symmetry: T depends only on k.R^ and |R|, so it is unchanged by any signed
-  axis permutation applied to both k and R, and by k -> -k, R -> -R;
+  axis permutation applied to both k and R, and by k -> -k, R -> -R, and two
+  offsets of equal length that no lattice symmetry relates (Pythagorean
+  quadruples such as (3, 4, 0) and (5, 0, 0)) give equal values for directions
+  at equal angles to them;
 * near offsets are zero;
 * the FFT route of Eq. 5 equals the brute-force Toeplitz sum.
 """
@@ -143,6 +146,41 @@ def test_operator_symmetries():
         anti = op.operator_at(-kh[p], -dx, -dy, -dz, 0.5, 2 * np.pi, 4)
         np.testing.assert_allclose(anti, base, rtol=1e-12, atol=1e-14)
     del K
+
+
+# offsets of equal length not related by a signed axis permutation
+_EQUAL_LENGTH = [[(3, 4, 0), (5, 0, 0), (0, -3, 4)],
+                 [(1, 2, 2), (3, 0, 0), (2, -1, -2)],
+                 [(2, 3, 6), (7, 0, 0), (6, -2, 3)],
+                 [(1, 4, 8), (4, 4, 7), (9, 0, 0)]]
+
+
+@pytest.mark.parametrize("group", _EQUAL_LENGTH)
+def test_operator_depends_only_on_angle_and_distance(group):
+    """Eq. 7 is a function of k.R^ and |R| alone: for each offset of the group
+    a direction at the same angle to it (rotated about no lattice axis) gives
+    the same value as the first offset with a random direction."""
+    rng = np.random.default_rng(sum(map(sum, group)))
+    a, k0, L = 0.5, 2 * np.pi, 6
+    for _ in range(3):
+        k1 = rng.normal(size=3)
+        k1 /= np.linalg.norm(k1)
+        d1 = np.array(group[0], dtype=float)
+        c = k1 @ d1 / np.linalg.norm(d1)
+        ref = op.operator_at(k1, *group[0], a, k0, L)
+        assert abs(ref) > 0
+        for d in group[1:]:
+            u = np.array(d, dtype=float) / np.linalg.norm(d)
+            e = rng.normal(size=3)
+            e -= (e @ u) * u
+            e /= np.linalg.norm(e)
+            k2 = c * u + np.sqrt(max(0.0, 1 - c * c)) * e
+            np.testing.assert_allclose(op.operator_at(k2, *d, a, k0, L), ref, rtol=1e-11)
+        # a different angle to the same offset changes the value
+        k3 = -c * d1 / np.linalg.norm(d1) + np.sqrt(max(0.0, 1 - c * c)) * np.cross(k1, d1) / \
+            max(np.linalg.norm(np.cross(k1, d1)), 1e-300)
+        if abs(c) > 0.1:
+            assert abs(op.operator_at(k3, *group[0], a, k0, L) - ref) > 1e-6 * abs(ref)
 
 
 def test_near_offsets_are_zero_and_far_are_not():
