@@ -124,7 +124,7 @@ enum {
                                     copy in, translate, copy out in sequence;
                                     at most 64); may be changed at any time   */
   FMMFFT_KEY_DIR_FIRST = 11,     /* shard plans: first direction of the block  */
-  FMMFFT_KEY_DIR_COUNT = 12      /* ... and its length (0, default: through the
+  FMMFFT_KEY_DIR_COUNT = 12,     /* ... and its length (0, default: through the
                                     last direction of the grid).  A shard plan
                                     holds, compresses and translates only the
                                     directions [first, first + count) of the
@@ -137,6 +137,12 @@ enum {
                                     the whole plan gives; 4D formats decompose
                                     the block's own 4D tensor.  Block outside
                                     the grid: INVALID_ARG                     */
+  FMMFFT_KEY_RESTORE_ERROR = 13  /* 1: the set-up also measures the FP64
+                                    restore error of the stored operator
+                                    (fmmfft_stats.restore_rel_err; costs one
+                                    host restoration of every direction and a
+                                    regeneration of its operator); 0 (default):
+                                    not measured                              */
 };
 
 /* Stages of one translation, in launch order (fmmfft_stage_times). */
@@ -178,6 +184,18 @@ typedef struct fmmfft_stats {
                                     on tensor cores (-1 default, 0 off, 1 on),
                                     pre-pass on tensor cores (same), pre-pass
                                     serial (1) or overlapped (0)            */
+  double restore_rel_err;        /* FP64 relative L2 error of the stored
+                                    operator's restoration against the plan's
+                                    own operator (Eq. 7, embedding, FFT), over
+                                    all directions: sqrt(sum_p ||T~_p - R_p||^2
+                                    / sum_p ||T~_p||^2), the measure the
+                                    tolerance gamma bounds (Algs. 1-3).  Set by
+                                    the set-up when FMMFFT_KEY_RESTORE_ERROR is
+                                    1: fmmfft_compress, fmmfft_compress_host and
+                                    the compressed imports (0 for a plain
+                                    operator from fmmfft_compress); -1 when not
+                                    measured (also after fmmfft_import_plain and
+                                    fmmfft_plan_load)                         */
 } fmmfft_stats;
 
 /*

@@ -56,6 +56,7 @@ FMMFFT_KEY_EPS_R_IM = 9
 FMMFFT_KEY_HOST_BLOCKS = 10
 FMMFFT_KEY_DIR_FIRST = 11
 FMMFFT_KEY_DIR_COUNT = 12
+FMMFFT_KEY_RESTORE_ERROR = 13
 FMMFFT_STAGE_RESTORE, FMMFFT_STAGE_XFWD, FMMFFT_STAGE_YZ, FMMFFT_STAGE_XINV = 0, 1, 2, 3
 FMMFFT_NUM_STAGES = 4
 
@@ -89,6 +90,7 @@ class _Stats(ctypes.Structure):
         ("device_bytes_scratch", ctypes.c_int64), ("setup_seconds", ctypes.c_double),
         ("restore_on_tensor_cores", ctypes.c_int), ("kernel_launches", ctypes.c_int),
         ("large_planes", ctypes.c_int), ("schedule", ctypes.c_int * 4),
+        ("restore_rel_err", ctypes.c_double),
     ]
 
 
@@ -544,7 +546,8 @@ class Plan:
                 "prefactor": FMMFFT_KEY_PREFACTOR, "trunc_rule": FMMFFT_KEY_TRUNC_RULE,
                 "profile": FMMFFT_KEY_PROFILE, "eps_r_re": FMMFFT_KEY_EPS_R_RE,
                 "eps_r_im": FMMFFT_KEY_EPS_R_IM, "host_blocks": FMMFFT_KEY_HOST_BLOCKS,
-                "dir_first": FMMFFT_KEY_DIR_FIRST, "dir_count": FMMFFT_KEY_DIR_COUNT}
+                "dir_first": FMMFFT_KEY_DIR_FIRST, "dir_count": FMMFFT_KEY_DIR_COUNT,
+                "restore_error": FMMFFT_KEY_RESTORE_ERROR}
         for k, v in opts.items():
             fmmfft_plan_set(self.handle, keys[k], v)
 

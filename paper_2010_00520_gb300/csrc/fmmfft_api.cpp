@@ -68,6 +68,8 @@ struct fmmfft_plan_s {
   fmm::Schedule sched;          // fmmfft_autotune's choices
   bool profile = false;
   bool profiled_run = false;
+  bool measure_err = false;     // FMMFFT_KEY_RESTORE_ERROR
+  double restore_err = -1.0;    // FP64 restore error of the set-up, -1: not measured
   cudaEvent_t events[FMMFFT_NUM_STAGES + 1] = {};
   // host-side bookkeeping
   std::vector<int> ranks3;      // 3D formats: n_dir x 3
@@ -417,8 +419,16 @@ void build_layout(const fmmfft_plan_s* p, fmm::Layout& L) {
   }
 }
 
+// FP64 relative error of a layout's restoration against the plan's own
+// operator (Eq. 7, embedding and FFT), over all directions.
+double measure_restore_error(const fmmfft_plan_s* p, const fmm::Layout& L) {
+  const fmm::OperatorSpec s = spec_of(p);
+  return fmm::restore_error_host(L, [&](int d, std::vector<cdouble>& T) { fmm::fft_operator(s, &p->khat[3 * d], T); });
+}
+
 // Adopt a compressed layout: support check, upload, common buffers.
 int install_layout(fmmfft_plan_s* p, const fmm::Layout& L) {
+  p->restore_err = -1.0;
   release_operator(p);
   p->layout = L;
   adopt_layout_shape(p, L);
@@ -429,6 +439,7 @@ int install_layout(fmmfft_plan_s* p, const fmm::Layout& L) {
   if ((st = ensure_slabs(p)) != FMMFFT_OK) return st;
   if ((st = ensure_common(p)) != FMMFFT_OK) return st;
   p->ready = true;
+  if (p->measure_err) p->restore_err = measure_restore_error(p, L);
   return FMMFFT_OK;
 }
 
@@ -546,6 +557,10 @@ int fmmfft_plan_set(fmmfft_plan p, int key, double v) {
       if (!(v <= 0) || !std::isfinite(v)) return FMMFFT_ERR_INVALID_ARG;
       p->eps_im = v;
       return FMMFFT_OK;
+    case FMMFFT_KEY_RESTORE_ERROR:
+      if ((iv != 0 && iv != 1) || iv != v) return FMMFFT_ERR_INVALID_ARG;
+      p->measure_err = iv == 1;
+      return FMMFFT_OK;
     default:
       return FMMFFT_ERR_INVALID_ARG;
   }
@@ -556,6 +571,7 @@ int fmmfft_compress(fmmfft_plan p) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!format_known(p) || !precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   int st;
+  p->restore_err = -1.0;
   if (p->format == FMMFFT_FORMAT_NONE) {
     if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
     release_operator(p);
@@ -567,6 +583,7 @@ int fmmfft_compress(fmmfft_plan p) {
     if (st != FMMFFT_OK) return st;
     if ((st = ensure_common(p)) != FMMFFT_OK) return st;
     p->ready = true;
+    if (p->measure_err) p->restore_err = 0.0;   // stored as generated
   } else {
     fmm::Layout L;
     build_layout(p, L);
@@ -580,6 +597,7 @@ int fmmfft_import_plain(fmmfft_plan p, const double* That) {
   if (!p || !That || p->format != FMMFFT_FORMAT_NONE) return FMMFFT_ERR_INVALID_ARG;
   if (!precision_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
   if (!check_supported(p)) return FMMFFT_ERR_UNSUPPORTED;
+  p->restore_err = -1.0;
   release_operator(p);
   int st = query_large_grid(p);
   if (st != FMMFFT_OK) return st;
@@ -729,6 +747,7 @@ int fmmfft_compress_host(fmmfft_plan p, int* ranks, double* restored) {
     p->elements_plain = (int64_t)p->n[0] * p->n[1] * p->n[2] * p->n_dir;
     p->elements_compressed = L.elements;
     p->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    p->restore_err = p->measure_err ? measure_restore_error(p, L) : -1.0;
   }
   if (p->format == FMMFFT_FORMAT_3D) {
     std::memcpy(ranks, L.ranks3.data(), sizeof(int) * L.ranks3.size());
@@ -1004,6 +1023,7 @@ int fmmfft_plan_stats(fmmfft_plan p, fmmfft_stats* o) {
   o->device_bytes_operator = p->bytes_operator;
   o->device_bytes_scratch = (int64_t)(p->inter_bytes + p->io_bytes + p->slabs_bytes) + p->bytes_restore;
   o->setup_seconds = p->setup_seconds;
+  o->restore_rel_err = p->restore_err;
   if (p->ready) {
     const fmm::TranslateArgs a = base_args(p);
     o->restore_on_tensor_cores = a.tc == 1 && a.tc_single ? 3 : a.tc;

@@ -2,6 +2,8 @@
 #include "plan_layout.h"
 
 #include <algorithm>
+#include <cmath>
+#include <functional>
 
 namespace fmm {
 
@@ -285,8 +287,11 @@ void bind_slabs(const Layout& L, const void* pack, void* scratch, size_t es, std
 // ---------------------------------------------------------------------------
 // host restore (FP64)
 // ---------------------------------------------------------------------------
-void restore_host(const Layout& L, std::vector<cdouble>& out) {
-  std::vector<cdouble> scratch((size_t)std::max<int64_t>(L.scratch, 1), cdouble(0.0, 0.0));
+namespace {
+
+// The pre-pass products of a layout, run on the host into `scratch`.
+void host_prepass(const Layout& L, std::vector<cdouble>& scratch) {
+  scratch.assign((size_t)std::max<int64_t>(L.scratch, 1), cdouble(0.0, 0.0));
   std::vector<std::vector<GemmDesc>> st;
   bind_gemms(L, L.pack.data(), scratch.data(), sizeof(cdouble), st);
   for (const auto& stage : st)
@@ -302,37 +307,75 @@ void restore_host(const Layout& L, std::vector<cdouble>& out) {
           C[(size_t)m * g.N + nn] = acc;
         }
     });
+}
+
+// Direction p's slab formula for every x: o = T~_p[x][y][z] (n1 x n2 x n3).
+void host_slabs(const Layout& L, const SlabDesc& d, cdouble* o) {
+  const int n1 = L.n[0], n2 = L.n[1], n3 = L.n[2];
+  const cdouble* U3 = (const cdouble*)d.u3;
+  std::vector<cdouble> G((size_t)n2 * d.rb);
+  for (int x = 0; x < n1; ++x) {
+    const cdouble* H = (const cdouble*)d.h + (size_t)x * d.hx;
+    if (L.yz_fmt == 1) {
+      const cdouble* U2 = (const cdouble*)d.u2;
+      for (int y = 0; y < n2; ++y)
+        for (int c = 0; c < d.rb; ++c) {
+          cdouble acc(0.0, 0.0);
+          for (int b = 0; b < d.ra; ++b) acc += U2[(size_t)y * d.ra + b] * H[(size_t)b * d.rb + c];
+          G[(size_t)y * d.rb + c] = acc;
+        }
+    } else {
+      for (size_t i = 0; i < (size_t)n2 * d.rb; ++i) G[i] = H[i];
+    }
+    cdouble* ox = o + (size_t)x * n2 * n3;
+    for (int y = 0; y < n2; ++y)
+      for (int z = 0; z < n3; ++z) {
+        cdouble acc(0.0, 0.0);
+        for (int c = 0; c < d.rb; ++c) acc += U3[(size_t)z * d.rb + c] * G[(size_t)y * d.rb + c];
+        ox[(size_t)y * n3 + z] = acc;
+      }
+  }
+}
+
+}  // namespace
+
+void restore_host(const Layout& L, std::vector<cdouble>& out) {
+  std::vector<cdouble> scratch;
+  host_prepass(L, scratch);
   std::vector<SlabDesc> sl;
   bind_slabs(L, L.pack.data(), scratch.data(), sizeof(cdouble), sl);
-  const int n1 = L.n[0], n2 = L.n[1], n3 = L.n[2];
-  const size_t per = (size_t)n1 * n2 * n3;
+  const size_t per = (size_t)L.n[0] * L.n[1] * L.n[2];
   out.assign(per * L.n_dir, cdouble(0.0, 0.0));
+  parallel_for(L.n_dir, [&](int p) { host_slabs(L, sl[p], &out[per * p]); });
+}
+
+double restore_error_host(const Layout& L, const std::function<void(int, std::vector<cdouble>&)>& op) {
+  std::vector<cdouble> scratch;
+  host_prepass(L, scratch);
+  std::vector<SlabDesc> sl;
+  bind_slabs(L, L.pack.data(), scratch.data(), sizeof(cdouble), sl);
+  const size_t per = (size_t)L.n[0] * L.n[1] * L.n[2];
+  // per-direction sums, added in direction order: the result does not depend
+  // on how the directions were spread over the threads
+  std::vector<double> diff2(L.n_dir, 0.0), norm2(L.n_dir, 0.0);
   parallel_for(L.n_dir, [&](int p) {
-    const SlabDesc& d = sl[p];
-    const cdouble* U3 = (const cdouble*)d.u3;
-    std::vector<cdouble> G((size_t)n2 * d.rb);
-    for (int x = 0; x < n1; ++x) {
-      const cdouble* H = (const cdouble*)d.h + (size_t)x * d.hx;
-      if (L.yz_fmt == 1) {
-        const cdouble* U2 = (const cdouble*)d.u2;
-        for (int y = 0; y < n2; ++y)
-          for (int c = 0; c < d.rb; ++c) {
-            cdouble acc(0.0, 0.0);
-            for (int b = 0; b < d.ra; ++b) acc += U2[(size_t)y * d.ra + b] * H[(size_t)b * d.rb + c];
-            G[(size_t)y * d.rb + c] = acc;
-          }
-      } else {
-        for (size_t i = 0; i < (size_t)n2 * d.rb; ++i) G[i] = H[i];
-      }
-      cdouble* o = &out[per * p + (size_t)x * n2 * n3];
-      for (int y = 0; y < n2; ++y)
-        for (int z = 0; z < n3; ++z) {
-          cdouble acc(0.0, 0.0);
-          for (int c = 0; c < d.rb; ++c) acc += U3[(size_t)z * d.rb + c] * G[(size_t)y * d.rb + c];
-          o[(size_t)y * n3 + z] = acc;
-        }
+    std::vector<cdouble> T, R(per);
+    op(p, T);
+    host_slabs(L, sl[p], R.data());
+    double e = 0.0, t = 0.0;
+    for (size_t i = 0; i < per; ++i) {
+      e += std::norm(T[i] - R[i]);
+      t += std::norm(T[i]);
     }
+    diff2[p] = e;
+    norm2[p] = t;
   });
+  double e = 0.0, t = 0.0;
+  for (int p = 0; p < L.n_dir; ++p) {
+    e += diff2[p];
+    t += norm2[p];
+  }
+  return t > 0.0 ? std::sqrt(e / t) : 0.0;
 }
 
 }  // namespace fmm

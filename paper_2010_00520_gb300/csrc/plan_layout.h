@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "host_decomp.h"
@@ -68,5 +69,11 @@ void bind_slabs(const Layout& L, const void* pack, void* scratch, size_t es, std
 // products and the slab formulas on the host).  out: n_dir x n1 x n2 x n3,
 // T~_p[x][y][z] (unscaled).
 void restore_host(const Layout& L, std::vector<cdouble>& out);
+
+// FP64 relative error of the layout's restoration, sqrt(sum_p ||T~_p - R_p||^2
+// / sum_p ||T~_p||^2) over all directions, where op(p, T) writes direction p's
+// uncompressed T~_p (n1 x n2 x n3, same indexing as restore_host) and R_p is
+// restored as in restore_host, one direction at a time.
+double restore_error_host(const Layout& L, const std::function<void(int, std::vector<cdouble>&)>& op);
 
 }  // namespace fmm

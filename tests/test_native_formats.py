@@ -90,3 +90,42 @@ def test_tridiagonal_eigensolver_on_large_gram(native):
     assert tuple(int(v) for v in ranks) == tuple(comp.parts.ranks)
     T4 = np.stack(ops)
     assert abs(_rel(R, T4) - _rel(np.stack([comp.restore(p) for p in range(plan.n_dir)]), T4)) <= 1e-8
+
+
+@pytest.mark.parametrize("fmt,dec,K,L,tol", [
+    ("3d", "tucker", (6, 5, 7), 3, 1e-4),
+    ("3d", "tt", (6, 5, 7), 3, 1e-3),
+    ("4d", "tucker", (6, 5, 7), 3, 1e-4),
+    ("4d", "htucker", (8, 8, 8), 4, 1e-3),
+    ("4d", "tt", (6, 5, 7), 3, 1e-4),
+])
+def test_restore_error_statistic(native, fmt, dec, K, L, tol):
+    """With FMMFFT_KEY_RESTORE_ERROR = 1 the set-up reports the FP64 relative
+    error of its stored operator, sqrt(sum_p ||T_p - R_p||^2 / sum_p ||T_p||^2):
+    it equals the error of the restored tensors against the oracle's
+    operators and stays within the tolerance the decompositions guarantee."""
+    plan = pl.Plan(K=K, L=L)
+    T4 = np.stack(pl.operators(plan))
+    h = native.fmmfft_plan_create(*K, 0.5, TWO_PI, L, FMT[fmt], DEC[dec], tol)
+    try:
+        assert native.fmmfft_plan_stats(h)["restore_rel_err"] == -1.0
+        native.fmmfft_plan_set(h, native.FMMFFT_KEY_RESTORE_ERROR, 1)
+        _, R = native.fmmfft_compress_host(h)
+        got = native.fmmfft_plan_stats(h)["restore_rel_err"]
+        want = _rel(R, T4)
+        assert 0.0 < got <= tol
+        assert abs(got - want) <= 1e-9 + 1e-6 * want, (got, want)
+    finally:
+        native.fmmfft_plan_destroy(h)
+
+
+def test_restore_error_is_opt_in(native):
+    h = native.fmmfft_plan_create(6, 5, 7, 0.5, TWO_PI, 3, 3, 1, 1e-4)
+    try:
+        native.fmmfft_compress_host(h, restored=False)
+        assert native.fmmfft_plan_stats(h)["restore_rel_err"] == -1.0
+        for bad in (2, -1, 0.5):
+            with pytest.raises(native.FmmfftError):
+                native.fmmfft_plan_set(h, native.FMMFFT_KEY_RESTORE_ERROR, bad)
+    finally:
+        native.fmmfft_plan_destroy(h)
