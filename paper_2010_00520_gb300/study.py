@@ -43,7 +43,8 @@ import numpy as np
 from . import (FMMFFT_FORMAT_3D, FMMFFT_FORMAT_4D, FMMFFT_FORMAT_NONE, FMMFFT_DECOMP_HTUCKER,
                FMMFFT_DECOMP_NONE, FMMFFT_DECOMP_TT, FMMFFT_DECOMP_TUCKER, FMMFFT_KEY_EPS_R_IM,
                FMMFFT_KEY_EPS_R_RE, FMMFFT_KEY_KAPPA, FMMFFT_KEY_NEAR_RULE, FMMFFT_KEY_NPHI_RULE,
-               FMMFFT_KEY_PRECISION, FMMFFT_KEY_TRUNC_RULE, FMMFFT_PREC_C64, FMMFFT_PREC_C128,
+               FMMFFT_KEY_PRECISION, FMMFFT_KEY_RESTORE_ERROR, FMMFFT_KEY_TRUNC_RULE, FMMFFT_PREC_C64,
+               FMMFFT_PREC_C128,
                FMMFFT_ERR_UNSUPPORTED,
                FmmfftError, fmmfft_compress,
                fmmfft_compress_host, fmmfft_multipole_count, fmmfft_plan_create, fmmfft_plan_destroy,
@@ -96,6 +97,7 @@ class StudyRow:
     saving: float
     setup_s: float
     gpu: dict = field(default_factory=dict)
+    restore_rel_err: float = -1.0  # FP64 error of the stored operator (-1: not measured)
 
 
 def _configure(h, c: StudyCase, precision=None):
@@ -119,11 +121,16 @@ def _plan(c: StudyCase, L: int, fmt_dec, tol, precision=None):
     return h
 
 
-def host_case(c: StudyCase) -> StudyRow:
-    """Ranks and memory saving of one case from the library's FP64 set-up."""
+def host_case(c: StudyCase, restore_error: bool = False) -> StudyRow:
+    """Ranks and memory saving of one case from the library's FP64 set-up;
+    with restore_error also the FP64 relative error of the stored operator
+    against the uncompressed one (the quantity the tolerance bounds), which
+    costs one host restoration of every direction."""
     L = c.multipoles()
     h = _plan(c, L, FORMATS[c.fmt], c.tol)
     try:
+        if restore_error:
+            fmmfft_plan_set(h, FMMFFT_KEY_RESTORE_ERROR, 1)
         t0 = time.perf_counter()
         r, _ = fmmfft_compress_host(h, restored=False)
         setup = time.perf_counter() - t0
@@ -139,7 +146,8 @@ def host_case(c: StudyCase) -> StudyRow:
         case["eps_r"] = [complex(c.eps_r).real, complex(c.eps_r).imag]
         return StudyRow(case=case, L=L, n=list(st["n"]), n_dir=st["n_dir"], ranks=ranks, mean_ranks=mean,
                         elements_plain=int(st["elements_plain"]), elements_compressed=int(st["elements_compressed"]),
-                        saving=float(st["saving"]), setup_s=setup)
+                        saving=float(st["saving"]), setup_s=setup,
+                        restore_rel_err=float(st["restore_rel_err"]))
     finally:
         fmmfft_plan_destroy(h)
 
@@ -232,10 +240,10 @@ def loss(formats, eps=(2.0, 2 - 1j, 2 - 2j, 2 - 8j), diameter=8, **kw):
 SWEEPS = {"size": structure_size, "tol": tolerance, "box": box_size, "digits": accuracy, "loss": loss}
 
 
-def run(cases, gpu=False, nrhs=1, log=None, precision=FMMFFT_PREC_C64):
+def run(cases, gpu=False, nrhs=1, log=None, precision=FMMFFT_PREC_C64, restore_error=False):
     rows = []
     for c in cases:
-        row = host_case(c)
+        row = host_case(c, restore_error)
         if gpu:
             gpu_case(c, row, nrhs=nrhs, precision=precision)
         rows.append(row)
@@ -248,6 +256,9 @@ def table(rows) -> str:
     """Markdown table of study rows."""
     head = "| format | K | a | digits | eps_r | tol | L | N_dir | n | ranks | saving % | host set-up s |"
     gpu = any(r.gpu for r in rows)
+    err = any(r.restore_rel_err >= 0 for r in rows)
+    if err:
+        head += " FP64 restore error |"
     if gpu:
         head += " ms compressed | ms plain | overhead |"
     out = [head, "|" + "---|" * (head.count("|") - 1)]
@@ -256,6 +267,8 @@ def table(rows) -> str:
         e = complex(*c["eps_r"])
         line = (f"| {c['fmt']} | {c['K']} | {c['a']:g} | {c['digits']:g} | {e.real:g}{e.imag:+g}j | {c['tol']:g} | "
                 f"{r.L} | {r.n_dir} | {r.n[0]} | {tuple(r.ranks)} | {100 * r.saving:.2f} | {r.setup_s:.1f} |")
+        if err:
+            line += f" {r.restore_rel_err:.2e} |" if r.restore_rel_err >= 0 else " - |"
         if gpu:
             g = r.gpu
             if "ms_compressed" in g:
@@ -282,6 +295,8 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=FMMFFT_PREC_C64,
                     help="FMMFFT_PREC_*: 0 complex128, 1 complex64 with FP32 restores (default), 2 3xTF32, "
                          "3 BF16x3")
+    ap.add_argument("--restore-error", action="store_true",
+                    help="also measure the FP64 restore error of each stored operator (host)")
     ap.add_argument("--json", help="write the rows to this file")
     a = ap.parse_args(argv)
     fmts = list(FORMATS) if a.formats == ["all"] else a.formats
@@ -292,7 +307,7 @@ def main(argv=None):
         cases = tolerance(fmts, diameter=a.diameter, **kw)
     else:
         cases = SWEEPS[a.sweep](fmts, diameter=a.diameter, tol=a.tol, **kw)
-    rows = run(cases, gpu=a.gpu, nrhs=a.nrhs, precision=a.precision,
+    rows = run(cases, gpu=a.gpu, nrhs=a.nrhs, precision=a.precision, restore_error=a.restore_error,
                log=lambda r: print(json.dumps(asdict(r)), flush=True))
     print(table(rows))
     if a.json:

@@ -102,3 +102,21 @@ def test_study_command_line_writes_rows(study, tmp_path, capsys):
     assert all(0.0 <= r["saving"] < 1.0 and r["gpu"] == {} for r in rows)
     printed = capsys.readouterr().out
     assert printed.count('{"case"') == 4 and "| tucker3d | 2 |" in printed
+
+
+def test_study_reports_the_restore_error_on_request(study, tmp_path):
+    """--restore-error: each row carries the FP64 relative error of the stored
+    operator against the uncompressed one, within the case's tolerance for
+    every format; without it the field stays -1 and the table has no column."""
+    import json
+    rows = study.run([study.StudyCase(fmt=f, K=4, L=3, tol=1e-4, near_rule=0, nphi_rule=0)
+                      for f in ("tucker3d", "tt3d", "tucker4d", "htucker", "tt4d")], restore_error=True)
+    assert all(0.0 < r.restore_rel_err <= 1e-4 for r in rows), [r.restore_rel_err for r in rows]
+    assert "FP64 restore error" in study.table(rows)
+    plain = study.host_case(study.StudyCase(fmt="tucker3d", K=4, L=3, tol=1e-4, near_rule=0, nphi_rule=0))
+    assert plain.restore_rel_err == -1.0 and "FP64 restore error" not in study.table([plain])
+    out = tmp_path / "rows.json"
+    study.main(["size", "--diameters", "2", "--formats", "tucker3d", "--tol", "1e-4", "--restore-error",
+                "--json", str(out)])
+    (row,) = json.loads(out.read_text())
+    assert 0.0 < row["restore_rel_err"] <= 1e-4
