@@ -88,19 +88,14 @@ void hermitian_eig_tridiag(int n, std::vector<cdouble>& A, std::vector<double>& 
     const double inv = 1.0 / std::sqrt(vn2);
     for (int i = 0; i < m; ++i) v[i] *= inv;
     // p = A_sub v, beta = v^H p, w = 2 (p - beta v); A_sub -= v w^H + w v^H
-    parallel_for(m, [&](int i) {
-      const cdouble* row = &A[(size_t)(k + 1 + i) * n + k + 1];
-      cdouble acc(0.0, 0.0);
-      for (int j = 0; j < m; ++j) acc += row[j] * v[j];
-      p[i] = acc;
-    });
+    parallel_for(m, [&](int i) { p[i] = cdot(&A[(size_t)(k + 1 + i) * n + k + 1], v.data(), m); });
     double beta = 0.0;
     for (int i = 0; i < m; ++i) beta += (std::conj(v[i]) * p[i]).real();
     for (int i = 0; i < m; ++i) w[i] = 2.0 * (p[i] - beta * v[i]);
     parallel_for(m, [&](int i) {
       cdouble* row = &A[(size_t)(k + 1 + i) * n + k + 1];
-      const cdouble vi = v[i], wi = w[i];
-      for (int j = 0; j < m; ++j) row[j] -= vi * std::conj(w[j]) + wi * std::conj(v[j]);
+      caxpy_conj(-v[i], w.data(), row, m);
+      caxpy_conj(-w[i], v.data(), row, m);
     });
     for (int i = 0; i < m; ++i) {
       A[(size_t)(k + 1 + i) * n + k] = (i == 0) ? alpha : cdouble(0.0, 0.0);
@@ -109,10 +104,7 @@ void hermitian_eig_tridiag(int n, std::vector<cdouble>& A, std::vector<double>& 
     // Q <- Q H_k, H_k = I - 2 v v^H on indices k+1 .. n-1
     parallel_for(n, [&](int r) {
       cdouble* q = &Q[(size_t)r * n + k + 1];
-      cdouble s(0.0, 0.0);
-      for (int j = 0; j < m; ++j) s += q[j] * v[j];
-      s *= 2.0;
-      for (int j = 0; j < m; ++j) q[j] -= s * std::conj(v[j]);
+      caxpy_conj(-2.0 * cdot(q, v.data(), m), v.data(), q, m);
     });
   }
   // T = D T' D^H with T' real: phases make every off-diagonal |e_k|
@@ -171,12 +163,7 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
     std::vector<cdouble> G((size_t)m * m, cdouble(0.0, 0.0));
     parallel_for((int)m, [&](int i) {
       const cdouble* a = A + (size_t)i * N;
-      for (int64_t j = i; j < m; ++j) {
-        const cdouble* b = A + (size_t)j * N;
-        cdouble acc(0.0, 0.0);
-        for (int64_t k = 0; k < N; ++k) acc += a[k] * std::conj(b[k]);
-        G[(size_t)i * m + j] = acc;
-      }
+      for (int64_t j = i; j < m; ++j) G[(size_t)i * m + j] = cdot_conj(a, A + (size_t)j * N, (size_t)N);
     });
     for (int64_t i = 0; i < m; ++i)
       for (int64_t j = i + 1; j < m; ++j) G[(size_t)j * m + i] = std::conj(G[(size_t)i * m + j]);
@@ -194,8 +181,7 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
       cdouble* g = &G[(size_t)i * N];
       for (int64_t row = 0; row < m; ++row) {
         const cdouble* a = A + (size_t)row * N;
-        const cdouble ci = std::conj(a[i]);
-        for (int64_t j = i; j < N; ++j) g[j] += ci * a[j];
+        caxpy(std::conj(a[i]), a + i, g + i, (size_t)(N - i));
       }
     });
     for (int64_t i = 0; i < N; ++i)
@@ -212,11 +198,7 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
     parallel_for((int)m, [&](int row) {
       const cdouble* a = A + (size_t)row * N;
       cdouble* u = &U[(size_t)row * r];
-      for (int64_t k = 0; k < N; ++k) {
-        const cdouble ak = a[k];
-        const cdouble* v = &V[(size_t)k * N];
-        for (int c = 0; c < r; ++c) u[c] += ak * v[c];
-      }
+      for (int64_t k = 0; k < N; ++k) caxpy(a[k], &V[(size_t)k * N], u, (size_t)r);
       for (int c = 0; c < r; ++c) u[c] *= isig[c];
     });
   }
@@ -224,11 +206,7 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
   Q.assign((size_t)r * N, cdouble(0.0, 0.0));
   parallel_for(r, [&](int c) {
     cdouble* q = &Q[(size_t)c * N];
-    for (int64_t row = 0; row < m; ++row) {
-      const cdouble u = std::conj(U[(size_t)row * r + c]);
-      const cdouble* a = A + (size_t)row * N;
-      for (int64_t k = 0; k < N; ++k) q[k] += u * a[k];
-    }
+    for (int64_t row = 0; row < m; ++row) caxpy(std::conj(U[(size_t)row * r + c]), A + (size_t)row * N, q, (size_t)N);
   });
   return r;
 }
@@ -267,24 +245,15 @@ void hosvd4(const std::vector<std::vector<cdouble>>& Tp, const int n[3], double 
     g3[p].assign((size_t)n3 * n3, cdouble(0.0, 0.0));
     const size_t len = (size_t)n2 * n3;
     for (int i = 0; i < n1; ++i)
-      for (int j = i; j < n1; ++j) {
-        cdouble acc(0.0, 0.0);
-        for (size_t k = 0; k < len; ++k) acc += T[i * len + k] * std::conj(T[j * len + k]);
-        g1[p][(size_t)i * n1 + j] = acc;
-      }
+      for (int j = i; j < n1; ++j) g1[p][(size_t)i * n1 + j] = cdot_conj(T + i * len, T + j * len, len);
     for (int x = 0; x < n1; ++x) {
       const cdouble* S = T + (size_t)x * len;
       for (int i = 0; i < n2; ++i)
-        for (int j = i; j < n2; ++j) {
-          cdouble acc(0.0, 0.0);
-          for (int z = 0; z < n3; ++z) acc += S[(size_t)i * n3 + z] * std::conj(S[(size_t)j * n3 + z]);
-          g2[p][(size_t)i * n2 + j] += acc;
-        }
+        for (int j = i; j < n2; ++j) g2[p][(size_t)i * n2 + j] += cdot_conj(S + (size_t)i * n3, S + (size_t)j * n3, n3);
     }
     for (size_t row = 0; row < (size_t)n1 * n2; ++row) {
       const cdouble* v = T + row * n3;
-      for (int i = 0; i < n3; ++i)
-        for (int j = i; j < n3; ++j) g3[p][(size_t)i * n3 + j] += v[i] * std::conj(v[j]);
+      for (int i = 0; i < n3; ++i) caxpy_conj(v[i], v + i, &g3[p][(size_t)i * n3 + i], n3 - i);
     }
   });
   std::vector<cdouble> G[4];
@@ -299,13 +268,7 @@ void hosvd4(const std::vector<std::vector<cdouble>>& Tp, const int n[3], double 
   // mode 4: G4[p][q] = <T_p, T_q>
   G[3].assign((size_t)K * K, cdouble(0.0, 0.0));
   parallel_for(K, [&](int p) {
-    for (int q = p; q < K; ++q) {
-      cdouble acc(0.0, 0.0);
-      const cdouble* a = Tp[p].data();
-      const cdouble* b = Tp[q].data();
-      for (size_t k = 0; k < N; ++k) acc += a[k] * std::conj(b[k]);
-      G[3][(size_t)p * K + q] = acc;
-    }
+    for (int q = p; q < K; ++q) G[3][(size_t)p * K + q] = cdot_conj(Tp[p].data(), Tp[q].data(), N);
   });
   for (int mode = 0; mode < 4; ++mode) {
     const int m = dims[mode];
@@ -322,35 +285,27 @@ void hosvd4(const std::vector<std::vector<cdouble>>& Tp, const int n[3], double 
   }
   const int r1 = out.r[0], r2 = out.r[1], r3 = out.r[2], r4 = out.r[3];
   const size_t R3 = (size_t)r1 * r2 * r3;
-  // per-direction projection Y_p = T_p x1 U1^H x2 U2^H x3 U3^H
+  // per-direction projection Y_p = T_p x1 U1^H x2 U2^H x3 U3^H (U3^H stored
+  // row by row so that the last sum runs over contiguous memory)
+  std::vector<cdouble> U3h((size_t)r3 * n3);
+  for (int z = 0; z < n3; ++z)
+    for (int c = 0; c < r3; ++c) U3h[(size_t)c * n3 + z] = std::conj(out.U[2][(size_t)z * r3 + c]);
   std::vector<std::vector<cdouble>> Y(K);
   parallel_for(K, [&](int p) {
     const cdouble* T = Tp[p].data();
     const size_t len = (size_t)n2 * n3;
     std::vector<cdouble> Y1((size_t)r1 * len, cdouble(0.0, 0.0));
     for (int x = 0; x < n1; ++x)
-      for (int a = 0; a < r1; ++a) {
-        const cdouble u = std::conj(out.U[0][(size_t)x * r1 + a]);
-        cdouble* dst = &Y1[a * len];
-        const cdouble* src = T + x * len;
-        for (size_t k = 0; k < len; ++k) dst[k] += u * src[k];
-      }
+      for (int a = 0; a < r1; ++a) caxpy(std::conj(out.U[0][(size_t)x * r1 + a]), T + x * len, &Y1[a * len], len);
     std::vector<cdouble> Y2((size_t)r1 * r2 * n3, cdouble(0.0, 0.0));
     for (int a = 0; a < r1; ++a)
       for (int y = 0; y < n2; ++y)
-        for (int b = 0; b < r2; ++b) {
-          const cdouble u = std::conj(out.U[1][(size_t)y * r2 + b]);
-          cdouble* dst = &Y2[((size_t)a * r2 + b) * n3];
-          const cdouble* src = &Y1[((size_t)a * n2 + y) * n3];
-          for (int z = 0; z < n3; ++z) dst[z] += u * src[z];
-        }
+        for (int b = 0; b < r2; ++b)
+          caxpy(std::conj(out.U[1][(size_t)y * r2 + b]), &Y1[((size_t)a * n2 + y) * n3], &Y2[((size_t)a * r2 + b) * n3],
+                n3);
     Y[p].assign(R3, cdouble(0.0, 0.0));
     for (size_t ab = 0; ab < (size_t)r1 * r2; ++ab)
-      for (int c = 0; c < r3; ++c) {
-        cdouble acc(0.0, 0.0);
-        for (int z = 0; z < n3; ++z) acc += std::conj(out.U[2][(size_t)z * r3 + c]) * Y2[ab * n3 + z];
-        Y[p][ab * r3 + c] = acc;
-      }
+      for (int c = 0; c < r3; ++c) Y[p][ab * r3 + c] = cdot(&U3h[(size_t)c * n3], &Y2[ab * n3], n3);
   });
   // core[abc][d] = sum_p Y_p[abc] conj(U4[p][d])
   out.core.assign(R3 * r4, cdouble(0.0, 0.0));
@@ -358,11 +313,7 @@ void hosvd4(const std::vector<std::vector<cdouble>>& Tp, const int n[3], double 
     for (size_t bc = 0; bc < (size_t)r2 * r3; ++bc) {
       const size_t abc = (size_t)a * r2 * r3 + bc;
       cdouble* dst = &out.core[abc * r4];
-      for (int p = 0; p < K; ++p) {
-        const cdouble yv = Y[p][abc];
-        const cdouble* u = &out.U[3][(size_t)p * r4];
-        for (int d = 0; d < r4; ++d) dst[d] += yv * std::conj(u[d]);
-      }
+      for (int p = 0; p < K; ++p) caxpy_conj(Y[p][abc], &out.U[3][(size_t)p * r4], dst, r4);
     }
   });
 }

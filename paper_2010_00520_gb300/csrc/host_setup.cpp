@@ -1,5 +1,6 @@
 // FP64 host set-up: directions, operator of Eq. 7, embedding + FFT, HOSVD.
 #include "host_setup.h"
+#include "host_decomp.h"
 
 #include <algorithm>
 #include <atomic>
@@ -241,20 +242,36 @@ void hermitian_eig(int n, std::vector<cdouble>& A, std::vector<double>& lam, std
         const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
         const cdouble sph = s * std::conj(ph);       // s e^{-i phi}
         const cdouble cph = c * std::conj(ph);       // c e^{-i phi}
+        const double sr = sph.real(), si = sph.imag(), cr = cph.real(), ci = cph.imag();
         // columns: A <- A V with V = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+        // (complex products written out: see cdot_conj)
+        double* a = reinterpret_cast<double*>(A.data());
+        double* v = reinterpret_cast<double*>(V.data());
         for (int k = 0; k < n; ++k) {
-          const cdouble akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
-          A[(size_t)k * n + p] = c * akp - sph * akq;
-          A[(size_t)k * n + q] = s * akp + cph * akq;
-          const cdouble vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = c * vkp - sph * vkq;
-          V[(size_t)k * n + q] = s * vkp + cph * vkq;
+          double* x = a + 2 * ((size_t)k * n + p);
+          double* y = a + 2 * ((size_t)k * n + q);
+          const double xr = x[0], xi = x[1], yr = y[0], yi = y[1];
+          x[0] = c * xr - (sr * yr - si * yi);
+          x[1] = c * xi - (sr * yi + si * yr);
+          y[0] = s * xr + (cr * yr - ci * yi);
+          y[1] = s * xi + (cr * yi + ci * yr);
+          double* u = v + 2 * ((size_t)k * n + p);
+          double* w = v + 2 * ((size_t)k * n + q);
+          const double ur = u[0], ui = u[1], wr = w[0], wi = w[1];
+          u[0] = c * ur - (sr * wr - si * wi);
+          u[1] = c * ui - (sr * wi + si * wr);
+          w[0] = s * ur + (cr * wr - ci * wi);
+          w[1] = s * ui + (cr * wi + ci * wr);
         }
-        // rows: A <- V^H A
+        // rows: A <- V^H A (conjugated coefficients)
         for (int k = 0; k < n; ++k) {
-          const cdouble apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
-          A[(size_t)p * n + k] = c * apk - std::conj(sph) * aqk;
-          A[(size_t)q * n + k] = s * apk + std::conj(cph) * aqk;
+          double* x = a + 2 * ((size_t)p * n + k);
+          double* y = a + 2 * ((size_t)q * n + k);
+          const double xr = x[0], xi = x[1], yr = y[0], yi = y[1];
+          x[0] = c * xr - (sr * yr + si * yi);
+          x[1] = c * xi - (sr * yi - si * yr);
+          y[0] = s * xr + (cr * yr + ci * yi);
+          y[1] = s * xi + (cr * yi - ci * yr);
         }
         A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
       }
@@ -302,44 +319,29 @@ void hosvd3(const std::vector<cdouble>& T, const int n[3], double gamma, int rul
   const double delta = (rule == 0) ? gamma * std::sqrt(norm2) / std::sqrt(3.0) : gamma / std::sqrt(3.0);
   for (int mode = 0; mode < 3; ++mode) {
     const int m = n[mode];
+    // Gram matrix of the mode-`mode` unfolding, upper triangle, then mirrored
     std::vector<cdouble> G((size_t)m * m, cdouble(0.0, 0.0));
     if (mode == 0) {
       const size_t len = (size_t)n1 * n2;
       for (int i = 0; i < n0; ++i)
-        for (int j = i; j < n0; ++j) {
-          cdouble acc(0.0, 0.0);
-          const cdouble* a = &T[i * len];
-          const cdouble* b = &T[j * len];
-          for (size_t k = 0; k < len; ++k) acc += a[k] * std::conj(b[k]);
-          G[(size_t)i * m + j] = acc;
-          G[(size_t)j * m + i] = std::conj(acc);
-        }
+        for (int j = i; j < n0; ++j) G[(size_t)i * m + j] = cdot_conj(&T[i * len], &T[j * len], len);
     } else if (mode == 1) {
       for (int x = 0; x < n0; ++x) {
         const cdouble* S = &T[(size_t)x * n1 * n2];
         for (int i = 0; i < n1; ++i)
-          for (int j = i; j < n1; ++j) {
-            cdouble acc(0.0, 0.0);
-            for (int z = 0; z < n2; ++z) acc += S[(size_t)i * n2 + z] * std::conj(S[(size_t)j * n2 + z]);
-            G[(size_t)i * m + j] += acc;
-          }
+          for (int j = i; j < n1; ++j) G[(size_t)i * m + j] += cdot_conj(&S[(size_t)i * n2], &S[(size_t)j * n2], n2);
       }
-      for (int i = 0; i < n1; ++i)
-        for (int j = i + 1; j < n1; ++j) G[(size_t)j * m + i] = std::conj(G[(size_t)i * m + j]);
     } else {
       for (size_t row = 0; row < (size_t)n0 * n1; ++row) {
         const cdouble* v = &T[row * n2];
-        for (int i = 0; i < n2; ++i) {
-          const cdouble vi = v[i];
-          for (int j = i; j < n2; ++j) G[(size_t)i * m + j] += vi * std::conj(v[j]);
-        }
+        for (int i = 0; i < n2; ++i) caxpy_conj(v[i], v + i, &G[(size_t)i * m + i], n2 - i);
       }
-      for (int i = 0; i < n2; ++i)
-        for (int j = i + 1; j < n2; ++j) G[(size_t)j * m + i] = std::conj(G[(size_t)i * m + j]);
     }
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) G[(size_t)j * m + i] = std::conj(G[(size_t)i * m + j]);
     std::vector<double> lam;
     std::vector<cdouble> V;
-    hermitian_eig(m, G, lam, V);
+    hermitian_eig_auto(m, G, lam, V);
     const int r = truncation_rank(lam, delta, rule);
     out.r[mode] = r;
     out.U[mode].assign((size_t)m * r, cdouble(0.0, 0.0));
@@ -351,32 +353,22 @@ void hosvd3(const std::vector<cdouble>& T, const int n[3], double gamma, int rul
   std::vector<cdouble> Y1((size_t)r0 * n1 * n2, cdouble(0.0, 0.0));
   const size_t len = (size_t)n1 * n2;
   for (int x = 0; x < n0; ++x)
-    for (int a = 0; a < r0; ++a) {
-      const cdouble u = std::conj(out.U[0][(size_t)x * r0 + a]);
-      cdouble* dst = &Y1[a * len];
-      const cdouble* src = &T[x * len];
-      for (size_t k = 0; k < len; ++k) dst[k] += u * src[k];
-    }
+    for (int a = 0; a < r0; ++a) caxpy(std::conj(out.U[0][(size_t)x * r0 + a]), &T[x * len], &Y1[a * len], len);
   // Y2[a][b][z] = sum_y conj(U1[y][b]) Y1[a][y][z]
   std::vector<cdouble> Y2((size_t)r0 * r1 * n2, cdouble(0.0, 0.0));
   for (int a = 0; a < r0; ++a)
     for (int y = 0; y < n1; ++y)
-      for (int b = 0; b < r1; ++b) {
-        const cdouble u = std::conj(out.U[1][(size_t)y * r1 + b]);
-        cdouble* dst = &Y2[((size_t)a * r1 + b) * n2];
-        const cdouble* src = &Y1[((size_t)a * n1 + y) * n2];
-        for (int z = 0; z < n2; ++z) dst[z] += u * src[z];
-      }
-  // C[a][b][c] = sum_z conj(U2[z][c]) Y2[a][b][z]
+      for (int b = 0; b < r1; ++b)
+        caxpy(std::conj(out.U[1][(size_t)y * r1 + b]), &Y1[((size_t)a * n1 + y) * n2], &Y2[((size_t)a * r1 + b) * n2],
+              n2);
+  // C[a][b][c] = sum_z conj(U2[z][c]) Y2[a][b][z], with U2 transposed once
+  // so that the sum runs over contiguous memory
+  std::vector<cdouble> U2h((size_t)r2 * n2);
+  for (int z = 0; z < n2; ++z)
+    for (int c = 0; c < r2; ++c) U2h[(size_t)c * n2 + z] = std::conj(out.U[2][(size_t)z * r2 + c]);
   out.core.assign((size_t)r0 * r1 * r2, cdouble(0.0, 0.0));
-  for (size_t ab = 0; ab < (size_t)r0 * r1; ++ab) {
-    const cdouble* src = &Y2[ab * n2];
-    for (int c = 0; c < r2; ++c) {
-      cdouble acc(0.0, 0.0);
-      for (int z = 0; z < n2; ++z) acc += std::conj(out.U[2][(size_t)z * r2 + c]) * src[z];
-      out.core[ab * r2 + c] = acc;
-    }
-  }
+  for (size_t ab = 0; ab < (size_t)r0 * r1; ++ab)
+    for (int c = 0; c < r2; ++c) out.core[ab * r2 + c] = cdot(&U2h[(size_t)c * n2], &Y2[ab * n2], n2);
 }
 
 }  // namespace fmm

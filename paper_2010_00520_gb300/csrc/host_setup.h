@@ -15,6 +15,80 @@ using cdouble = std::complex<double>;
 // Run fn(i) for i in [0, n) on the host cores.
 void parallel_for(int n, const std::function<void(int)>& fn);
 
+// Complex inner loops of the set-up in explicit real arithmetic.  The
+// std::complex operators send every product through the C99 special-value
+// handling (a library call per multiply); these compute the textbook
+// formulas, which give the same values for finite operands.
+// sum_k a[k] conj(b[k])
+inline cdouble cdot_conj(const cdouble* a, const cdouble* b, size_t n) {
+  const double* x = reinterpret_cast<const double*>(a);
+  const double* y = reinterpret_cast<const double*>(b);
+  double r0 = 0.0, i0 = 0.0, r1 = 0.0, i1 = 0.0;
+  size_t k = 0;
+  for (; k + 2 <= n; k += 2) {
+    const double* p = x + 2 * k;
+    const double* q = y + 2 * k;
+    r0 += p[0] * q[0] + p[1] * q[1];
+    i0 += p[1] * q[0] - p[0] * q[1];
+    r1 += p[2] * q[2] + p[3] * q[3];
+    i1 += p[3] * q[2] - p[2] * q[3];
+  }
+  if (k < n) {
+    const double* p = x + 2 * k;
+    const double* q = y + 2 * k;
+    r0 += p[0] * q[0] + p[1] * q[1];
+    i0 += p[1] * q[0] - p[0] * q[1];
+  }
+  return cdouble(r0 + r1, i0 + i1);
+}
+
+// sum_k a[k] b[k]
+inline cdouble cdot(const cdouble* a, const cdouble* b, size_t n) {
+  const double* x = reinterpret_cast<const double*>(a);
+  const double* y = reinterpret_cast<const double*>(b);
+  double r0 = 0.0, i0 = 0.0, r1 = 0.0, i1 = 0.0;
+  size_t k = 0;
+  for (; k + 2 <= n; k += 2) {
+    const double* p = x + 2 * k;
+    const double* q = y + 2 * k;
+    r0 += p[0] * q[0] - p[1] * q[1];
+    i0 += p[0] * q[1] + p[1] * q[0];
+    r1 += p[2] * q[2] - p[3] * q[3];
+    i1 += p[2] * q[3] + p[3] * q[2];
+  }
+  if (k < n) {
+    const double* p = x + 2 * k;
+    const double* q = y + 2 * k;
+    r0 += p[0] * q[0] - p[1] * q[1];
+    i0 += p[0] * q[1] + p[1] * q[0];
+  }
+  return cdouble(r0 + r1, i0 + i1);
+}
+
+// y[k] += u x[k]
+inline void caxpy(cdouble u, const cdouble* x, cdouble* y, size_t n) {
+  const double ur = u.real(), ui = u.imag();
+  const double* X = reinterpret_cast<const double*>(x);
+  double* Y = reinterpret_cast<double*>(y);
+  for (size_t k = 0; k < n; ++k) {
+    const double xr = X[2 * k], xi = X[2 * k + 1];
+    Y[2 * k] += ur * xr - ui * xi;
+    Y[2 * k + 1] += ur * xi + ui * xr;
+  }
+}
+
+// y[k] += u conj(x[k])
+inline void caxpy_conj(cdouble u, const cdouble* x, cdouble* y, size_t n) {
+  const double ur = u.real(), ui = u.imag();
+  const double* X = reinterpret_cast<const double*>(x);
+  double* Y = reinterpret_cast<double*>(y);
+  for (size_t k = 0; k < n; ++k) {
+    const double xr = X[2 * k], xi = X[2 * k + 1];
+    Y[2 * k] += ur * xr + ui * xi;
+    Y[2 * k + 1] += ui * xr - ur * xi;
+  }
+}
+
 // Gauss-Legendre nodes (ascending) and weights on [-1, 1], by Newton's method
 // on P_n from the asymptotic initial guesses.
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
