@@ -14,11 +14,39 @@ namespace fmm {
 // diagonal d[0..n) and off-diagonal e[i] = T[i+1][i] (e[n-1] unused); the
 // rotations are accumulated into the eigenvector matrix, stored transposed
 // (Zt[j] is eigenvector j, contiguous) so that a rotation of two vectors
-// touches two contiguous rows.
+// touches two contiguous rows.  The rotations of one iteration are recorded
+// and then applied to blocks of columns of Zt on the host cores: every
+// column sees the same rotations in the same order as one at a time would
+// apply them, so the result does not depend on the split.
 static void tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Zt) {
   const double eps = 2.220446049250313e-16;
   e.resize(n);
   e[n - 1] = 0.0;
+  std::vector<double> rc(n), rs(n);
+  // rotations i = hi, hi - 1, ..., lo of rows (i, i + 1)
+  auto rotate = [&](int hi, int lo) {
+    if (hi < lo) return;
+    constexpr int kCols = 64;
+    auto block = [&](int b) {
+      const int k0 = b * kCols, k1 = std::min(n, k0 + kCols);
+      for (int i = hi; i >= lo; --i) {
+        const double c = rc[i], s = rs[i];
+        double* za = &Zt[(size_t)i * n];
+        double* zb = &Zt[(size_t)(i + 1) * n];
+        for (int k = k0; k < k1; ++k) {
+          const double zi = za[k], zi1 = zb[k];
+          zb[k] = s * zi + c * zi1;
+          za[k] = c * zi - s * zi1;
+        }
+      }
+    };
+    const int nb = (n + kCols - 1) / kCols;
+    if ((int64_t)(hi - lo + 1) * n >= (1 << 16) && nb > 1) {
+      parallel_for(nb, block);
+    } else {
+      for (int b = 0; b < nb; ++b) block(b);
+    }
+  };
   for (int l = 0; l < n; ++l) {
     for (int iter = 0; iter < 100; ++iter) {
       int m = l;
@@ -51,14 +79,11 @@ static void tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, st
         p = s * r;
         d[i + 1] = g + p;
         g = c * r - b;
-        double* za = &Zt[(size_t)i * n];
-        double* zb = &Zt[(size_t)(i + 1) * n];
-        for (int k = 0; k < n; ++k) {
-          const double zi = za[k], zi1 = zb[k];
-          zb[k] = s * zi + c * zi1;
-          za[k] = c * zi - s * zi1;
-        }
+        rc[i] = c;
+        rs[i] = s;
       }
+      // recorded: m - 1 down to l, or down to i + 1 when the sweep stopped early
+      rotate(m - 1, underflow ? i + 1 : l);
       if (underflow) continue;
       d[l] -= p;
       e[l] = g;
@@ -161,10 +186,9 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
   if (m <= N) {
     // G = A A^H (m x m)
     std::vector<cdouble> G((size_t)m * m, cdouble(0.0, 0.0));
-    parallel_for((int)m, [&](int i) {
-      const cdouble* a = A + (size_t)i * N;
-      for (int64_t j = i; j < m; ++j) G[(size_t)i * m + j] = cdot_conj(a, A + (size_t)j * N, (size_t)N);
-    });
+    std::vector<const cdouble*> rows(m);
+    for (int64_t i = 0; i < m; ++i) rows[i] = A + (size_t)i * N;
+    gram_upper(rows.data(), m, N, G.data());
     for (int64_t i = 0; i < m; ++i)
       for (int64_t j = i + 1; j < m; ++j) G[(size_t)j * m + i] = std::conj(G[(size_t)i * m + j]);
     hermitian_eig_auto((int)m, G, lam, V);
@@ -175,15 +199,16 @@ int truncated_left(const cdouble* A, int64_t m, int64_t N, double delta, int rul
   } else {
     // G = A^H A (N x N): G[i][j] = sum_row conj(A[row][i]) A[row][j]
     std::vector<cdouble> G((size_t)N * N, cdouble(0.0, 0.0));
-    // row i of G accumulates conj(A[row][i]) A[row][j>=i] over the rows of A,
-    // each read contiguously
+    // G = conj(At At^H) with At = A^T (N x m): the Gram of At's rows
+    std::vector<cdouble> At((size_t)N * m);
     parallel_for((int)N, [&](int i) {
-      cdouble* g = &G[(size_t)i * N];
-      for (int64_t row = 0; row < m; ++row) {
-        const cdouble* a = A + (size_t)row * N;
-        caxpy(std::conj(a[i]), a + i, g + i, (size_t)(N - i));
-      }
+      for (int64_t row = 0; row < m; ++row) At[(size_t)i * m + row] = A[(size_t)row * N + i];
     });
+    std::vector<const cdouble*> rows(N);
+    for (int64_t i = 0; i < N; ++i) rows[i] = &At[(size_t)i * m];
+    gram_upper(rows.data(), N, m, G.data());
+    for (int64_t i = 0; i < N; ++i)
+      for (int64_t j = i; j < N; ++j) G[(size_t)i * N + j] = std::conj(G[(size_t)i * N + j]);
     for (int64_t i = 0; i < N; ++i)
       for (int64_t j = i + 1; j < N; ++j) G[(size_t)j * N + i] = std::conj(G[(size_t)i * N + j]);
     hermitian_eig_auto((int)N, G, lam, V);
@@ -267,9 +292,11 @@ void hosvd4(const std::vector<std::vector<cdouble>>& Tp, const int n[3], double 
   }
   // mode 4: G4[p][q] = <T_p, T_q>
   G[3].assign((size_t)K * K, cdouble(0.0, 0.0));
-  parallel_for(K, [&](int p) {
-    for (int q = p; q < K; ++q) G[3][(size_t)p * K + q] = cdot_conj(Tp[p].data(), Tp[q].data(), N);
-  });
+  {
+    std::vector<const cdouble*> rows(K);
+    for (int p = 0; p < K; ++p) rows[p] = Tp[p].data();
+    gram_upper(rows.data(), K, (int64_t)N, G[3].data());
+  }
   for (int mode = 0; mode < 4; ++mode) {
     const int m = dims[mode];
     for (int i = 0; i < m; ++i)

@@ -34,6 +34,45 @@ void parallel_for(int n, const std::function<void(int)>& fn) {
   for (auto& t : th) t.join();
 }
 
+void gram_upper(const cdouble* const* rows, int64_t m, int64_t N, cdouble* G) {
+  constexpr int kB = 8;          // rows per block
+  constexpr int64_t kC = 256;    // terms of the sum per chunk (4 KB of a row)
+  const int64_t nb = (m + kB - 1) / kB;
+  parallel_for((int)nb, [&](int b) {
+    const int64_t i0 = (int64_t)b * kB;
+    const int ni = (int)std::min<int64_t>(kB, m - i0);
+    // partial sums [j - i0][u] (re, im) of block row u against row j
+    std::vector<double> acc((size_t)(m - i0) * kB * 2, 0.0);
+    for (int64_t k0 = 0; k0 < N; k0 += kC) {
+      const int64_t kn = std::min(kC, N - k0);
+      const double* x[kB];
+      for (int u = 0; u < kB; ++u) x[u] = reinterpret_cast<const double*>(rows[i0 + std::min(u, ni - 1)] + k0);
+      for (int64_t j = i0; j < m; ++j) {
+        const double* y = reinterpret_cast<const double*>(rows[j] + k0);
+        double re[kB] = {}, im[kB] = {};
+        for (int64_t k = 0; k < kn; ++k) {
+          const double yr = y[2 * k], yi = y[2 * k + 1];
+          for (int u = 0; u < kB; ++u) {
+            const double xr = x[u][2 * k], xi = x[u][2 * k + 1];
+            re[u] += xr * yr + xi * yi;
+            im[u] += xi * yr - xr * yi;
+          }
+        }
+        double* s = &acc[(size_t)(j - i0) * kB * 2];
+        for (int u = 0; u < kB; ++u) {
+          s[2 * u] += re[u];
+          s[2 * u + 1] += im[u];
+        }
+      }
+    }
+    for (int64_t j = i0; j < m; ++j)
+      for (int u = 0; u < ni && i0 + u <= j; ++u) {
+        const double* s = &acc[((size_t)(j - i0) * kB + u) * 2];
+        G[(size_t)(i0 + u) * m + j] = cdouble(s[0], s[1]);
+      }
+  });
+}
+
 // ---------------------------------------------------------------------------
 // directions (Sec. II.A)
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <complex>
+#include <cstdint>
 #include <functional>
 #include <vector>
 
@@ -88,6 +89,13 @@ inline void caxpy_conj(cdouble u, const cdouble* x, cdouble* y, size_t n) {
     Y[2 * k + 1] += ui * xr - ur * xi;
   }
 }
+
+// Upper triangle (j >= i) of the Gram matrix G[i][j] = sum_k x_i[k] conj(x_j[k])
+// of m rows of length N (row i at rows[i]); G is m x m row-major, entries
+// below the diagonal are left as they are.  Blocks of eight rows meet every
+// later row over chunks of the sum, so a block stays in cache while the other
+// rows stream past it; the blocks run on the host cores.
+void gram_upper(const cdouble* const* rows, int64_t m, int64_t N, cdouble* G);
 
 // Gauss-Legendre nodes (ascending) and weights on [-1, 1], by Newton's method
 // on P_n from the asymptotic initial guesses.
