@@ -300,12 +300,12 @@ void host_prepass(const Layout& L, std::vector<cdouble>& scratch) {
       const cdouble* A = (const cdouble*)g.A;
       const cdouble* B = (const cdouble*)g.B;
       cdouble* C = (cdouble*)g.C;
-      for (int m = 0; m < g.M; ++m)
-        for (int nn = 0; nn < g.N; ++nn) {
-          cdouble acc(0.0, 0.0);
-          for (int k = 0; k < g.K; ++k) acc += A[(size_t)m * g.K + k] * B[(size_t)k * g.N + nn];
-          C[(size_t)m * g.N + nn] = acc;
-        }
+      // row m of C accumulates A[m][k] B[k][:] in the order of k
+      for (int m = 0; m < g.M; ++m) {
+        cdouble* c = C + (size_t)m * g.N;
+        for (int nn = 0; nn < g.N; ++nn) c[nn] = cdouble(0.0, 0.0);
+        for (int k = 0; k < g.K; ++k) caxpy(A[(size_t)m * g.K + k], B + (size_t)k * g.N, c, (size_t)g.N);
+      }
     });
 }
 
@@ -318,22 +318,17 @@ void host_slabs(const Layout& L, const SlabDesc& d, cdouble* o) {
     const cdouble* H = (const cdouble*)d.h + (size_t)x * d.hx;
     if (L.yz_fmt == 1) {
       const cdouble* U2 = (const cdouble*)d.u2;
-      for (int y = 0; y < n2; ++y)
-        for (int c = 0; c < d.rb; ++c) {
-          cdouble acc(0.0, 0.0);
-          for (int b = 0; b < d.ra; ++b) acc += U2[(size_t)y * d.ra + b] * H[(size_t)b * d.rb + c];
-          G[(size_t)y * d.rb + c] = acc;
-        }
+      for (int y = 0; y < n2; ++y) {
+        cdouble* g = &G[(size_t)y * d.rb];
+        for (int c = 0; c < d.rb; ++c) g[c] = cdouble(0.0, 0.0);
+        for (int b = 0; b < d.ra; ++b) caxpy(U2[(size_t)y * d.ra + b], H + (size_t)b * d.rb, g, (size_t)d.rb);
+      }
     } else {
       for (size_t i = 0; i < (size_t)n2 * d.rb; ++i) G[i] = H[i];
     }
     cdouble* ox = o + (size_t)x * n2 * n3;
     for (int y = 0; y < n2; ++y)
-      for (int z = 0; z < n3; ++z) {
-        cdouble acc(0.0, 0.0);
-        for (int c = 0; c < d.rb; ++c) acc += U3[(size_t)z * d.rb + c] * G[(size_t)y * d.rb + c];
-        ox[(size_t)y * n3 + z] = acc;
-      }
+      for (int z = 0; z < n3; ++z) ox[(size_t)y * n3 + z] = cdot(U3 + (size_t)z * d.rb, &G[(size_t)y * d.rb], d.rb);
   }
 }
 
