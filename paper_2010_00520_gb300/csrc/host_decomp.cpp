@@ -365,15 +365,29 @@ void htucker4(const std::vector<std::vector<cdouble>>& Tp, const int n[3], doubl
   }
   const int r1 = tk.r[0], r2 = tk.r[1], r3 = tk.r[2], r4 = tk.r[3];
   const int64_t m12 = (int64_t)r1 * r2, m34 = (int64_t)r3 * r4;
-  // W12 = core as (r1 r2) x (r3 r4); node {1,2}
+  // W12 = core as (r1 r2) x (r3 r4); node {1,2}: W12 ~ C12 S V^H, Q12 = S V^H
   std::vector<cdouble> Q12;
   out.r[4] = truncated_left(tk.core.data(), m12, m34, delta, rule, out.C12, Q12);
-  // node {3,4}: W12^T
-  std::vector<cdouble> W34((size_t)m34 * m12), Q34;
-  for (int64_t i = 0; i < m12; ++i)
-    for (int64_t j = 0; j < m34; ++j) W34[(size_t)j * m12 + i] = tk.core[(size_t)i * m34 + j];
-  out.r[5] = truncated_left(W34.data(), m34, m12, delta, rule, out.C34, Q34);
-  const int r12 = out.r[4], r34 = out.r[5];
+  const int r12 = out.r[4];
+  // node {3,4}: its matricization W12^T = conj(V) S C12^T has the same
+  // singular values, so the same rank at the same budget, and left singular
+  // vectors conj(V) = (S^-1 Q12)^T; S is read off the row norms of Q12.
+  // Directions whose singular value is lost in rounding are dropped, as in
+  // the Gram route of truncated_left.
+  std::vector<double> sig(r12, 0.0);
+  parallel_for(r12, [&](int t) {
+    double s2 = 0.0;
+    for (int64_t j = 0; j < m34; ++j) s2 += std::norm(Q12[(size_t)t * m34 + j]);
+    sig[t] = std::sqrt(s2);
+  });
+  int r34 = r12;
+  while (r34 > 1 && !(sig[r34 - 1] > sig[0] * 1e-14)) --r34;
+  out.r[5] = r34;
+  out.C34.assign((size_t)m34 * r34, cdouble(0.0, 0.0));
+  for (int t = 0; t < r34; ++t) {
+    const double inv = 1.0 / sig[t];
+    for (int64_t j = 0; j < m34; ++j) out.C34[(size_t)j * r34 + t] = Q12[(size_t)t * m34 + j] * inv;
+  }
   // B = C12^H W12 conj(C34) = Q12 conj(C34)
   out.B.assign((size_t)r12 * r34, cdouble(0.0, 0.0));
   parallel_for(r12, [&](int s) {
