@@ -6,8 +6,9 @@ the kernels follow (pre-pass products, then each direction's slab formula),
 so these tests pin the decompositions and the descriptor plumbing of all five
 formats against the oracle:
   * Tucker-3D, TT-3D, Tucker-4D, H-Tucker: the library's ranks equal the
-    oracle's (same algorithm, same truncation rule) and the restoration error
-    equals the oracle's to rounding;
+    oracle's (same algorithm, same truncation rule), the restoration error
+    equals the oracle's to rounding, and the stored element count and memory
+    saving (Sec. III) equal the oracle's;
   * TT-4D: the library runs TT-SVD on the Tucker core of T_4D (budget
     gamma ||T|| / sqrt(7) per step); its error must stay within gamma and its
     ranks within the oracle's direct TT-SVD ranks at gamma / sqrt(7) * sqrt(3).
@@ -23,10 +24,11 @@ FMT = {"3d": 3, "4d": 4}
 DEC = {"tucker": 1, "tt": 2, "htucker": 3}
 
 
-def _host(native, K, L, fmt, dec, tol):
+def _host(native, K, L, fmt, dec, tol, stats=False):
     h = native.fmmfft_plan_create(*K, 0.5, TWO_PI, L, FMT[fmt], DEC[dec], tol)
     try:
-        return native.fmmfft_compress_host(h)
+        ranks, R = native.fmmfft_compress_host(h)
+        return (ranks, R, native.fmmfft_plan_stats(h)) if stats else (ranks, R)
     finally:
         native.fmmfft_plan_destroy(h)
 
@@ -48,7 +50,7 @@ def test_library_compression_matches_oracle(native, fmt, dec, K, L, tol):
     plan = pl.Plan(K=K, L=L)
     ops = pl.operators(plan)
     comp = pl.compress(ops, fmt, dec, tol)
-    ranks, R = _host(native, K, L, fmt, dec, tol)
+    ranks, R, st = _host(native, K, L, fmt, dec, tol, stats=True)
     T4 = np.stack(ops)
     ref = np.stack([comp.restore(p) for p in range(plan.n_dir)])
     err, err_ref = _rel(R, T4), _rel(ref, T4)
@@ -60,6 +62,11 @@ def test_library_compression_matches_oracle(native, fmt, dec, K, L, tol):
     else:
         got = [int(v) for v in ranks if v]
         assert tuple(got) == tuple(comp.parts.ranks)
+    # equal ranks, so the stored element counts (Sec. III's memory saving,
+    # counted by the oracle as the storage pins fix it) must agree exactly
+    assert st["elements_compressed"] == comp.elements()
+    assert st["elements_plain"] == int(np.prod(comp.shape))
+    assert st["saving"] == pytest.approx(comp.saving(), abs=1e-12)
 
 
 @pytest.mark.parametrize("K,L,tol", [((6, 5, 7), 3, 1e-4), ((8, 8, 8), 4, 1e-3)])
@@ -67,8 +74,13 @@ def test_library_tt4d_within_tolerance(native, K, L, tol):
     plan = pl.Plan(K=K, L=L)
     ops = pl.operators(plan)
     T4 = np.stack(ops)
-    ranks, R = _host(native, K, L, "4d", "tt", tol)
+    ranks, R, st = _host(native, K, L, "4d", "tt", tol, stats=True)
     assert _rel(R, T4) <= tol
+    # its ranks are its own, so its element count is checked against Eq. 14's
+    # storage written out with them
+    r1, r2, r3 = (int(v) for v in ranks[:3])
+    n1, n2, n3 = plan.n
+    assert st["elements_compressed"] == n1 * r1 + r1 * n2 * r2 + r2 * n3 * r3 + plan.n_dir * r3
     # each TT step of the library truncates at budget gamma ||T|| / sqrt(7);
     # a direct TT-SVD at that per-step budget (gamma' = gamma sqrt(3/7)) can
     # keep no fewer ranks than an optimal one, so it bounds the library's
