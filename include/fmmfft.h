@@ -324,8 +324,11 @@ int fmmfft_translate(fmmfft_plan plan, const void* S_in, void* S_out, int nrhs, 
  * Arguments, layouts, ownership and results are those of fmmfft_translate;
  * FMMFFT_KEY_PROFILE is ignored (no stage times are recorded).
  * Set-up: the first call on a device, with that device current, looks up the
- * device address of the array (cudaGetSymbolAddress); make that first call
- * before any stream capture begins.
+ * device address of the array (cudaGetSymbolAddress) and keeps it for the
+ * later calls on that device; make that first call before any stream capture
+ * begins.  The kept address belongs to the device's current context: after
+ * cudaDeviceReset (or anything else that destroys the primary context) it is
+ * stale, so do not call this entry point again in that process after a reset.
  * Sharing: every call, from any plan or thread, uses the same array.  Calls
  * whose kernels overlap on the GPU (different streams, or host threads
  * without ordering between them) race on it and give wrong results; order
@@ -467,7 +470,11 @@ int fmmfft_batch_destroy(fmmfft_batch batch);
  * there for the same device, grid, format, precision, ranks and nrhs is
  * applied without timing, and a newly tuned one is appended.  The schedule
  * changes only speed, not the results beyond rounding; fmmfft_stats reports
- * it.  Errors: NOT_COMPRESSED, INVALID_ARG, OOM, CUDA.
+ * it.  A candidate that sets a bit of the device status word (a rank over its
+ * launch's shared memory, a tensor-core wait limit) is dropped; the status
+ * word and the stream fmmfft_poll_status waits on are left as the caller's
+ * last translation left them (the call first waits for that stream).
+ * Errors: NOT_COMPRESSED, INVALID_ARG, OOM, CUDA.
  * fmmfft_batch_autotune: the same for every plan of a batch (nrhs[i] RHS,
  * budget_ms shared evenly); drops the batch's captured graph.
  */

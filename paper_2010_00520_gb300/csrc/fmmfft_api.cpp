@@ -1466,6 +1466,23 @@ int fmmfft_autotune(fmmfft_plan p, int nrhs, double budget_ms) {
     st = FMMFFT_ERR_CUDA;
   const bool profile = p->profile;
   p->profile = false;
+  // the caller's stream and status word stay as they were: the timing runs on
+  // a private stream, whose handle must not outlive this call in last_stream,
+  // and a status bit raised by a candidate belongs to that candidate alone
+  cudaStream_t caller_stream = p->last_stream;
+  int prior_status = 0;
+  if (st == FMMFFT_OK && p->d_status) {
+    if (cudaStreamSynchronize(caller_stream) != cudaSuccess ||
+        cudaMemcpy(&prior_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = FMMFFT_ERR_CUDA;
+  }
+  auto take_status = [&](int* word) -> bool {   // read and clear; false on a CUDA error
+    *word = 0;
+    if (!p->d_status) return true;
+    return cudaStreamSynchronize(s) == cudaSuccess &&
+           cudaMemcpy(word, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+           cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess;
+  };
   fmm::Schedule best = before;
   float best_ms = 0.f;
   bool have = false;
@@ -1484,8 +1501,18 @@ int fmmfft_autotune(fmmfft_plan p, int nrhs, double budget_ms) {
     cudaEventRecord(e1, s);
     if (rs != FMMFFT_OK || cudaEventSynchronize(e1) != cudaSuccess) {
       cudaGetLastError();
+      int ignored = 0;
+      take_status(&ignored);
       continue;
     }
+    // a candidate that tripped a device check (rank over its shared memory,
+    // a tensor-core wait limit) is not a valid schedule, however fast
+    int cand_status = 0;
+    if (!take_status(&cand_status)) {
+      st = FMMFFT_ERR_CUDA;
+      break;
+    }
+    if (cand_status != 0) continue;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     ms /= reps;
@@ -1502,6 +1529,10 @@ int fmmfft_autotune(fmmfft_plan p, int nrhs, double budget_ms) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
+  p->last_stream = caller_stream;
+  if (p->d_status && cudaMemcpy(p->d_status, &prior_status, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess &&
+      st == FMMFFT_OK)
+    st = FMMFFT_ERR_CUDA;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   free_dev(din);

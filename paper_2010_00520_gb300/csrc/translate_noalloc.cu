@@ -23,7 +23,9 @@ void* g_scratch_addr[fmm::kMaxDevices] = {};
 
 // Device address of g_translate_scratch on the current device.  In host code
 // the array's name stands for a host-side shadow, not device memory, so the
-// address comes from the runtime once per device and is cached.
+// address comes from the runtime once per device and is cached.  The cache is
+// tied to the context the first call saw: a cudaDeviceReset invalidates it
+// (the header tells callers not to use this entry point after a reset).
 int scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {

@@ -86,6 +86,70 @@ def field_spectra_rows(seed: int, n_dir: int, nrhs: int, K: tuple[int, int, int]
     return out
 
 
+def _u64_as_i64(v: int) -> int:
+    """The int64 with the same 64 bits as the unsigned value v."""
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _shr(z, k: int):
+    """Logical right shift of int64 words holding uint64 bit patterns."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def complex_gaussian_torch(seed: int, count: int, offset: int = 0, device="cpu", chunk: int = 1 << 24):
+    """The values of complex_gaussian(seed, count, offset), computed with
+    PyTorch int64 / float64 tensor operations on `device` (same SplitMix64
+    words, same uniforms, Box-Muller in float64): complex128 tensor.
+
+    For workloads whose fields take gigabytes, where the NumPy generator would
+    take minutes.  The integer steps (int64 words with wrap-around products
+    and masked shifts standing in for uint64 arithmetic) give the same bits;
+    log, cos and sin are the device library's float64 functions, so values may
+    differ from NumPy's in the last bit of float64 (and, rarely, one bit of a
+    value rounded to complex64)."""
+    import torch
+
+    g = _u64_as_i64(0x9E3779B97F4A7C15)
+    m1, m2 = _u64_as_i64(0xBF58476D1CE4E5B9), _u64_as_i64(0x94D049BB133111EB)
+    s0 = _u64_as_i64(seed)
+    out = torch.empty(count, dtype=torch.complex128, device=device)
+
+    def words(ctr):
+        z = s0 + (ctr + 1) * g
+        z = (z ^ _shr(z, 30)) * m1
+        z = (z ^ _shr(z, 27)) * m2
+        return z ^ _shr(z, 31)
+
+    for c0 in range(0, count, chunk):
+        n = min(chunk, count - c0)
+        idx = torch.arange(offset + c0, offset + c0 + n, dtype=torch.int64, device=device)
+        u1 = (_shr(words(2 * idx), 11).to(torch.float64) + 1.0) * (2.0 ** -53)
+        u2 = (_shr(words(2 * idx + 1), 11).to(torch.float64) + 1.0) * (2.0 ** -53)
+        rad = torch.sqrt(-torch.log(u1))
+        ang = 2.0 * np.pi * u2
+        out[c0:c0 + n] = torch.complex(rad * torch.cos(ang), rad * torch.sin(ang))
+    return out
+
+
+def field_spectra_torch(seed: int, n_dir: int, nrhs: int, K: tuple[int, int, int], first: int = 0,
+                        count: int | None = None, device="cpu", dtype=None):
+    """Directions first .. first + count - 1 of field_spectra(seed, n_dir, nrhs,
+    K), generated on `device` one direction at a time by complex_gaussian_torch
+    and stored as `dtype` (default complex64): shape (count, 2, nrhs, Kz, Ky, Kx)."""
+    import torch
+
+    Kx, Ky, Kz = K
+    count = n_dir - first if count is None else count
+    dtype = torch.complex64 if dtype is None else dtype
+    per_dir = 2 * nrhs * Kx * Ky * Kz
+    out = torch.empty((count, 2, nrhs, Kz, Ky, Kx), dtype=dtype, device=device)
+    for q in range(count):
+        vals = complex_gaussian_torch(seed, per_dir, (first + q) * per_dir, device=device)
+        out[q] = vals.reshape(2, nrhs, Kz, Ky, Kx).to(dtype)
+    return out
+
+
 # Workloads (box grids, multipole counts, formats) of the synthetic benchmark
 # suite.  All use box edge a = 0.5 wavelengths with wavelength 1 (k0 = 2 pi),
 # the Chebyshev near rule max|d_i| <= 1 and N_phi = 2(L+1).

@@ -89,3 +89,22 @@ def test_batch_autotune_then_translate(native, cuda, monkeypatch):
     finally:
         for h in plans:
             F.fmmfft_plan_destroy(h)
+
+
+def test_poll_straight_after_autotune(native, cuda):
+    """The timing stream is private to the autotuner: a poll right after it
+    (no translation in between) must neither wait on a destroyed stream nor
+    see a status bit left by a candidate."""
+    F, torch = native, cuda
+    K, nrhs = (9, 30, 32), 2
+    h = _plan(F, K)
+    try:
+        nd = F.fmmfft_plan_stats(h)["n_dir"]
+        x = torch.from_numpy(field_spectra(6, nd, nrhs, K).astype(np.complex64)).to("cuda")
+        y = torch.empty_like(x)
+        F.fmmfft_translate(h, x, y, nrhs, torch.cuda.current_stream())
+        F.fmmfft_autotune(h, nrhs, 2000.0)
+        assert F.fmmfft_poll_status(h) == 0
+        assert F.fmmfft_poll_status(h) == 0
+    finally:
+        F.fmmfft_plan_destroy(h)
