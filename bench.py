@@ -446,6 +446,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=0, help="override the RHS count (profiling cases)")
+    ap.add_argument("--L", type=int, default=-1, help="override the multipole count (profiling cases)")
     ap.add_argument("--only", default="both", choices=["both", "compressed", "plain"])
     ap.add_argument("--restore", default="", choices=["", "3xtf32", "bf16x3", "tf32", "fp32"],
                     help="restore arithmetic of the compressed arm (default: the workload's): tensor cores "
@@ -456,6 +457,8 @@ def main():
                          "per GPU (default; strong scaling), or independent problems per GPU (weak scaling)")
     ap.add_argument("--no-farfield", action="store_true",
                     help="skip timing the aggregation / disaggregation steps (Eqs. 4, 6)")
+    ap.add_argument("--no-occupancy", action="store_true",
+                    help="skip timing the translation on a shell occupancy mask (Sec. II.A)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default schedule instead of autotuning each arm before timing")
     ap.add_argument("--workload", default=DEFAULT_WL, choices=sorted(WORKLOADS))
@@ -498,6 +501,10 @@ def main():
             dist.barrier()
 
     W = workload(args.workload)
+    if args.L >= 0:
+        W["L"] = args.L
+        W["name"] = W["name"].replace(f"_L{WORKLOADS[args.workload]['L']}_", f"_L{args.L}_")
+        args.no_cpu_baseline = True
     K, L, nrhs = W["K"], W["L"], (args.nrhs or W["nrhs"])
     shard = args.shard == "directions" and world > 1
     n_dir_grid = n_dir_of(W)
@@ -575,6 +582,10 @@ def main():
             return _units(n, n_dir_grid, nrhs) / seconds
         return job_throughput(units, world, seconds)
 
+    def spread(v):
+        q = statistics.quantiles(v, n=4) if len(v) >= 2 else [v[0]] * 3
+        return {"median": statistics.median(v), "p25": q[0], "p75": q[2], "min": min(v), "max": max(v)}
+
     clocks = ClockSampler(local)
     clocks.start()
     ms, per_step = {}, {}
@@ -585,9 +596,25 @@ def main():
         assert F.fmmfft_poll_status(h) == 0
     value = {name: job_value(t * 1e-3) / 1e9 for name, t in ms.items()}
 
-    def spread(v):
-        q = statistics.quantiles(v, n=4) if len(v) >= 2 else [v[0]] * 3
-        return {"median": statistics.median(v), "p25": q[0], "p75": q[2], "min": min(v), "max": max(v)}
+
+    # the same arm on the shell of boxes a meshed sphere occupies (Sec. II.A:
+    # empty boxes carry no sources and receive nothing; x-lines with no
+    # occupied box are pruned from both x passes)
+    occupancy = None
+    if not args.no_occupancy and world == 1:
+        from seeded_inputs import shell_occupancy
+        m = shell_occupancy(K)
+        hm = plans[main_arm]
+        F.fmmfft_plan_set_occupancy(hm, m)
+        ms_m, per_m = timed(hm, args.steps)
+        assert F.fmmfft_poll_status(hm) == 0
+        F.fmmfft_plan_set_occupancy(hm, None)
+        occupancy = {"mask": "shell of boxes within one box edge of the inscribed sphere",
+                     "occupied_boxes": int(m.sum()), "boxes": int(m.size),
+                     "occupied_x_lines": int(m.any(axis=2).sum()), "x_lines": int(K[1] * K[2]),
+                     "ms_per_step": ms_m, "per_step_ms": spread(per_m),
+                     "value": job_value(ms_m * 1e-3) / 1e9, "unit": UNIT,
+                     "note": "same metric (padded voxels x fields / t): the pruned x-lines are not discounted"}
 
     # per-stage device times (CUDA events on the launch stream between the
     # kernels, which then run serially)
@@ -634,6 +661,8 @@ def main():
 
         ms_agg = t_ff(lambda: F.fmmfft_aggregate(hf, Pd, Id, Ad, nb, nrhs, stream))
         ms_dis = t_ff(lambda: F.fmmfft_disaggregate(hf, Pd, x, Yd, nb, nrhs, stream))
+        # Eq. 5 and Eq. 6 in one call: the translated fields stay on chip
+        ms_tdis = t_ff(lambda: F.fmmfft_translate_disaggregate(hf, x, Pd, Yd, nb, nrhs, stream))
         pk = _peaks()[0].get("hbm_gbs", 6800.0)
         es = x.element_size()
         b_agg = (Pd.numel() + Id.numel() + Ad.numel()) * es
@@ -645,7 +674,9 @@ def main():
                     "disaggregate": {"ms": ms_dis, "algorithmic_bytes": b_dis,
                                      "achieved_gbs": b_dis / (ms_dis * 1e-3) / 1e9,
                                      "frac_of_hbm": b_dis / (ms_dis * 1e-3) / 1e9 / pk},
-                    "far_field_matvec_ms": ms_agg + ms[main_arm] + ms_dis}
+                    "far_field_matvec_ms": ms_agg + ms[main_arm] + ms_dis,
+                    "translate_disaggregate_ms": ms_tdis,
+                    "far_field_matvec_fused_ms": ms_agg + ms_tdis}
         del Pd, Id, Ad, Yd
         torch.cuda.empty_cache()
 
@@ -767,6 +798,8 @@ def main():
         out["e2e"] = e2e
     if farfield is not None:
         out["farfield"] = farfield
+    if occupancy is not None:
+        out["occupancy_shell"] = occupancy
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nrhs == W["nrhs"]:
         import tempfile
         with tempfile.TemporaryDirectory() as td:

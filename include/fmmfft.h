@@ -309,6 +309,27 @@ int fmmfft_import_tt4d(fmmfft_plan plan, const int* ranks, const double* U1, con
 int fmmfft_translate(fmmfft_plan plan, const void* S_in, void* S_out, int nrhs, void* stream);
 
 /*
+ * Box occupancy (Sec. II.A): boxes that hold no basis function carry no
+ * source (A_v = 0) and need no translated field.  `occupied` is a host array
+ * of Kx Ky Kz bytes, box index v = (z Ky + y) Kx + x, nonzero for an occupied
+ * box; NULL clears the mask (every box occupied, the default).  With a mask,
+ * every translation of the plan (fmmfft_translate and its host, batch and
+ * allocation-free forms, and fmmfft_translate_disaggregate) reads S_in only
+ * at occupied boxes (others taken as zero), writes zero to S_out at empty
+ * boxes, and prunes its FFTs: an x-line (y, z) with no occupied box is
+ * neither read nor transformed in either x pass.  The result at occupied
+ * boxes equals fmmfft_translate of the input with its empty boxes zeroed.
+ * May be called before or after fmmfft_compress.  The first call with a mask
+ * allocates Kx Ky Kz + Ky Kz bytes on the current device (kept until
+ * fmmfft_plan_destroy); every call waits for the device to finish the work
+ * already queued (a kernel in flight may read the previous mask) and copies
+ * the mask synchronously.  A batch's CUDA graph keeps the occupancy its plans
+ * had when it was captured (set masks before a batch's first translation).
+ * The mask is not part of plan files.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int fmmfft_plan_set_occupancy(fmmfft_plan plan, const unsigned char* occupied);
+
+/*
  * Allocation-free variant of fmmfft_translate (the paper has no counterpart;
  * this is an interface for callers).  Some callers cannot call cudaMalloc
  * while they translate: an iterative solver that runs inside a framework
@@ -419,6 +440,26 @@ int fmmfft_aggregate(fmmfft_plan plan, const void* patterns, const void* current
                      int nrhs, void* stream);
 int fmmfft_disaggregate(fmmfft_plan plan, const void* patterns, const void* B, void* y, int nb,
                         int nrhs, void* stream);
+
+/*
+ * Translation (Eq. 5) and disaggregation (Eq. 6) in one call, the translated
+ * fields kept on chip:
+ *   y[r][i][v] = sum_p w_p sum_c conj(P[p][c][i][v]) B[p][c][r][v],
+ *   B = fmmfft_translate(S_in)
+ * with the arrays, layouts and weights of fmmfft_disaggregate.  The inverse x
+ * DFT of the translation (the last step of Eq. 5) hands each field's boxes to
+ * the sum of Eq. 6 in shared memory, so B is neither stored nor read back.
+ * Asynchronous on `stream`; the plan must hold an operator (NOT_COMPRESSED
+ * otherwise) and uses its intermediate buffer as fmmfft_translate does
+ * (allocated on the first call, or when nrhs grows).  Each output sums over
+ * four consecutive quarters of the directions added in a fixed order:
+ * reproducible bit for bit (the sum order differs from fmmfft_disaggregate's,
+ * so the two agree to rounding).  Errors: those of fmmfft_disaggregate (y
+ * must not overlap S_in or the patterns), NOT_COMPRESSED, UNSUPPORTED
+ * (Kx > 128, nb > 48).
+ */
+int fmmfft_translate_disaggregate(fmmfft_plan plan, const void* S_in, const void* patterns, void* y, int nb,
+                                  int nrhs, void* stream);
 
 /*
  * The multipole count L of the excess-bandwidth rule (Sec. II.A) for boxes of

@@ -155,6 +155,16 @@ def translate_with(restore, S_in: np.ndarray, dirs=None) -> np.ndarray:
     return out
 
 
+def translate_occupied(restore, S_in: np.ndarray, occupied: np.ndarray, dirs=None) -> np.ndarray:
+    """Eq. 5 on a grid whose empty boxes hold no basis function (Sec. II.A):
+    the aggregated field of an empty box is zero (A_v = 0) and no translated
+    field is needed there.  `occupied` is a (Kz, Ky, Kx) boolean array; inputs
+    at empty boxes are taken as zero and outputs there are zero."""
+    m = np.asarray(occupied, dtype=bool)
+    out = translate_with(restore, np.where(m, S_in, 0), dirs)
+    return np.where(m, out, 0)
+
+
 def relative_l2(x, ref) -> float:
     ref = np.asarray(ref)
     den = np.linalg.norm(ref)

@@ -70,7 +70,7 @@ EXPORTED = (
     "fmmfft_import_htucker", "fmmfft_import_tt4d", "fmmfft_compress_host",
     "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy", "fmmfft_plan_save",
     "fmmfft_plan_load", "fmmfft_autotune", "fmmfft_batch_autotune", "fmmfft_multipole_count",
-    "fmmfft_aggregate", "fmmfft_disaggregate",
+    "fmmfft_aggregate", "fmmfft_disaggregate", "fmmfft_translate_disaggregate", "fmmfft_plan_set_occupancy",
 )
 
 
@@ -140,6 +140,8 @@ def lib() -> ctypes.CDLL:
         "fmmfft_multipole_count": [d, d, d, d, d, ip],
         "fmmfft_aggregate": [vp, vp, vp, vp, i, i, vp],
         "fmmfft_disaggregate": [vp, vp, vp, vp, i, i, vp],
+        "fmmfft_translate_disaggregate": [vp, vp, vp, vp, i, i, vp],
+        "fmmfft_plan_set_occupancy": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -453,6 +455,32 @@ def fmmfft_disaggregate(plan, patterns, B, y, nb, nrhs, stream=None):
     p, o, b = _far_field(plan, patterns, y, B, int(nb), int(nrhs), "fmmfft_disaggregate",
                          ("patterns", "y", "B"))
     _check(lib().fmmfft_disaggregate(plan, p, b, o, int(nb), int(nrhs), _stream(stream)), "fmmfft_disaggregate")
+
+
+def fmmfft_translate_disaggregate(plan, S_in, patterns, y, nb, nrhs, stream=None):
+    """Eq. 5 then Eq. 6 on the device, the translated fields kept on chip:
+    y[r][i][v] = sum_p w_p sum_c conj(P[p][c][i][v]) B[p][c][r][v] with
+    B the translation of S_in."""
+    p, o, b = _far_field(plan, patterns, y, S_in, int(nb), int(nrhs), "fmmfft_translate_disaggregate",
+                         ("patterns", "y", "S_in"))
+    _check(lib().fmmfft_translate_disaggregate(plan, b, p, o, int(nb), int(nrhs), _stream(stream)),
+           "fmmfft_translate_disaggregate")
+
+
+def fmmfft_plan_set_occupancy(plan, occupied=None):
+    """Box occupancy mask (Kz, Ky, Kx) of the plan's grid, nonzero = occupied
+    (Sec. II.A: empty boxes carry no sources and receive nothing), or None to
+    clear it."""
+    if occupied is None:
+        _check(lib().fmmfft_plan_set_occupancy(plan, None), "fmmfft_plan_set_occupancy")
+        return
+    st = fmmfft_plan_stats(plan)
+    Kx, Ky, Kz = st["K"]
+    m = np.ascontiguousarray(np.asarray(occupied) != 0, dtype=np.uint8)
+    if m.size != Kx * Ky * Kz:
+        raise FmmfftError(FMMFFT_ERR_INVALID_ARG,
+                          f"fmmfft_plan_set_occupancy: mask of {m.size} boxes for a grid of {Kx * Ky * Kz}")
+    _check(lib().fmmfft_plan_set_occupancy(plan, m.ctypes.data_as(ctypes.c_void_p)), "fmmfft_plan_set_occupancy")
 
 
 def fmmfft_translate_noalloc(plan, S_in, S_out, nrhs, stream=None):

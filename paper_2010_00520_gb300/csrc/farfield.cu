@@ -209,6 +209,180 @@ __global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kDisBoxes)
   cluster.sync();
 }
 
+// ---------------------------------------------------------------------------
+// Inverse x pass fused with the disaggregation: the translated fields B of
+// Eq. 5 leave the last inverse DFT in shared memory and go straight into the
+// sum of Eq. 6, so they are never written to (or read back from) HBM.
+//
+// A block owns a tile of TR whole (y, z) rows (TR Kx <= 128 boxes), kXdRT
+// right-hand sides and kXdNB basis functions, and one of the kDisSplit
+// quarters of the directions (the quarters of a tile are the CTAs of one
+// cluster and add their partial sums through distributed shared memory in a
+// fixed order, as the separate disaggregation does).  For each direction p of
+// its quarter, in order: the x-spectra of its 2 x kXdRT x TR lines are loaded
+// (for each x, the TR rows are contiguous), inverse-transformed along x
+// (first Kx outputs kept), and every thread adds w_p conj(P) B for its box
+// and its 8 basis functions over both polarisations.  Threads 0..127 take
+// basis functions 0..7 of the chunk, threads 128..255 functions 8..15, each
+// for the box t % 128 of the tile.
+// ---------------------------------------------------------------------------
+constexpr int kXdRT = 2;           // right-hand sides per block
+constexpr int kXdNB = 16;          // basis functions per block
+constexpr int kXdIT = 8;           // basis functions per thread
+constexpr int kXdBoxes = 128;      // boxes per tile (at most)
+
+template <typename R, int N1>
+__global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kThreads)
+    xinv_disagg_kernel(const cx<R>* __restrict__ inter, const cx<R>* __restrict__ P,
+                       const double* __restrict__ w, cx<R>* __restrict__ y, const cx<R>* __restrict__ twg,
+                       const unsigned char* __restrict__ occ, const unsigned char* __restrict__ rowocc,
+                       int Kx, int rows, int TR, int nb, int nrhs, int n_dir) {
+  using C = cx<R>;
+  using L = Line<N1>;
+  constexpr int PX = N1 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* xs = tw + N1;
+  C* Q = xs + kWarps * L::XW;                    // lines x PX
+  C* part = Q;                                   // reused for the partial sums at the end
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = (int)cluster.block_rank();
+  const int tile = blockIdx.x / kDisSplit;
+  const int r0 = tile * TR;
+  const int nrow = min(TR, rows - r0);
+  const int rh0 = blockIdx.y * kXdRT;
+  const int nr = min(kXdRT, nrhs - rh0);
+  const int i0 = blockIdx.z * kXdNB;
+  const int t = threadIdx.x;
+  const int b = t % kXdBoxes, g = t / kXdBoxes;
+  const int brow = b / Kx, bx = b - brow * Kx;
+  // an empty box (occupancy mask) receives nothing: its B is zero, so are
+  // its outputs
+  const bool inb = brow < nrow;
+  const bool live = inb && (!occ || occ[(int64_t)(r0 + brow) * Kx + bx]);
+  const int64_t V = (int64_t)rows * Kx;
+  const int64_t v = (int64_t)(r0 + brow) * Kx + bx;
+  const int ia = i0 + g * kXdIT;
+  const int ni = max(0, min(kXdIT, nb - ia));
+  const int lines = 2 * kXdRT * TR;
+  const int per = (n_dir + kDisSplit - 1) / kDisSplit;
+  const int pa = s * per, pb = min(n_dir, pa + per);
+  for (int i = t; i < N1; i += kThreads) tw[i] = twg[i];
+  TeamPos<N1> tp;
+  C* xt = tp.xs(xs);
+  C acc[kXdIT][kXdRT];
+#pragma unroll
+  for (int i = 0; i < kXdIT; ++i)
+#pragma unroll
+    for (int r = 0; r < kXdRT; ++r) acc[i][r] = czero<C>();
+  for (int p = pa; p < pb; ++p) {
+    // patterns of this direction, issued before the transform so that their
+    // latency overlaps it
+    C pv[2][kXdIT];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int i = 0; i < kXdIT; ++i)
+        pv[c][i] = (live && i < ni) ? P[((int64_t)(p * 2 + c) * nb + ia + i) * V + v] : czero<C>();
+    __syncthreads();                             // previous direction done with Q
+    // line l = (c kXdRT + rr) TR + row holds field ((p 2 + c) nrhs + rh0 + rr), row r0 + row
+    for (int e = t; e < lines * N1; e += kThreads) {
+      const int row = e % TR, rest = e / TR;
+      const int x = rest % N1, cr = rest / N1;
+      const int c = cr / kXdRT, rr = cr % kXdRT;
+      C val = czero<C>();
+      if (rr < nr && row < nrow && (!rowocc || rowocc[r0 + row])) {
+        const int64_t f = ((int64_t)(p * 2 + c) * nrhs + rh0 + rr);
+        val = inter[(f * N1 + x) * rows + r0 + row];
+      }
+      Q[(cr * TR + row) * PX + x] = val;
+    }
+    __syncthreads();
+    for (int base = 0; base < lines; base += L::LPI) {
+      const int ln = base + tp.line;
+      const bool act = ln < lines;
+      line_fft<N1, +1, false>(Q + (act ? ln : 0) * PX, 1, xt, tw, tp.t, act, Kx);
+    }
+    __syncthreads();
+    const R wp = (R)w[p];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      C bv[kXdRT];
+#pragma unroll
+      for (int rr = 0; rr < kXdRT; ++rr)
+        bv[rr] = live ? Q[((c * kXdRT + rr) * TR + brow) * PX + bx] : czero<C>();
+#pragma unroll
+      for (int i = 0; i < kXdIT; ++i) {
+        const C q = mk<C>(wp * pv[c][i].x, -wp * pv[c][i].y);    // w_p conj(P)
+#pragma unroll
+        for (int rr = 0; rr < kXdRT; ++rr) cfma(acc[i][rr], q, bv[rr]);
+      }
+    }
+  }
+  __syncthreads();                               // Q no longer read
+#pragma unroll
+  for (int i = 0; i < kXdIT; ++i)
+#pragma unroll
+    for (int rr = 0; rr < kXdRT; ++rr) part[(i * kXdRT + rr) * kThreads + t] = acc[i][rr];
+  cluster.sync();
+  // CTA s finishes the outputs k = s, s + kDisSplit, ... in CTA order
+  if (inb) {
+    for (int k = s; k < kXdIT * kXdRT; k += kDisSplit) {
+      const int i = k / kXdRT, rr = k % kXdRT;
+      if (i >= ni || rr >= nr) continue;
+      C sum = czero<C>();
+#pragma unroll
+      for (int q = 0; q < kDisSplit; ++q) {
+        const C* rp = cluster.map_shared_rank(&part[k * kThreads + t], q);
+        sum = cadd(sum, *rp);
+      }
+      y[((int64_t)(rh0 + rr) * nb + ia + i) * V + v] = sum;
+    }
+  }
+  cluster.sync();
+}
+
+// Tile rows and shared memory of the fused kernel.
+template <typename R, int N1>
+size_t xinv_disagg_smem(int TR) {
+  const size_t q = (size_t)2 * kXdRT * TR * (N1 + 1);
+  const size_t part = (size_t)kXdIT * kXdRT * kThreads;
+  return sizeof(cx<R>) * (N1 + kWarps * Line<N1>::XW + (q > part ? q : part));
+}
+
+template <typename R, int N1>
+cudaError_t xinv_disagg_t(const XDisArgs& a) {
+  if (a.Kx > kXdBoxes || a.Kx < 1) return cudaErrorInvalidValue;
+  const int TR = kXdBoxes / a.Kx;
+  const int tiles = (a.rows + TR - 1) / TR;
+  const int rchunks = (a.nrhs + kXdRT - 1) / kXdRT;
+  const int nchunks = (a.nb + kXdNB - 1) / kXdNB;
+  if ((int64_t)tiles * kDisSplit > 0x7fffffff || rchunks > 65535 || nchunks > 65535) return cudaErrorInvalidValue;
+  const size_t smem = xinv_disagg_smem<R, N1>(TR);
+  static std::atomic<int> optin[kMaxDevices];
+  auto kern = xinv_disagg_kernel<R, N1>;
+  cudaError_t e = smem_optin((const void*)kern, optin);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((unsigned)(tiles * kDisSplit), rchunks, nchunks), kThreads, smem, a.stream>>>(
+      (const cx<R>*)a.inter, (const cx<R>*)a.P, a.w, (cx<R>*)a.y, (const cx<R>*)a.tw, a.occ, a.rowocc, a.Kx,
+      a.rows, TR, a.nb, a.nrhs, a.n_dir);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t xinv_disagg_any(const XDisArgs& a) {
+  switch (a.n1) {
+    case 4: return xinv_disagg_t<R, 4>(a);
+    case 8: return xinv_disagg_t<R, 8>(a);
+    case 16: return xinv_disagg_t<R, 16>(a);
+    case 32: return xinv_disagg_t<R, 32>(a);
+    case 64: return xinv_disagg_t<R, 64>(a);
+    case 128: return xinv_disagg_t<R, 128>(a);
+    case 256: return xinv_disagg_t<R, 256>(a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R>
 cudaError_t aggregate_t(const FarFieldArgs& a) {
   constexpr int RT = FarTile<R>::RT;
@@ -260,6 +434,11 @@ cudaError_t launch_aggregate(const FarFieldArgs& a) {
 cudaError_t launch_disaggregate(const FarFieldArgs& a) {
   if (a.V == 0) return cudaSuccess;
   return a.fp64 ? disaggregate_t<double>(a) : disaggregate_t<float>(a);
+}
+
+cudaError_t launch_xinv_disaggregate(const XDisArgs& a) {
+  if (a.rows == 0 || a.Kx == 0) return cudaSuccess;
+  return a.fp64 ? xinv_disagg_any<double>(a) : xinv_disagg_any<float>(a);
 }
 
 }  // namespace fmm

@@ -289,7 +289,10 @@ __device__ __forceinline__ void line_fft(C* ln, int es, C* xs, const C* tw, int 
 
 // Forward transform of a half-filled line, Hadamard product with op[k * op_es]
 // (k < N), inverse transform; outputs with index < keep (<= N) written back.
-template <int N, typename C>
+// OP_EARLY: the lane's operator values are loaded before the forward
+// transform, so that their latency overlaps it (op in global memory; it costs
+// 2 R2 registers across the transform); otherwise when they are used.
+template <int N, bool OP_EARLY = false, typename C>
 __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, const C* op, int op_es,
                                           int t, bool active, int keep) {
   using L = Line<N>;
@@ -297,6 +300,13 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
   constexpr int A = R2 / T;          // forward stage-1 DFTs per lane
   constexpr int B2 = R2 / T;         // inverse stage-2 DFTs per lane
   constexpr int NZ1 = R1 / 2;
+  C opv[OP_EARLY ? R2 : 1];
+  if constexpr (OP_EARLY) {
+    if (active) {
+#pragma unroll
+      for (int d = 0; d < R2; ++d) opv[d] = op[(t + R1 * d) * op_es];
+    }
+  }
   // forward stage 1
   if (active) {
 #pragma unroll
@@ -324,7 +334,10 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
     // forward stage 2: v[d] = X[t + R1 d]
     dft<R2, R2, -1>(v);
 #pragma unroll
-    for (int d = 0; d < R2; ++d) v[d] = cmul(v[d], op[(t + R1 * d) * op_es]);
+    for (int d = 0; d < R2; ++d) {
+      if constexpr (OP_EARLY) v[d] = cmul(v[d], opv[d]);
+      else v[d] = cmul(v[d], op[(t + R1 * d) * op_es]);
+    }
     // inverse stage 1 of the swapped shape (R1' = R2, R2' = R1): a' = t,
     // inputs x[t + R1 b'] = v[b'] for b' < R2
     dft<R2, R2, +1>(v);

@@ -40,6 +40,7 @@ struct fmmfft_plan_s {
   // device state
   void* d_tw[3] = {nullptr, nullptr, nullptr};
   void* d_op = nullptr;         // format NONE: T~_p / (n1 n2 n3), [p][x][z][y]
+                                //   ([p][x][y][z] for the large-plane yz kernel)
   void* d_pack = nullptr;       // compressed formats: stored factors
   void* d_scratch = nullptr;    // compressed formats: restore pre-pass outputs
   fmm::SlabDesc* d_slab = nullptr;
@@ -53,6 +54,8 @@ struct fmmfft_plan_s {
   int large_grid = 0;           // blocks of the persistent large-plane kernel
   void* d_inter = nullptr;
   void* d_weights = nullptr;   // quadrature weights on the device (far-field steps)
+  void* d_occ = nullptr;       // box occupancy (V bytes) then x-line occupancy (Ky Kz bytes)
+  bool occ_set = false;        // a mask is in force (d_occ stays allocated once made)
   size_t inter_bytes = 0;
   void* d_io = nullptr;       // device copies for fmmfft_translate_host
   size_t io_bytes = 0;
@@ -225,6 +228,10 @@ fmm::TranslateArgs base_args(const fmmfft_plan_s* p) {
   a.p0 = 0;
   a.nw = 0;
   a.prepass = true;
+  if (p->occ_set && p->d_occ) {
+    a.occ = (const unsigned char*)p->d_occ;
+    a.rowocc = a.occ + (size_t)p->K[0] * p->K[1] * p->K[2];
+  }
   return a;
 }
 
@@ -255,19 +262,25 @@ int ensure_slabs(fmmfft_plan_s* p) {
   return FMMFFT_OK;
 }
 
-// Plain store: T~_p scaled by 1/(n1 n2 n3), [p][x][z][y].  `That` is indexed
-// ((p n1 + x) n2 + y) n3 + z.
+// Plain store: T~_p scaled by 1/(n1 n2 n3), [p][x][z][y] for the fused yz
+// kernel (rows copied into its shared-memory slab) or [p][x][y][z] for the
+// large-plane one (read column by column from global memory).  `That` is
+// indexed ((p n1 + x) n2 + y) n3 + z.
 int upload_plain(fmmfft_plan_s* p, const std::function<const cdouble*(int)>& slab_of) {
   const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
   const size_t per = (size_t)n1 * n2 * n3;
   const double sc = 1.0 / (double)per;
+  const bool by_column = base_args(p).large != 0;
   std::vector<cdouble> h(per * p->n_dir);
   fmm::parallel_for(p->n_dir, [&](int d) {
     const cdouble* T = slab_of(d);
     cdouble* o = &h[per * d];
     for (int x = 0; x < n1; ++x)
       for (int y = 0; y < n2; ++y)
-        for (int z = 0; z < n3; ++z) o[((size_t)x * n3 + z) * n2 + y] = T[((size_t)x * n2 + y) * n3 + z] * sc;
+        for (int z = 0; z < n3; ++z) {
+          const size_t to = by_column ? ((size_t)x * n2 + y) * n3 + z : ((size_t)x * n3 + z) * n2 + y;
+          o[to] = T[((size_t)x * n2 + y) * n3 + z] * sc;
+        }
   });
   free_dev(p->d_op);
   int st = upload_complex(&p->d_op, h, p->precision == FMMFFT_PREC_C128);
@@ -399,22 +412,40 @@ void build_layout(const fmmfft_plan_s* p, fmm::Layout& L) {
     fmm::layout_tt3d(tt, p->n, L);
     return;
   }
-  std::vector<std::vector<cdouble>> Tp(nd);
-  fmm::parallel_for(nd, [&](int d) { fmm::fft_operator(s, &p->khat[3 * d], Tp[d]); });
+  // 4D formats decompose T_4D over the whole direction grid (Sec. II.B: the
+  // directions are the fourth mode).  A shard plan keeps the shared cores and
+  // only its block's rows of the direction factor (U4, or U3 of TT), so every
+  // shard restores its directions from one global decomposition, exactly as
+  // the whole plan does.
+  const bool shard = nd != p->n_dir_grid;
+  std::vector<double> kh_all = p->khat, w_all;
+  if (shard) fmm::direction_grid(p->L, p->nphi_rule == 0 ? 2 * (p->L + 1) : 2 * p->L + 1, kh_all, w_all);
+  const int nd_all = shard ? p->n_dir_grid : nd;
+  std::vector<std::vector<cdouble>> Tp(nd_all);
+  fmm::parallel_for(nd_all, [&](int d) { fmm::fft_operator(s, &kh_all[3 * d], Tp[d]); });
+  // rows dir_first .. dir_first + nd - 1 of a direction factor with r columns
+  auto rows_of_block = [&](std::vector<cdouble>& U, int r) {
+    if (!shard) return;
+    std::vector<cdouble> sub(U.begin() + (size_t)p->dir_first * r, U.begin() + (size_t)(p->dir_first + nd) * r);
+    U.swap(sub);
+  };
   if (p->decomp == FMMFFT_DECOMP_TUCKER) {
     double n2 = 0.0;
     for (auto& T : Tp)
       for (auto& z : T) n2 += std::norm(z);
     fmm::Tucker4 tk;
     fmm::hosvd4(Tp, p->n, fmm::step_budget(std::sqrt(n2), p->tol, 4.0, p->trunc_rule), p->trunc_rule, tk);
+    rows_of_block(tk.U[3], tk.r[3]);
     fmm::layout_tucker4d(tk, p->n, nd, L);
   } else if (p->decomp == FMMFFT_DECOMP_HTUCKER) {
     fmm::HTucker4 ht;
     fmm::htucker4(Tp, p->n, p->tol, p->trunc_rule, ht);
+    rows_of_block(ht.U[3], ht.r[3]);
     fmm::layout_htucker(ht, p->n, nd, L);
   } else {
     fmm::TT4 tt;
     fmm::tt4_via_tucker(Tp, p->n, p->tol, p->trunc_rule, tt);
+    rows_of_block(tt.U3, tt.r[2]);
     fmm::layout_tt4d(tt, p->n, nd, L);
   }
 }
@@ -1110,6 +1141,85 @@ int fmmfft_disaggregate(fmmfft_plan p, const void* patterns, const void* B, void
   return FMMFFT_OK;
 }
 
+int fmmfft_translate_disaggregate(fmmfft_plan p, const void* S_in, const void* patterns, void* y, int nb, int nrhs,
+                                  void* stream) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  if (!p->ready) return FMMFFT_ERR_NOT_COMPRESSED;
+  fmm::FarFieldArgs fa;
+  // the fields S_in play the role of the far-field input for the aliasing
+  // and alignment checks: y must overlap neither them nor the patterns
+  int st = farfield_args(p, patterns, S_in, y, nb, nrhs, stream, (size_t)p->n_dir * 2 * (nrhs > 0 ? nrhs : 0),
+                         (size_t)nb * (nrhs > 0 ? nrhs : 0), fa);
+  if (st != FMMFFT_OK) return st;
+  if (p->K[0] > 128) return FMMFFT_ERR_UNSUPPORTED;
+  void* inter = nullptr;
+  size_t ib = 0;
+  if ((st = fmm::plan_intermediate(p, nrhs, stream, &inter, &ib)) != FMMFFT_OK) return st;
+  fmm::XDisArgs d;
+  d.P = patterns;
+  d.w = fa.w;
+  d.y = y;
+  d.nb = nb;
+  fmm::TranslateArgs a = base_args(p);
+  a.nrhs = nrhs;
+  a.s_in = S_in;
+  a.s_out = nullptr;
+  a.inter = inter;
+  a.stream = (cudaStream_t)stream;
+  a.dis = &d;
+  p->last_stream = a.stream;
+  if (p->profile) {
+    if (!p->events[0])
+      for (auto& ev : p->events)
+        if (cudaEventCreate(&ev) != cudaSuccess) return FMMFFT_ERR_CUDA;
+    a.events = p->events;
+    p->profiled_run = true;
+  }
+  cudaError_t e = fmm::launch_translate(a);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  return FMMFFT_OK;
+}
+
+int fmmfft_plan_set_occupancy(fmmfft_plan p, const unsigned char* occupied) {
+  if (!p) return FMMFFT_ERR_INVALID_ARG;
+  const size_t V = (size_t)p->K[0] * p->K[1] * p->K[2];
+  const size_t rows = (size_t)p->K[1] * p->K[2];
+  // box mask, then per x-line: whether any box of the line is occupied; a
+  // cleared mask is stored as a full one so that a launch captured earlier
+  // keeps valid memory
+  std::vector<unsigned char> h(V + rows, 1);
+  if (occupied) {
+    for (size_t r = 0; r < rows; ++r) {
+      unsigned char any = 0;
+      for (int x = 0; x < p->K[0]; ++x) {
+        const unsigned char o = occupied[r * p->K[0] + x] ? 1 : 0;
+        h[r * p->K[0] + x] = o;
+        any |= o;
+      }
+      h[V + r] = any;
+    }
+  }
+  // the plan's work in flight may read the previous mask
+  if (p->d_occ && cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  if (!p->d_occ) {
+    if (!occupied) return FMMFFT_OK;
+    int st = dev_alloc(&p->d_occ, V + rows);
+    if (st != FMMFFT_OK) return st;
+  }
+  if (cudaMemcpy(p->d_occ, h.data(), V + rows, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  p->occ_set = occupied != nullptr;
+  return FMMFFT_OK;
+}
+
 int fmmfft_multipole_count(double a, double k0, double eps_re, double eps_im, double digits, int* L_out) {
   if (!L_out || !(a > 0) || !(k0 > 0) || !(eps_re > 0) || !(eps_im <= 0) || !(digits > 0) ||
       !std::isfinite(a * k0 * eps_re * eps_im * digits))
@@ -1552,6 +1662,7 @@ int fmmfft_plan_destroy(fmmfft_plan p) {
   free_dev(p->d_inter);
   free_dev(p->d_io);
   free_dev(p->d_weights);
+  free_dev(p->d_occ);
   for (auto& ev : p->events)
     if (ev) cudaEventDestroy(ev);
   if (p->side) {

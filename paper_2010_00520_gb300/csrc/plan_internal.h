@@ -68,6 +68,8 @@ struct GemmStage {
 
 constexpr int kMaxGemmStages = 4;
 
+struct XDisArgs;
+
 // Arguments of one translation, prepared by the host for the launchers.
 struct TranslateArgs {
   int K[3];           // Kx, Ky, Kz
@@ -106,6 +108,15 @@ struct TranslateArgs {
                                      // lines one block iteration covers (1, 2, 4)
   int no_overlap;                    // 1: pre-pass in line with the x pass
   int tc_gemm;                       // pre-pass products on the tensor cores: 1 3xTF32, 2 BF16x3
+  // box occupancy (Sec. II.A: empty boxes carry no sources and no testing
+  // functions), device bytes, or null for a full grid: occ[v] per box
+  // (v = (z Ky + y) Kx + x), rowocc[z Ky + y] per x-line (any box occupied)
+  const unsigned char* occ = nullptr;
+  const unsigned char* rowocc = nullptr;
+  // when set, the inverse x pass is replaced by the fused inverse x pass +
+  // disaggregation (Eq. 6) with these patterns / weights / output; s_out is
+  // then not written.  Whole-plan launches only (p0 = 0, nw = 0).
+  const XDisArgs* dis = nullptr;
   // direction block of this launch: directions p0 .. p0 + nw - 1 (nw = 0: all),
   // fields and intermediate addressed at their place in the full arrays; the
   // restore pre-pass runs only when `prepass` is set (it covers every direction)
@@ -166,6 +177,25 @@ struct FarFieldArgs {
   cudaStream_t stream = nullptr;
 };
 constexpr int kFarFieldMaxNb = 48;   // basis functions per box
+
+// The inverse x pass fused with the disaggregation (Eq. 5's last DFT, then
+// Eq. 6): reads the translated x-spectra `inter` ([F][n1][Ky Kz], F =
+// n_dir 2 nrhs fields in the translation's order) and the patterns P, writes
+// y = [nrhs][nb][V]; the translated fields themselves are never stored.
+struct XDisArgs {
+  const void* inter = nullptr;
+  const void* P = nullptr;
+  const double* w = nullptr;       // n_dir quadrature weights (device)
+  void* y = nullptr;
+  const void* tw = nullptr;        // W_n1^m, m < n1
+  const unsigned char* occ = nullptr;      // box occupancy or null (TranslateArgs)
+  const unsigned char* rowocc = nullptr;
+  int n1 = 0, Kx = 0, rows = 0;    // rows = Ky Kz
+  int nb = 0, nrhs = 0, n_dir = 0;
+  bool fp64 = false;
+  cudaStream_t stream = nullptr;
+};
+cudaError_t launch_xinv_disaggregate(const XDisArgs& a);
 size_t aggregate_smem_bytes(int nb, bool fp64);
 cudaError_t launch_aggregate(const FarFieldArgs& a);
 cudaError_t launch_disaggregate(const FarFieldArgs& a);

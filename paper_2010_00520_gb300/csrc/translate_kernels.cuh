@@ -44,6 +44,11 @@ struct XPassParams {
   const void* tw;    // W_n1^m table
   int Kx, rows;      // rows = Ky * Kz per field
   int rows_per_block;
+  // box occupancy or null: empty boxes are read as zero (xfwd) and written as
+  // zero (xinv); x-lines with no occupied box are neither read nor
+  // transformed (xfwd writes their zero spectra, xinv their zero outputs)
+  const unsigned char* occ;
+  const unsigned char* rowocc;
 };
 
 struct YZParams {
@@ -104,7 +109,8 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
     for (int j = 0; j < kLd; ++j) {
       const int i = i0 + j * kThreads;
       const int r = i / half, x = i - r * half;
-      v[j] = (i < nr * half && x < P.Kx) ? src[(size_t)r * P.Kx + x] : czero<C>();
+      const bool occupied = !P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x];
+      v[j] = (i < nr * half && x < P.Kx && occupied) ? src[(size_t)r * P.Kx + x] : czero<C>();
     }
 #pragma unroll
     for (int j = 0; j < kLd; ++j) {
@@ -118,14 +124,16 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
   C* xt = tp.xs(xs);
   for (int base = 0; base < nr; base += L::LPI) {
     const int line = base + tp.line;
-    const bool act = line < nr;
-    line_fft<N1, -1, true>(Q + (act ? line : 0) * PX, 1, xt, tw, tp.t, act, N1);
+    const bool act = line < nr && (!P.rowocc || P.rowocc[r0 + line]);
+    line_fft<N1, -1, true>(Q + (line < nr ? line : 0) * PX, 1, xt, tw, tp.t, act, N1);
   }
   __syncthreads();
-  // I[f][x][r]: rows contiguous for fixed x
+  // I[f][x][r]: rows contiguous for fixed x; a line with no occupied box has
+  // a zero spectrum
   for (int i = threadIdx.x; i < N1 * nr; i += kThreads) {
     const int x = i / nr, r = i - x * nr;
-    dst[((size_t)f * N1 + x) * P.rows + r0 + r] = Q[r * PX + x];
+    const bool live = !P.rowocc || P.rowocc[r0 + r];
+    dst[((size_t)f * N1 + x) * P.rows + r0 + r] = live ? Q[r * PX + x] : czero<C>();
   }
 }
 
@@ -147,20 +155,22 @@ __global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P) {
   for (int i = threadIdx.x; i < N1; i += kThreads) tw[i] = reinterpret_cast<const C*>(P.tw)[i];
   for (int i = threadIdx.x; i < N1 * nr; i += kThreads) {
     const int x = i / nr, r = i - x * nr;
-    Q[r * PX + x] = src[((size_t)f * N1 + x) * P.rows + r0 + r];
+    const bool live = !P.rowocc || P.rowocc[r0 + r];
+    Q[r * PX + x] = live ? src[((size_t)f * N1 + x) * P.rows + r0 + r] : czero<C>();
   }
   __syncthreads();
   TeamPos<N1> tp;
   C* xt = tp.xs(xs);
   for (int base = 0; base < nr; base += L::LPI) {
     const int line = base + tp.line;
-    const bool act = line < nr;
-    line_fft<N1, +1, false>(Q + (act ? line : 0) * PX, 1, xt, tw, tp.t, act, P.Kx);
+    const bool act = line < nr && (!P.rowocc || P.rowocc[r0 + line]);
+    line_fft<N1, +1, false>(Q + (line < nr ? line : 0) * PX, 1, xt, tw, tp.t, act, P.Kx);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nr * P.Kx; i += kThreads) {
     const int r = i / P.Kx, x = i - r * P.Kx;
-    dst[(size_t)r * P.Kx + x] = Q[r * PX + x];
+    const bool occupied = !P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x];
+    dst[(size_t)r * P.Kx + x] = occupied ? Q[r * PX + x] : czero<C>();
   }
 }
 
@@ -236,16 +246,17 @@ __global__ void __launch_bounds__(kThreads) cgemm_batched_kernel(const GemmDesc*
 // The per-field work of a yz block (x, p), G fields per round: forward y DFT
 // of rows z < Kz, z DFT x Hadamard with the slab x inverse z DFT of every
 // column, inverse y DFT, corner written back in place.  `op` is the slab
-// T~_p[x] as [z][y] with row pitch `op_pitch` (shared or global memory);
-// `planes` holds G planes of N3 / 2 rows of pitch N2 + 1 (a forward z line
-// reads only its first half, an inverse one writes only rows z < Kz <= N3/2).
-// The G fields of a round share the phase barriers; each phase runs the
-// unchanged line loop once per field.
+// T~_p[x]: element (z, y) at op[y * op_cs + z * op_es] (shared memory [z][y]
+// with an odd row pitch, or global memory [y][z] so that a team's z-line
+// reads are contiguous); `planes` holds G planes of N3 / 2 rows of pitch
+// N2 + 1 (a forward z line reads only its first half, an inverse one writes
+// only rows z < Kz <= N3/2).  The G fields of a round share the phase
+// barriers; each phase runs the unchanged line loop once per field.
 // ---------------------------------------------------------------------------
-template <typename R, int N2, int N3, int G>
+template <typename R, int N2, int N3, int G, bool OP_GLOBAL>
 __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>* planes, cx<R>* xs,
                                           const cx<R>* tw2, const cx<R>* tw3, const cx<R>* op,
-                                          int op_pitch) {
+                                          int op_cs, int op_es) {
   using C = cx<R>;
   constexpr int PY = N2 + 1;
   constexpr int PS = (N3 / 2) * PY;          // plane stride
@@ -302,6 +313,25 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
           }
       }
       if (j0 + G < P.nf) prefetch(j0 + G);
+    } else if constexpr (OP_GLOBAL) {
+      // batches of kLd loads per thread in flight before their stores
+      constexpr int kLd = 8;
+      for (int g = 0; g < ng; ++g)
+        for (int i0 = tid; i0 < Kz * hy; i0 += kLd * kThreads) {
+          C v[kLd];
+#pragma unroll
+          for (int j = 0; j < kLd; ++j) {
+            const int i = i0 + j * kThreads;
+            const int z = i / hy, y = i - z * hy;
+            v[j] = (i < Kz * hy && y < Ky) ? io[g * fstride + z * Ky + y] : czero<C>();
+          }
+#pragma unroll
+          for (int j = 0; j < kLd; ++j) {
+            const int i = i0 + j * kThreads;
+            const int z = i / hy, y = i - z * hy;
+            if (i < Kz * hy) planes[g * PS + z * PY + y] = v[j];
+          }
+        }
     } else {
       for (int g = 0; g < ng; ++g)
         for (int i = tid; i < Kz * hy; i += kThreads) {
@@ -327,7 +357,7 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
         const int col = base + tz.line;
         const bool act = col < N2;
         const int cc = act ? col : 0;
-        line_conv<N3>(plane + cc, PY, xz, tw3, op + cc, op_pitch, tz.t, act, Kz);
+        line_conv<N3, OP_GLOBAL>(plane + cc, PY, xz, tw3, op + (size_t)cc * op_cs, op_es, tz.t, act, Kz);
       }
     }
     __syncthreads();
@@ -596,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
       }
     }
   }
-  yz_fields<R, N2, N3, LY::G>(P, x, p, plane, xs, tw2, tw3, Tt, PY);
+  yz_fields<R, N2, N3, LY::G, false>(P, x, p, plane, xs, tw2, tw3, Tt, 1, PY);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,10 +634,12 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
 // the shared memory (n2 x n3 = 128 x 128, 256 x 64, 256 x 128).  Persistent
 // blocks walk the (x, p) items; the slab T~_p[x] stays in global memory: the
 // plain operator in place, a restored slab in the block's own scratch slot,
-// which stays resident in L2 while the block's fields use it.  Shared memory
-// holds the twiddles, half a field plane and the exchange buffers; the
-// restore's staging (tensor-core operand chunks) reuses the plane.  Two FP32
-// blocks share an SM (the launch bound caps their registers at 128).
+// which stays resident in L2 while the block's fields use it.  Both are
+// stored column by column ([y][z], z fastest), so that the eight lanes of a
+// z-line team read consecutive elements.  Shared memory holds the twiddles,
+// half a field plane and the exchange buffers; the restore's staging
+// (tensor-core operand chunks) reuses the plane.  Two FP32 blocks share an
+// SM (the launch bound caps their registers at 128).
 // ---------------------------------------------------------------------------
 template <typename R, int N2, int N3>
 struct YZLLayout {
@@ -621,7 +653,7 @@ struct YZLLayout {
   }
   // global scratch per block: the slab, then G (rb x N2) of the Tucker-like
   // restore
-  static long long slot_elems(int fmt, int rb) {
+  static long long slot_elems(int fmt, int rb) {   // slab [y][z], then G
     return fmt == 0 ? 0 : (long long)N3 * N2 + (fmt == 1 ? (long long)rb * N2 : 0);
   }
 };
@@ -653,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
   const int items = P.n1 * P.n_dir;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int x = it % P.n1, p = P.p0 + it / P.n1;
-    const C* op;
+    const C* op;   // [y][z]
     if constexpr (FMT == 0) {
       op = reinterpret_cast<const C*>(P.op) + ((size_t)p * P.n1 + x) * (N3 * N2);
     } else {
@@ -674,20 +706,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
         const float2* U3f = reinterpret_cast<const float2*>(U3);
         float2* Gf = reinterpret_cast<float2*>(G);
         float2* Sf = reinterpret_cast<float2*>(slot);
+        // slab[y][z] tiles of 64 x 64
         if constexpr (FMT == 1) {
           for (int y0 = 0; y0 < N2; y0 += 64)
             tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
                        [&](int b, int y) { return U2f[(y0 + y) * ra + b]; }, Gf + y0, N2, 1.0f);
-          for (int z0 = 0; z0 < N3; z0 += 64)
-            for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int z, int c) { return U3f[(z0 + z) * rb + c]; },
-                         [&](int c, int y) { return Gf[c * N2 + y0 + y]; }, Sf + (size_t)z0 * N2 + y0, N2,
+          for (int y0 = 0; y0 < N2; y0 += 64)
+            for (int z0 = 0; z0 < N3; z0 += 64)
+              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int y, int c) { return Gf[c * N2 + y0 + y]; },
+                         [&](int c, int z) { return U3f[(z0 + z) * rb + c]; }, Sf + (size_t)y0 * N3 + z0, N3,
                          (float)P.scale);
         } else {
-          for (int z0 = 0; z0 < N3; z0 += 64)
-            for (int y0 = 0; y0 < N2; y0 += 64)
-              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int z, int b) { return U3f[(z0 + z) * rb + b]; },
-                         [&](int b, int y) { return Hf[(y0 + y) * rb + b]; }, Sf + (size_t)z0 * N2 + y0, N2,
+          for (int y0 = 0; y0 < N2; y0 += 64)
+            for (int z0 = 0; z0 < N3; z0 += 64)
+              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int y, int b) { return Hf[(y0 + y) * rb + b]; },
+                         [&](int b, int z) { return U3f[(z0 + z) * rb + b]; }, Sf + (size_t)y0 * N3 + z0, N3,
                          (float)P.scale);
         }
       } else {
@@ -695,15 +728,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
           // G[c][y] = sum_b H[x][b][c] U2[y][b]
           block_cgemm_strided(rb, N2, ra, H, 1, rb, U2, 1, ra, G, N2, (R)1);
           __syncthreads();
-          block_cgemm_strided(N3, N2, rb, U3, rb, 1, G, N2, 1, slot, N2, (R)P.scale);
+          // slab[y][z] = scale sum_c G[c][y] U3[z][c]
+          block_cgemm_strided(N2, N3, rb, G, 1, N2, U3, 1, rb, slot, N3, (R)P.scale);
         } else {
-          block_cgemm_strided(N3, N2, rb, U3, rb, 1, H, 1, rb, slot, N2, (R)P.scale);
+          // slab[y][z] = scale sum_b T1[x][y][b] R_p[z][b]
+          block_cgemm_strided(N2, N3, rb, H, rb, 1, U3, 1, rb, slot, N3, (R)P.scale);
         }
       }
       __syncthreads();
       op = slot;
     }
-    yz_fields<R, N2, N3, 1>(P, x, p, plane, xs, tw2, tw3, op, N2);
+    yz_fields<R, N2, N3, 1, true>(P, x, p, plane, xs, tw2, tw3, op, N3, 1);
   }
   if constexpr (TC != 0) {
     if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);

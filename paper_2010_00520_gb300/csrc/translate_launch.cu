@@ -249,6 +249,8 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   X.Kx = a.K[0];
   X.rows = rows;
   X.rows_per_block = a.xrows;   // multiplier in, rows per block chosen per launch
+  X.occ = a.occ;
+  X.rowocc = a.rowocc;
   if ((e = launch_x<R>(true, a.n[0], X, F, a.stream)) != cudaSuccess) return e;
   if (overlap && (e = cudaStreamWaitEvent(a.stream, a.join, 0)) != cudaSuccess) return e;
   mark(2);
@@ -280,6 +282,24 @@ static cudaError_t launch_all(const TranslateArgs& a) {
   if ((e = launch_yz(a, Y, grid, smem)) != cudaSuccess) return e;
   mark(3);
 
+  if (a.dis) {
+    if (a.p0 != 0 || nw != a.n_dir) return cudaErrorInvalidValue;
+    XDisArgs d = *a.dis;
+    d.inter = a.inter;
+    d.tw = a.tw[0];
+    d.occ = a.occ;
+    d.rowocc = a.rowocc;
+    d.n1 = a.n[0];
+    d.Kx = a.K[0];
+    d.rows = rows;
+    d.nrhs = a.nrhs;
+    d.n_dir = a.n_dir;
+    d.fp64 = sizeof(R) == 8;
+    d.stream = a.stream;
+    e = launch_xinv_disaggregate(d);
+    mark(4);
+    return e;
+  }
   X.src = (const char*)a.inter + f0 * a.n[0] * rows * es;
   X.dst = (char*)a.s_out + f0 * a.K[0] * rows * es;
   e = launch_x<R>(false, a.n[0], X, F, a.stream);

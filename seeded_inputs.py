@@ -150,6 +150,19 @@ def field_spectra_torch(seed: int, n_dir: int, nrhs: int, K: tuple[int, int, int
     return out
 
 
+def shell_occupancy(K: tuple[int, int, int], thickness: float = 1.0) -> np.ndarray:
+    """Box occupancy of a surface mesh of the sphere inscribed in the box
+    grid: a (Kz, Ky, Kx) boolean array, True where a box centre lies within
+    `thickness` box edges of the sphere.  Stands in for the shell of boxes a
+    meshed sphere occupies (its interior boxes are empty)."""
+    Kx, Ky, Kz = K
+    z, y, x = np.meshgrid(np.arange(Kz), np.arange(Ky), np.arange(Kx), indexing="ij")
+    c = [(k - 1) / 2.0 for k in (Kx, Ky, Kz)]
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    R = min(Kx, Ky, Kz) / 2.0 - 0.5
+    return np.abs(r - R) <= thickness
+
+
 # Workloads (box grids, multipole counts, formats) of the synthetic benchmark
 # suite.  All use box edge a = 0.5 wavelengths with wavelength 1 (k0 = 2 pi),
 # the Chebyshev near rule max|d_i| <= 1 and N_phi = 2(L+1).

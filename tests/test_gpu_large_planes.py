@@ -5,7 +5,8 @@ scratch slot.  Reduced x extent and few directions keep the oracle fast.
 
 Same operator / factors on both sides: rel L2 <= 2e-6 (complex64, FP32
 restores), <= 5e-6 (3xTF32 tensor-core restores and pre-pass products, see
-test_gpu_formats.py), <= 1e-10 (complex128)."""
+test_gpu_formats.py), <= 4e-5 (BF16x3, the 64^3-box workload's restore
+arithmetic: about 2^-16 per product), <= 1e-10 (complex128)."""
 import numpy as np
 import pytest
 
@@ -52,7 +53,8 @@ def test_large_plane_plain(native, cuda, K, L, nrhs, c128):
 
 @pytest.mark.parametrize("K,L,nrhs", SHAPES)
 @pytest.mark.parametrize("fmt,dec,prec", [("3d", "tucker", 1), ("3d", "tucker", 2), ("4d", "tt", 2),
-                                          ("4d", "htucker", 2), ("3d", "tt", 1)])
+                                          ("4d", "htucker", 2), ("3d", "tt", 1), ("3d", "tucker", 3),
+                                          ("4d", "tt", 3), ("4d", "htucker", 3)])
 def test_large_plane_compressed(native, cuda, K, L, nrhs, fmt, dec, prec):
     F, torch = native, cuda
     plan = pl.Plan(K=K, L=L)
@@ -78,6 +80,7 @@ def test_large_plane_compressed(native, cuda, K, L, nrhs, fmt, dec, prec):
             F.fmmfft_import_htucker(h, np.array(P.ranks, dtype=np.int32), *P.U, P.C12, P.C34, P.B)
         S = field_spectra(93 + DEC, plan.n_dir, nrhs, K)
         out = _run(F, torch, h, S, nrhs)
-        assert _rel(out, pl.translate_with(comp.restore, S)) <= (5e-6 if prec == 2 else 2e-6)
+        bound = {1: 2e-6, 2: 5e-6, 3: 4e-5}[prec]
+        assert _rel(out, pl.translate_with(comp.restore, S)) <= bound
     finally:
         F.fmmfft_plan_destroy(h)

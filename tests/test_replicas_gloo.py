@@ -71,9 +71,11 @@ def test_direction_blocks_partition_the_grid():
         direction_block(3, 4, 0)
 
 
-def _shard_worker(rank, world, port, out):
-    """Each rank compresses only its block of directions (host FP64 set-up,
-    Tucker-3D) with a shard plan; rank 0 gathers the restored operators."""
+def _shard_worker(rank, world, port, out, fmt=3, dec=1):
+    """Each rank compresses its block of directions (host FP64 set-up) with a
+    shard plan; rank 0 gathers the restored operators.  3D formats decompose
+    each direction on its own; 4D formats decompose the whole grid's T_4D and
+    keep the block's rows of the direction factor."""
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
                       LOCAL_RANK=str(rank))
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -84,7 +86,7 @@ def _shard_worker(rank, world, port, out):
         K, L = (6, 5, 7), 3
         n_dir = 2 * (L + 1) ** 2
         first, count = direction_block(n_dir, world, rank)
-        h = F.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 3, 1, 1e-4)
+        h = F.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, fmt, dec, 1e-4)
         try:
             F.fmmfft_plan_set(h, F.FMMFFT_KEY_DIR_FIRST, first)
             F.fmmfft_plan_set(h, F.FMMFFT_KEY_DIR_COUNT, count)
@@ -100,20 +102,29 @@ def _shard_worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_direction_shards_on_gloo_ranks_equal_the_whole_plan():
+@pytest.mark.parametrize("fmt,dec", [(3, 1), (4, 1), (4, 3), (4, 2)])
+def test_direction_shards_on_gloo_ranks_equal_the_whole_plan(fmt, dec):
+    """The shards' restored operators, concatenated in rank order, equal the
+    whole plan's bit for bit (Sec. II.C: directions are restored
+    independently; for the 4D formats from one global decomposition, so the
+    result does not depend on the number of ranks)."""
     import numpy as np
     import paper_2010_00520_gb300 as F
     world = 2
     with mp.Manager() as m:
         out = m.dict()
-        mp.spawn(_shard_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        mp.spawn(_shard_worker, args=(world, _free_port(), out, fmt, dec), nprocs=world, join=True)
         parts = out["parts"]
     K, L = (6, 5, 7), 3
-    h = F.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, 3, 1, 1e-4)
+    h = F.fmmfft_plan_create(*K, 0.5, 2 * np.pi, L, fmt, dec, 1e-4)
     try:
         ranks, restored = F.fmmfft_compress_host(h)
     finally:
         F.fmmfft_plan_destroy(h)
     parts = sorted(parts, key=lambda t: t[0])
-    assert np.array_equal(np.concatenate([p[1] for p in parts]), ranks)
+    if fmt == 3:
+        assert np.array_equal(np.concatenate([p[1] for p in parts]), ranks)
+    else:
+        for p in parts:
+            assert np.array_equal(p[1], ranks)           # the global ranks on every shard
     assert np.array_equal(np.concatenate([p[2] for p in parts]), restored)
