@@ -438,6 +438,102 @@ def tensor_peak_tflops(peaks: dict, restore: str) -> tuple:
     return bf16 * 1.1 / 2.25, f"measured bf16 burst {bf16:.0f} TFLOP/s x nominal TF32/BF16 1.1/2.25"
 
 
+# The batched workload: 64 independent FMM-FFT instances of uneven box grids
+# (K_i drawn uniformly from 16..32 per axis, so FFT extents 32 or 64), L drawn
+# from 4..10, Tucker-3D per direction at tol 1e-4 with 3xTF32 restores, 2
+# polarisations x 8 RHS each, seeded fields per instance.
+BATCH_WL = "batch64_tucker3d_K16-32_L4-10_tol1e-4_2pol_8rhs"
+BATCH = dict(instances=64, K=(16, 32), L=(4, 10), tol=1e-4, nrhs=8, seed=1004)
+
+
+def batch_specs():
+    import numpy as np
+    rng = np.random.default_rng(BATCH["seed"])
+    out = []
+    for i in range(BATCH["instances"]):
+        K = tuple(int(k) for k in rng.integers(BATCH["K"][0], BATCH["K"][1] + 1, size=3))
+        L = int(rng.integers(BATCH["L"][0], BATCH["L"][1] + 1))
+        out.append((K, L, BATCH["seed"] * 1000 + i))
+    return out
+
+
+def run_batch(args):
+    """One step = one fmmfft_batch_translate over all instances (graph
+    replay after the first calls); the same batch with one launch sequence
+    per instance (FMMFFT_BATCH_SEPARATE=1) is timed beside it."""
+    import torch
+
+    import paper_2010_00520_gb300 as F
+    from seeded_inputs import field_spectra_torch
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(F.LIB_PATH):
+        from paper_2010_00520_gb300 import build as _b
+        _b.build()
+    specs = batch_specs()
+    plans, xs, ys, nr, units = [], [], [], [], 0
+    t0 = time.perf_counter()
+    for (K, L, seed) in specs:
+        h = F.fmmfft_plan_create(*K, 0.5, 2 * math.pi, L, 3, 1, BATCH["tol"])
+        F.fmmfft_plan_set(h, F.FMMFFT_KEY_PRECISION, F.FMMFFT_PREC_C64_3XTF32)
+        F.fmmfft_compress(h)
+        st = F.fmmfft_plan_stats(h)
+        plans.append(h)
+        xs.append(field_spectra_torch(seed, st["n_dir"], BATCH["nrhs"], K, device="cuda"))
+        ys.append(torch.empty_like(xs[-1]))
+        nr.append(BATCH["nrhs"])
+        units += _units(st["n"], st["n_dir"], BATCH["nrhs"])
+    t_setup = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    io_bytes = sum(2 * x.numel() * x.element_size() for x in xs)
+
+    def timed(separate):
+        os.environ["FMMFFT_BATCH_SEPARATE"] = "1" if separate else "0"
+        b = F.fmmfft_batch_create(plans)
+        try:
+            for _ in range(max(args.warmup, 3)):
+                F.fmmfft_batch_translate(b, xs, ys, nr, stream)
+            stream.synchronize()
+            shared = F.fmmfft_batch_shared_count(b)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            ev[0].record(stream)
+            for i in range(args.steps):
+                F.fmmfft_batch_translate(b, xs, ys, nr, stream)
+                ev[i + 1].record(stream)
+            stream.synchronize()
+            for h in plans:
+                assert F.fmmfft_poll_status(h) == 0
+            per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+            return ev[0].elapsed_time(ev[-1]) / args.steps, per, shared
+        finally:
+            F.fmmfft_batch_destroy(b)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, per, shared = timed(False)
+    clk = clocks.stop()
+    ms_sep, _, _ = timed(True)
+    os.environ.pop("FMMFFT_BATCH_SEPARATE", None)
+    ns = [F.fmmfft_plan_stats(h)["n"] for h in plans]
+    out = {"metric": METRIC, "value": units / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
+           "config": {"workload": BATCH_WL, "instances": len(plans),
+                      "K_range": list(BATCH["K"]), "L_range": list(BATCH["L"]), "nrhs": BATCH["nrhs"],
+                      "format": "tucker3d", "tol": BATCH["tol"],
+                      "precision": "FP32 FFTs, 3xTF32 restores on the tensor cores",
+                      "fft_extents": sorted({tuple(n) for n in ns}),
+                      "fields_bytes": io_bytes, "setup_s": round(t_setup, 1),
+                      "l2": "inputs and outputs larger than the 129 MB L2; no flush"},
+           "per_step_ms": {"median": statistics.median(per), "min": min(per), "max": max(per)},
+           "shared_launch_instances": shared,
+           "separate_launches": {"ms_per_step": ms_sep, "value": units / (ms_sep * 1e-3) / 1e9},
+           "clocks": clk}
+    for h in plans:
+        F.fmmfft_plan_destroy(h)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,7 +557,7 @@ def main():
                     help="skip timing the translation on a shell occupancy mask (Sec. II.A)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default schedule instead of autotuning each arm before timing")
-    ap.add_argument("--workload", default=DEFAULT_WL, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WL, choices=sorted(WORKLOADS) + [BATCH_WL])
     ap.add_argument("--cpu-baseline-child", default="")
     ap.add_argument("--cpu-baseline-out", default="")
     ap.add_argument("--reference-child", nargs=3, default=None)
@@ -473,9 +569,15 @@ def main():
         reference_child(args.reference_child[0], int(args.reference_child[1]), int(args.reference_child[2]))
         return
     if args.impl == "reference":
+        if args.workload == BATCH_WL:
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle arm"}))
+            return
         run_reference(args)
         return
     args.warmup = max(args.warmup, 3)
+    if args.workload == BATCH_WL:
+        run_batch(args)
+        return
 
     import numpy as np
     import torch

@@ -480,9 +480,23 @@ int fmmfft_multipole_count(double a, double k0, double eps_re, double eps_im, do
  * they must outlive the batch and be compressed before the first translate).
  * fmmfft_batch_translate: translates instance i from S_in[i] to S_out[i]
  * with nrhs[i] RHS (device pointers and layouts as fmmfft_translate), all
- * asynchronous on `stream`: the instances are forked over up to four internal
- * streams so that small ones run side by side, and joined back into `stream`.
- * A call with the same pointers and RHS counts as the previous call is
+ * asynchronous on `stream`.  The complex64 instances whose y-z planes fit
+ * the fused yz kernel (any format and restore arithmetic) run together: they
+ * are grouped into shape classes and every phase runs one persistent launch
+ * per class for all its instances -- the merged restore pre-pass (one launch
+ * per stage), the forward x pass (per x extent), the yz pass (per plane
+ * shape, operator kind and restore arithmetic) and the inverse x pass --
+ * each a grid of the SMs' resident blocks walking the work items of every
+ * instance of the class, with the same device code as a single translation,
+ * so results equal each instance's fmmfft_translate bit for bit.  Any other
+ * instance (complex128, or planes of the large-plane kernel) runs its own
+ * launches on one of up to four internal streams.  The environment variable
+ * FMMFFT_BATCH_SEPARATE=1 at fmmfft_batch_create gives every instance its
+ * own launches.  A device failure inside the shared launches (status word) is
+ * reported on the plan whose item raised it, or for the merged pre-pass on
+ * the batch's first plan.  When the batch's arguments change, the first call
+ * waits for `stream` and uploads the new work descriptors (a few KB).  A
+ * call with the same pointers and RHS counts as the previous call is
  * captured as one CUDA graph on its first repetition and replayed from then
  * on (never for the legacy default stream, NULL).  Each plan's intermediate
  * is allocated, if needed, before anything is launched.
@@ -497,6 +511,9 @@ int fmmfft_batch_create(fmmfft_batch* out, const fmmfft_plan* plans, int nplans)
 int fmmfft_batch_translate(fmmfft_batch batch, const void* const* S_in, void* const* S_out,
                            const int* nrhs, void* stream);
 int fmmfft_batch_destroy(fmmfft_batch batch);
+/* Number of instances that ran in the shared (persistent) launches of the
+ * batch's last fmmfft_batch_translate call (the others ran on their own). */
+int fmmfft_batch_shared_count(fmmfft_batch batch, int* count);
 
 /*
  * Autotuner (no counterpart in the paper): times the plan's candidate

@@ -71,6 +71,7 @@ EXPORTED = (
     "fmmfft_batch_create", "fmmfft_batch_translate", "fmmfft_batch_destroy", "fmmfft_plan_save",
     "fmmfft_plan_load", "fmmfft_autotune", "fmmfft_batch_autotune", "fmmfft_multipole_count",
     "fmmfft_aggregate", "fmmfft_disaggregate", "fmmfft_translate_disaggregate", "fmmfft_plan_set_occupancy",
+    "fmmfft_batch_shared_count",
 )
 
 
@@ -142,6 +143,7 @@ def lib() -> ctypes.CDLL:
         "fmmfft_disaggregate": [vp, vp, vp, vp, i, i, vp],
         "fmmfft_translate_disaggregate": [vp, vp, vp, vp, i, i, vp],
         "fmmfft_plan_set_occupancy": [vp, vp],
+        "fmmfft_batch_shared_count": [vp, ip],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -465,6 +467,14 @@ def fmmfft_translate_disaggregate(plan, S_in, patterns, y, nb, nrhs, stream=None
                          ("patterns", "y", "S_in"))
     _check(lib().fmmfft_translate_disaggregate(plan, b, p, o, int(nb), int(nrhs), _stream(stream)),
            "fmmfft_translate_disaggregate")
+
+
+def fmmfft_batch_shared_count(batch) -> int:
+    """Instances of the last batch call that ran in the shared (persistent)
+    launches."""
+    n = ctypes.c_int()
+    _check(lib().fmmfft_batch_shared_count(batch, ctypes.byref(n)), "fmmfft_batch_shared_count")
+    return n.value
 
 
 def fmmfft_plan_set_occupancy(plan, occupied=None):

@@ -1,8 +1,11 @@
 // Batched translation of several independent plans (uneven grids, ranks and
-// RHS counts): one call launches every instance, forked over a few streams so
-// that small instances run side by side, and repeated calls with the same
-// buffers replay one captured CUDA graph.
+// RHS counts).  The instances that the persistent batch kernels cover
+// (batch_persistent_ok) run together, one launch per phase for all of them
+// (batch_kernels.cu); any other instance runs its own launch sequence on one
+// of a few side streams.  Repeated calls with the same buffers replay one
+// captured CUDA graph.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -22,6 +25,9 @@ struct fmmfft_batch_s {
   int key_seen = 0;                     // consecutive calls with this key
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  fmm::BatchDev dev;                    // descriptors of the persistent launches
+  int persistent = 1;                   // 0: every instance on its own launches
+  int shared_last = 0;                  // instances in the shared launches of the last call
 };
 
 namespace {
@@ -35,14 +41,34 @@ void drop_graph(fmmfft_batch_s* b) {
   b->graph = nullptr;
 }
 
-// Fork from `stream`, launch every instance on a side stream, join back.
+// Fork from `stream`: the persistent launches of the instances they cover on
+// `stream`, every other instance on a side stream; join back.
 int launch_all(fmmfft_batch_s* b, const void* const* in, void* const* out, const int* nrhs,
                const std::vector<void*>& inter, const std::vector<size_t>& cap, cudaStream_t stream) {
   if (cudaEventRecord(b->forked, stream) != cudaSuccess) return FMMFFT_ERR_CUDA;
   for (auto s : b->side)
     if (cudaStreamWaitEvent(s, b->forked, 0) != cudaSuccess) return FMMFFT_ERR_CUDA;
+  std::vector<fmm::TranslateArgs> together;
+  std::vector<size_t> alone;
   for (size_t i = 0; i < b->plans.size(); ++i) {
-    const int st = fmm::translate_into(b->plans[i], in[i], out[i], nrhs[i], b->side[i % b->side.size()],
+    fmm::TranslateArgs a;
+    const int st = fmm::translate_args_for(b->plans[i], in[i], out[i], nrhs[i], inter[i], cap[i], &a);
+    if (st != FMMFFT_OK) return st;
+    if (b->persistent && fmm::batch_persistent_ok(a)) {
+      a.stream = stream;
+      together.push_back(a);
+    } else {
+      alone.push_back(i);
+    }
+  }
+  b->shared_last = (int)together.size();
+  if (!together.empty() && fmm::launch_translate_batch(together, b->dev, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FMMFFT_ERR_CUDA;
+  }
+  for (size_t k = 0; k < alone.size(); ++k) {
+    const size_t i = alone[k];
+    const int st = fmm::translate_into(b->plans[i], in[i], out[i], nrhs[i], b->side[k % b->side.size()],
                                        inter[i], cap[i]);
     if (st != FMMFFT_OK) return st;
   }
@@ -65,6 +91,8 @@ int fmmfft_batch_create(fmmfft_batch* out, const fmmfft_plan* plans, int nplans)
   fmmfft_batch_s* b = new (std::nothrow) fmmfft_batch_s();
   if (!b) return FMMFFT_ERR_OOM;
   b->plans.assign(plans, plans + nplans);
+  const char* sep = std::getenv("FMMFFT_BATCH_SEPARATE");
+  b->persistent = (sep && *sep && std::strcmp(sep, "0") != 0) ? 0 : 1;
   const int ns = nplans < kSideStreams ? nplans : kSideStreams;
   b->side.assign(ns, nullptr);
   b->joined.assign(ns, nullptr);
@@ -151,6 +179,12 @@ int fmmfft_batch_autotune(fmmfft_batch b, const int* nrhs, double budget_ms) {
   return FMMFFT_OK;
 }
 
+int fmmfft_batch_shared_count(fmmfft_batch b, int* count) {
+  if (!b || !count) return FMMFFT_ERR_INVALID_ARG;
+  *count = b->shared_last;
+  return FMMFFT_OK;
+}
+
 int fmmfft_batch_destroy(fmmfft_batch b) {
   if (!b) return FMMFFT_ERR_INVALID_ARG;
   for (auto s : b->side)
@@ -161,6 +195,7 @@ int fmmfft_batch_destroy(fmmfft_batch b) {
   for (auto e : b->joined)
     if (e) cudaEventDestroy(e);
   if (b->forked) cudaEventDestroy(b->forked);
+  fmm::batch_dev_release(b->dev);
   delete b;
   return FMMFFT_OK;
 }

@@ -243,14 +243,19 @@ __global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* xs = tw + N1;
-  C* Q = xs + kWarps * L::XW;                    // lines x PX
-  C* part = Q;                                   // reused for the partial sums at the end
+  C* Q0 = xs + kWarps * L::XW;                   // two buffers of lines x PX (directions alternate)
+  C* part = Q0;                                  // reused for the partial sums at the end
   cg::cluster_group cluster = cg::this_cluster();
   const int s = (int)cluster.block_rank();
-  const int tile = blockIdx.x / kDisSplit;
+  // blockIdx.x = (tile * rchunks + RHS chunk) * kDisSplit + quarter: the
+  // blocks of one tile's RHS chunks are neighbours, so the patterns they all
+  // read come from HBM once and from L2 after that
+  const int rchunks = (nrhs + kXdRT - 1) / kXdRT;
+  const int unit = blockIdx.x / kDisSplit;
+  const int tile = unit / rchunks;
   const int r0 = tile * TR;
   const int nrow = min(TR, rows - r0);
-  const int rh0 = blockIdx.y * kXdRT;
+  const int rh0 = (unit - tile * rchunks) * kXdRT;
   const int nr = min(kXdRT, nrhs - rh0);
   const int i0 = blockIdx.z * kXdNB;
   const int t = threadIdx.x;
@@ -275,7 +280,33 @@ __global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kThreads)
   for (int i = 0; i < kXdIT; ++i)
 #pragma unroll
     for (int r = 0; r < kXdRT; ++r) acc[i][r] = czero<C>();
+  // line l = (c kXdRT + rr) TR + row of direction q's buffer holds field
+  // ((q 2 + c) nrhs + rh0 + rr), row r0 + row: copied asynchronously
+  // (cp.async), so that direction q + 1's lines arrive while q is
+  // transformed and summed; lines of absent fields or empty rows are zeroed
+  const int qbuf = lines * PX;
+  auto issue = [&](int q, C* Qb) {
+    for (int e = t; e < lines * N1; e += kThreads) {
+      const int row = e % TR, rest = e / TR;
+      const int x = rest % N1, cr = rest / N1;
+      const int c = cr / kXdRT, rr = cr % kXdRT;
+      C* dst = Qb + (cr * TR + row) * PX + x;
+      if (rr < nr && row < nrow && (!rowocc || rowocc[r0 + row])) {
+        const int64_t f = ((int64_t)(q * 2 + c) * nrhs + rh0 + rr);
+        const C* src = inter + (f * N1 + x) * rows + r0 + row;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(src),
+                     "n"((int)sizeof(C))
+                     : "memory");
+      } else {
+        *dst = czero<C>();
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (pa < pb) issue(pa, Q0);
   for (int p = pa; p < pb; ++p) {
+    C* Q = Q0 + ((p - pa) & 1) * qbuf;
     // patterns of this direction, issued before the transform so that their
     // latency overlaps it
     C pv[2][kXdIT];
@@ -284,20 +315,12 @@ __global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kThreads)
 #pragma unroll
       for (int i = 0; i < kXdIT; ++i)
         pv[c][i] = (live && i < ni) ? P[((int64_t)(p * 2 + c) * nb + ia + i) * V + v] : czero<C>();
-    __syncthreads();                             // previous direction done with Q
-    // line l = (c kXdRT + rr) TR + row holds field ((p 2 + c) nrhs + rh0 + rr), row r0 + row
-    for (int e = t; e < lines * N1; e += kThreads) {
-      const int row = e % TR, rest = e / TR;
-      const int x = rest % N1, cr = rest / N1;
-      const int c = cr / kXdRT, rr = cr % kXdRT;
-      C val = czero<C>();
-      if (rr < nr && row < nrow && (!rowocc || rowocc[r0 + row])) {
-        const int64_t f = ((int64_t)(p * 2 + c) * nrhs + rh0 + rr);
-        val = inter[(f * N1 + x) * rows + r0 + row];
-      }
-      Q[(cr * TR + row) * PX + x] = val;
-    }
+    // this direction's lines have landed (own copies), then everyone's
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
+    // the other buffer was last read in the previous iteration, before the
+    // barrier above
+    if (p + 1 < pb) issue(p + 1, Q0 + ((p + 1 - pa) & 1) * qbuf);
     for (int base = 0; base < lines; base += L::LPI) {
       const int ln = base + tp.line;
       const bool act = ln < lines;
@@ -345,7 +368,7 @@ __global__ void __cluster_dims__(kDisSplit, 1, 1) __launch_bounds__(kThreads)
 // Tile rows and shared memory of the fused kernel.
 template <typename R, int N1>
 size_t xinv_disagg_smem(int TR) {
-  const size_t q = (size_t)2 * kXdRT * TR * (N1 + 1);
+  const size_t q = (size_t)2 * 2 * kXdRT * TR * (N1 + 1);     // two line buffers
   const size_t part = (size_t)kXdIT * kXdRT * kThreads;
   return sizeof(cx<R>) * (N1 + kWarps * Line<N1>::XW + (q > part ? q : part));
 }
@@ -357,13 +380,13 @@ cudaError_t xinv_disagg_t(const XDisArgs& a) {
   const int tiles = (a.rows + TR - 1) / TR;
   const int rchunks = (a.nrhs + kXdRT - 1) / kXdRT;
   const int nchunks = (a.nb + kXdNB - 1) / kXdNB;
-  if ((int64_t)tiles * kDisSplit > 0x7fffffff || rchunks > 65535 || nchunks > 65535) return cudaErrorInvalidValue;
+  if ((int64_t)tiles * rchunks * kDisSplit > 0x7fffffff || nchunks > 65535) return cudaErrorInvalidValue;
   const size_t smem = xinv_disagg_smem<R, N1>(TR);
   static std::atomic<int> optin[kMaxDevices];
   auto kern = xinv_disagg_kernel<R, N1>;
   cudaError_t e = smem_optin((const void*)kern, optin);
   if (e != cudaSuccess) return e;
-  kern<<<dim3((unsigned)(tiles * kDisSplit), rchunks, nchunks), kThreads, smem, a.stream>>>(
+  kern<<<dim3((unsigned)((int64_t)tiles * rchunks * kDisSplit), 1, nchunks), kThreads, smem, a.stream>>>(
       (const cx<R>*)a.inter, (const cx<R>*)a.P, a.w, (cx<R>*)a.y, (const cx<R>*)a.tw, a.occ, a.rowocc, a.Kx,
       a.rows, TR, a.nb, a.nrhs, a.n_dir);
   return cudaGetLastError();

@@ -251,11 +251,12 @@ template <int N> struct TeamPos {
 // Every lane of the warp must call this (active = false lanes only sync).
 template <int N, int S, bool IN_HALF, typename C>
 __device__ __forceinline__ void line_fft(C* ln, int es, C* xs, const C* tw, int t, bool active,
-                                         int keep) {
+                                         int keep, const C* wpre = nullptr) {
   using L = Line<N>;
   constexpr int R1 = L::R1, R2 = L::R2, T = L::T;
   constexpr int A = R2 / T;
   constexpr int NZ1 = IN_HALF ? R1 / 2 : R1;
+  constexpr bool kSquare = R1 == R2 && A == 1;   // wpre: as in line_conv
   if (active) {
 #pragma unroll
     for (int i = 0; i < A; ++i) {
@@ -265,7 +266,12 @@ __device__ __forceinline__ void line_fft(C* ln, int es, C* xs, const C* tw, int 
       for (int b = 0; b < NZ1; ++b) v[b] = ln[(a + R2 * b) * es];
       dft<R1, NZ1, S>(v);
       C w[R1];
-      twiddle_powers<R1>(tw[a], w);
+      if (kSquare && wpre) {
+#pragma unroll
+        for (int c = 0; c < R1; ++c) w[c] = wpre[c];
+      } else {
+        twiddle_powers<R1>(tw[a], w);
+      }
       xs[a] = v[0];
 #pragma unroll
       for (int c = 1; c < R1; ++c) xs[c * (R2 + 1) + a] = twmul<S>(v[c], w[c]);
@@ -292,14 +298,18 @@ __device__ __forceinline__ void line_fft(C* ln, int es, C* xs, const C* tw, int 
 // OP_EARLY: the lane's operator values are loaded before the forward
 // transform, so that their latency overlaps it (op in global memory; it costs
 // 2 R2 registers across the transform); otherwise when they are used.
+// wpre: for square shapes (R1 = R2, one stage-1 DFT per lane) the lane's
+// twiddles W^(t c), c < R1, computed once by the caller (line_twiddles) and
+// shared by the forward and the inverse stage 1; null: computed here.
 template <int N, bool OP_EARLY = false, typename C>
 __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, const C* op, int op_es,
-                                          int t, bool active, int keep) {
+                                          int t, bool active, int keep, const C* wpre = nullptr) {
   using L = Line<N>;
   constexpr int R1 = L::R1, R2 = L::R2, T = L::T;
   constexpr int A = R2 / T;          // forward stage-1 DFTs per lane
   constexpr int B2 = R2 / T;         // inverse stage-2 DFTs per lane
   constexpr int NZ1 = R1 / 2;
+  constexpr bool kSquare = R1 == R2 && A == 1;
   C opv[OP_EARLY ? R2 : 1];
   if constexpr (OP_EARLY) {
     if (active) {
@@ -317,7 +327,12 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
       for (int b = 0; b < NZ1; ++b) v[b] = ln[(a + R2 * b) * es];
       dft<R1, NZ1, -1>(v);
       C w[R1];
-      twiddle_powers<R1>(tw[a], w);
+      if (kSquare && wpre) {
+#pragma unroll
+        for (int c = 0; c < R1; ++c) w[c] = wpre[c];
+      } else {
+        twiddle_powers<R1>(tw[a], w);
+      }
       xs[a] = v[0];
 #pragma unroll
       for (int c = 1; c < R1; ++c) xs[c * (R2 + 1) + a] = twmul<-1>(v[c], w[c]);
@@ -343,7 +358,12 @@ __device__ __forceinline__ void line_conv(C* ln, int es, C* xs, const C* tw, con
     dft<R2, R2, +1>(v);
     {
       C w[R2];
-      twiddle_powers<R2>(tw[t], w);
+      if (kSquare && wpre) {
+#pragma unroll
+        for (int c = 0; c < R2; ++c) w[c] = wpre[c];
+      } else {
+        twiddle_powers<R2>(tw[t], w);
+      }
       xs[t] = v[0];
 #pragma unroll
       for (int c = 1; c < R2; ++c) xs[c * (R1 + 1) + t] = twmul<+1>(v[c], w[c]);

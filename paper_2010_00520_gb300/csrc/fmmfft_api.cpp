@@ -871,6 +871,29 @@ void plan_set_last_stream(fmmfft_plan p, void* stream) {
   if (p) p->last_stream = (cudaStream_t)stream;
 }
 
+int translate_args_for(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* scratch, size_t scratch_bytes,
+                       TranslateArgs* out) {
+  size_t need = 0;
+  int st = translate_scratch_bytes(p, nrhs, &need);
+  if (st != FMMFFT_OK) return st;
+  if (!S_in || !S_out || !scratch || !out) return FMMFFT_ERR_INVALID_ARG;
+  const size_t es = elem_bytes(p);
+  const size_t bytes = (size_t)p->n_dir * 2 * nrhs * p->K[0] * p->K[1] * p->K[2] * es;
+  const char* i0 = (const char*)S_in;
+  const char* o0 = (const char*)S_out;
+  if (i0 < o0 + bytes && o0 < i0 + bytes) return FMMFFT_ERR_INVALID_ARG;
+  if (((uintptr_t)S_in | (uintptr_t)S_out | (uintptr_t)scratch) % es) return FMMFFT_ERR_INVALID_ARG;
+  if (need > scratch_bytes) return FMMFFT_ERR_TOO_LARGE;
+  fmm::TranslateArgs a = base_args(p);
+  a.nrhs = nrhs;
+  a.s_in = S_in;
+  a.s_out = S_out;
+  a.inter = scratch;
+  a.events = nullptr;
+  *out = a;
+  return FMMFFT_OK;
+}
+
 int translate_into(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* stream,
                    void* scratch, size_t scratch_bytes) {
   size_t need = 0;

@@ -161,6 +161,32 @@ int plan_intermediate(fmmfft_plan p, int nrhs, void* stream, void** inter, size_
 // Stream that fmmfft_poll_status synchronises for this plan.
 void plan_set_last_stream(fmmfft_plan p, void* stream);
 
+// Arguments of one translation of plan p (the checks of fmmfft_translate,
+// with `scratch` as the intermediate), without launching anything
+// (fmmfft_api.cpp).
+int translate_args_for(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* scratch, size_t scratch_bytes,
+                       TranslateArgs* out);
+
+// Persistent launches of a batch (batch_launch.cu).  BatchDev: the batch's
+// device descriptor buffer and the host copy of what it holds.
+struct BatchDev {
+  void* d_desc = nullptr;
+  size_t bytes = 0;
+  std::vector<unsigned char> host;
+  std::vector<const void*> gemm_src;
+};
+// Whether a translation can join the batch's persistent launches: complex64,
+// y-z planes of the fused yz kernel (not the large-plane one), whole-plan
+// launch.
+bool batch_persistent_ok(const TranslateArgs& a);
+// All translations of `args` grouped into shape classes, one persistent
+// launch per phase and class (merged restore pre-pass, x forward per x
+// extent, yz per plane shape / operator kind / restore arithmetic, x
+// inverse), on stream s.  Uploads the descriptors to dev when they changed,
+// after synchronising s.
+cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, BatchDev& dev, cudaStream_t s);
+void batch_dev_release(BatchDev& dev);
+
 // Aggregation (Eq. 4) and disaggregation (Eq. 6), farfield.cu.  P: patterns
 // [n_dir][2][nb][V]; aggregation reads `in` = coefficients [nrhs][nb][V] and
 // writes `out` = spectra [n_dir][2][nrhs][V]; disaggregation reads `in` =

@@ -68,6 +68,31 @@ struct YZParams {
   long long slot_elems;
 };
 
+// Persistent batch mode of the x and yz kernels (batch_launch.cu): the
+// launch walks the work items of several instances of one shape class,
+// items item0 .. next item0 - 1 belonging to the instance; a block copies
+// the instance's parameters to shared memory and runs the same per-item code
+// as a single translation.
+struct BatchX {
+  XPassParams P;
+  long long item0;
+};
+struct BatchYZ {
+  YZParams P;
+  long long item0;
+};
+
+template <typename D>
+__device__ __forceinline__ int find_instance(const D* inst, int ninst, long long item) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].item0 <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Plans whose restore can run on the tensor cores (3xTF32 or BF16x3):
 // complex64, planes of 32 or 64 per side or multiples of 64, and (checked on
 // the host) for the Tucker-like format at most 64 columns of H_p[x].
@@ -83,18 +108,19 @@ struct TcRestore {
 // ---------------------------------------------------------------------------
 // x passes
 // ---------------------------------------------------------------------------
+// Work item `item` (field item / row blocks, row block item % row blocks) of
+// the forward x pass, by the whole block; `smem_raw` holds xpass_smem bytes.
 template <typename R, int N1>
-__global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
+__device__ __forceinline__ void xfwd_body(const XPassParams& P, int item, unsigned char* smem_raw) {
   using C = cx<R>;
   using L = Line<N1>;
   constexpr int PX = N1 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* xs = tw + N1;
   C* Q = xs + kWarps * L::XW;
   const int nrb = (P.rows + P.rows_per_block - 1) / P.rows_per_block;
-  const int f = blockIdx.x / nrb;
-  const int r0 = (blockIdx.x - f * nrb) * P.rows_per_block;
+  const int f = item / nrb;
+  const int r0 = (item - f * nrb) * P.rows_per_block;
   const int nr = min(P.rows_per_block, P.rows - r0);
   const C* src = reinterpret_cast<const C*>(P.src) + ((size_t)f * P.rows + r0) * P.Kx;
   C* dst = reinterpret_cast<C*>(P.dst);
@@ -109,8 +135,8 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
     for (int j = 0; j < kLd; ++j) {
       const int i = i0 + j * kThreads;
       const int r = i / half, x = i - r * half;
-      const bool occupied = !P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x];
-      v[j] = (i < nr * half && x < P.Kx && occupied) ? src[(size_t)r * P.Kx + x] : czero<C>();
+      const bool in = i < nr * half && x < P.Kx;
+      v[j] = (in && (!P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x])) ? src[(size_t)r * P.Kx + x] : czero<C>();
     }
 #pragma unroll
     for (int j = 0; j < kLd; ++j) {
@@ -137,18 +163,35 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
   }
 }
 
+// One item per block, or (inst != null) the persistent batch mode.
 template <typename R, int N1>
-__global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P) {
+__global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P, const BatchX* __restrict__ inst, int ninst,
+                                                        long long total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (!inst) {
+    xfwd_body<R, N1>(P, blockIdx.x, smem_raw);
+    return;
+  }
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = find_instance(inst, ninst, item);
+    const XPassParams Pi = inst[i].P;
+    __syncthreads();                                 // the previous item is done with shared memory
+    xfwd_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
+  }
+}
+
+// Work item `item` of the inverse x pass (as xfwd_body).
+template <typename R, int N1>
+__device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsigned char* smem_raw) {
   using C = cx<R>;
   using L = Line<N1>;
   constexpr int PX = N1 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* xs = tw + N1;
   C* Q = xs + kWarps * L::XW;
   const int nrb = (P.rows + P.rows_per_block - 1) / P.rows_per_block;
-  const int f = blockIdx.x / nrb;
-  const int r0 = (blockIdx.x - f * nrb) * P.rows_per_block;
+  const int f = item / nrb;
+  const int r0 = (item - f * nrb) * P.rows_per_block;
   const int nr = min(P.rows_per_block, P.rows - r0);
   const C* src = reinterpret_cast<const C*>(P.src);
   C* dst = reinterpret_cast<C*>(P.dst) + ((size_t)f * P.rows + r0) * P.Kx;
@@ -174,10 +217,36 @@ __global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P) {
   }
 }
 
+template <typename R, int N1>
+__global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P, const BatchX* __restrict__ inst, int ninst,
+                                                        long long total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (!inst) {
+    xinv_body<R, N1>(P, blockIdx.x, smem_raw);
+    return;
+  }
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = find_instance(inst, ninst, item);
+    const XPassParams Pi = inst[i].P;
+    __syncthreads();                                 // the previous item is done with shared memory
+    xinv_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
+  }
+}
+
 // Shared memory of the x passes (bytes).
 template <typename R, int N1>
 constexpr size_t xpass_smem(int rows_per_block) {
   return sizeof(cx<R>) * (N1 + kWarps * Line<N1>::XW + (size_t)rows_per_block * (N1 + 1));
+}
+
+// Rows per x-pass block: `mult` (1, 2, 4; 0 = 2) times the lines one block
+// iteration covers, halved while the shared memory exceeds 96 KB, at most
+// the rows of a field.
+template <typename R, int N1>
+inline int xpass_rows_per_block(int rows, int mult) {
+  int rpb = (mult > 0 ? mult : 2) * Line<N1>::LPI;
+  while (rpb > Line<N1>::LPI && xpass_smem<R, N1>(rpb) > 96 * 1024) rpb /= 2;
+  return rpb < rows ? rpb : rows;
 }
 
 // ---------------------------------------------------------------------------
@@ -273,6 +342,12 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
   TeamPos<N3> tz;
   C* xy = ty.xs(xs);
   C* xz = tz.xs(xs);
+  // a lane keeps its z-line position for every column and field: its
+  // stage-1 twiddles W_N3^(t c) are computed once here (square z shapes);
+  // with N2 = N3 the y-lines use the same team positions and twiddles
+  constexpr bool kSqZ = Line<N3>::R1 == Line<N3>::R2;
+  C wz[kSqZ ? Line<N3>::R1 : 1];
+  if constexpr (kSqZ) twiddle_powers<Line<N3>::R1>(tw3[tz.t], wz);
   C* inter = reinterpret_cast<C*>(P.inter);
   const int hy = N2 / 2;
   const size_t fstride = (size_t)P.n1 * Kz * Ky;   // between consecutive fields
@@ -346,7 +421,8 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
       for (int base = 0; base < Kz; base += Line<N2>::LPI) {
         const int ln = base + ty.line;
         const bool act = ln < Kz;
-        line_fft<N2, -1, true>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, N2);
+        line_fft<N2, -1, true>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, N2,
+                               (kSqZ && N2 == N3) ? wz : nullptr);
       }
     }
     __syncthreads();
@@ -357,7 +433,8 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
         const int col = base + tz.line;
         const bool act = col < N2;
         const int cc = act ? col : 0;
-        line_conv<N3, OP_GLOBAL>(plane + cc, PY, xz, tw3, op + (size_t)cc * op_cs, op_es, tz.t, act, Kz);
+        line_conv<N3, OP_GLOBAL>(plane + cc, PY, xz, tw3, op + (size_t)cc * op_cs, op_es, tz.t, act, Kz,
+                                 kSqZ ? wz : nullptr);
       }
     }
     __syncthreads();
@@ -367,7 +444,8 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
       for (int base = 0; base < Kz; base += Line<N2>::LPI) {
         const int ln = base + ty.line;
         const bool act = ln < Kz;
-        line_fft<N2, +1, false>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, Ky);
+        line_fft<N2, +1, false>(plane + (act ? ln : 0) * PY, 1, xy, tw2, ty.t, act, Ky,
+                                (kSqZ && N2 == N3) ? wz : nullptr);
       }
     }
     __syncthreads();
@@ -539,19 +617,22 @@ __device__ __forceinline__ void slab_tt_chunked(int rb, const C* __restrict__ H,
   }
 }
 
+// Item (x, p) of the fused yz pass, by the whole block: the slab of direction
+// p at x loaded or restored into shared memory, then every field of p.
+// `smem_raw` holds YZLayout::smem_bytes; `tcp` is the block's tensor-core
+// state (TC != 0, set up by the caller, whose operand staging this item
+// points at its own work area).
 template <typename R, int N2, int N3, int FMT, int TC>   // TC: 0 CUDA cores, 1 3xTF32, 2 BF16x3
-__global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
+__device__ __forceinline__ void yz_body(const YZParams& P, int x, int p, unsigned char* smem_raw, TcState* tcp) {
   using C = cx<R>;
   using LY = YZLayout<R, N2, N3>;
   constexpr int PY = LY::PY;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Tt = reinterpret_cast<C*>(smem_raw);   // N3 x PY, operator slab [z][y]
   C* tw2 = Tt + N3 * PY;
   C* tw3 = tw2 + N2;
   C* work = tw3 + N3;
   C* plane = work;                          // LY::G planes of N3/2 x PY, field [z][y]
   C* xs = plane + LY::G * (N3 / 2) * PY;
-  const int x = blockIdx.x, p = P.p0 + blockIdx.y;
   const int tid = threadIdx.x;
   for (int i = tid; i < N2; i += kThreads) tw2[i] = reinterpret_cast<const C*>(P.tw2)[i];
   for (int i = tid; i < N3; i += kThreads) tw3[i] = reinterpret_cast<const C*>(P.tw3)[i];
@@ -572,10 +653,8 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
     const C* H = reinterpret_cast<const C*>(d.h) + (size_t)x * d.hx;
     if constexpr (TC != 0) {
       // tensor cores, 3xTF32 or BF16x3 (tc_cgemm.cuh); factors read straight from L2
-      __shared__ uint32_t tmem_slot;
-      __shared__ uint64_t tc_bar;
-      TcState tc = tc_setup(work, &tc_bar, &tmem_slot);
-      tc.single = P.tc_single != 0;
+      TcState& tc = *tcp;
+      tc.buf = reinterpret_cast<float*>(work);
       const float2* U3 = reinterpret_cast<const float2*>(d.u3);
       const float2* Hf = reinterpret_cast<const float2*>(H);
       if constexpr (FMT == 1) {
@@ -595,8 +674,6 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
                    [&](int b, int y) { return Hf[y * rb + b]; }, reinterpret_cast<float2*>(Tt), PY,
                    (float)P.scale);
       }
-      if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
-      tc_teardown(tc);
     } else {
       // CUDA cores; row tiles sized so that every warp has an output tile
       using ST = SlabTile<N2, N3>;
@@ -627,6 +704,37 @@ __global__ void __launch_bounds__(kThreads, 1) yz_kernel(YZParams P) {
     }
   }
   yz_fields<R, N2, N3, LY::G, false>(P, x, p, plane, xs, tw2, tw3, Tt, 1, PY);
+}
+
+// One (x, p) item per block, or (inst != null) the persistent batch mode over
+// the items (instance, x, p), p-major, of instances of this shape class.
+template <typename R, int N2, int N3, int FMT, int TC>   // TC: 0 CUDA cores, 1 3xTF32, 2 BF16x3
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yz_kernel(YZParams P, const BatchYZ* __restrict__ inst, int ninst,
+                                                         long long total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint64_t tc_bar;
+  TcState tc;
+  if constexpr (FMT != 0 && TC != 0) tc = tc_setup(smem_raw, &tc_bar, &tmem_slot);
+  // one code path for both modes; the item's parameters in registers (a
+  // shared copy would be re-read after every shared-memory store)
+  const long long count = inst ? total : 1;
+  for (long long item = inst ? blockIdx.x : 0; item < count; item += gridDim.x) {
+    const int i = inst ? find_instance(inst, ninst, item) : 0;
+    const YZParams sp = inst ? inst[i].P : P;
+    if (inst) __syncthreads();                       // the previous item is done with shared memory
+    const int local = inst ? (int)(item - inst[i].item0) : 0;
+    const int x = inst ? local % sp.n1 : (int)blockIdx.x;
+    const int p = inst ? local / sp.n1 : sp.p0 + (int)blockIdx.y;
+    if constexpr (FMT != 0 && TC != 0) tc.single = sp.tc_single != 0;
+    const bool ok_before = tc.ok;
+    yz_body<R, N2, N3, FMT, TC>(sp, x, p, smem_raw, &tc);
+    if constexpr (FMT != 0 && TC != 0) {
+      // a wait that ran out marks the plan of the item it happened in
+      if (ok_before && !tc.ok && threadIdx.x == 0) atomicOr(sp.status, kStatusTcTimeout);
+    }
+  }
+  if constexpr (FMT != 0 && TC != 0) tc_teardown(tc);
 }
 
 // ---------------------------------------------------------------------------
@@ -744,6 +852,25 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
     if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
     tc_teardown(tc);
   }
+}
+
+// Blocks of a persistent batch launch of `kern`: the SMs times the blocks
+// its shared memory allows (at most four with a tensor-core restore: each
+// block holds 128 of an SM's 512 TMEM columns), at most `total`.
+template <typename K>
+int persistent_grid(K kern, size_t smem, bool tc, long long total) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+    per = 1;
+  }
+  if (per < 1) per = 1;
+  if (tc && per > 4) per = 4;
+  const long long g = (long long)sms * per;
+  return (int)(g < total ? g : total);
 }
 
 }  // namespace fmm

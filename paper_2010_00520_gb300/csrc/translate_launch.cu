@@ -1,4 +1,6 @@
 // Launch sequence of one translation: [restore pre-pass] -> xfwd -> yz -> xinv.
+#include <cstring>
+
 #include "translate_kernels.cuh"
 
 namespace fmm {
@@ -13,6 +15,13 @@ FMM_YZ_DECL(f64, 0)
 FMM_YZ_DECL(f64, 1)
 FMM_YZ_DECL(f64, 2)
 #undef FMM_YZ_DECL
+#define FMM_YZB_DECL(TAG, F)                                                                       \
+  cudaError_t launch_yz_batch_##TAG##_##F(const YZParams& P, int n2, int n3, size_t smem, cudaStream_t s, \
+                                          const BatchYZ* inst, int ninst, long long total);
+FMM_YZB_DECL(f32, 0)
+FMM_YZB_DECL(f32, 1)
+FMM_YZB_DECL(f32, 2)
+#undef FMM_YZB_DECL
 #define FMM_YZL_DECL(TAG, F)                                                                  \
   cudaError_t launch_yzl_##TAG##_##F(const YZParams& P, int n2, int n3, dim3 grid, size_t smem, \
                                      cudaStream_t s);
@@ -27,13 +36,6 @@ FMM_YZL_DECL(f64, 2)
 static const size_t kMaxSmem = 227 * 1024;
 
 template <typename R, int N1>
-static int xpass_rows_per_block(int rows, int mult) {
-  int rpb = (mult > 0 ? mult : 2) * Line<N1>::LPI;
-  while (rpb > Line<N1>::LPI && xpass_smem<R, N1>(rpb) > 96 * 1024) rpb /= 2;
-  return rpb < rows ? rpb : rows;
-}
-
-template <typename R, int N1>
 static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s) {
   static std::atomic<int> optin_f[kMaxDevices], optin_i[kMaxDevices];
   P.rows_per_block = xpass_rows_per_block<R, N1>(P.rows, P.rows_per_block);
@@ -42,13 +44,76 @@ static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s)
   if (fwd) {
     cudaError_t e = smem_optin((const void*)xfwd_kernel<R, N1>, optin_f);
     if (e != cudaSuccess) return e;
-    xfwd_kernel<R, N1><<<grid, kThreads, smem, s>>>(P);
+    xfwd_kernel<R, N1><<<grid, kThreads, smem, s>>>(P, nullptr, 0, 0);
   } else {
     cudaError_t e = smem_optin((const void*)xinv_kernel<R, N1>, optin_i);
     if (e != cudaSuccess) return e;
-    xinv_kernel<R, N1><<<grid, kThreads, smem, s>>>(P);
+    xinv_kernel<R, N1><<<grid, kThreads, smem, s>>>(P, nullptr, 0, 0);
   }
   return cudaGetLastError();
+}
+
+// Persistent batch mode of the x passes over `total` items of `ninst`
+// instances with this n1 (float).
+template <int N1>
+static cudaError_t launch_x_batch_inst(bool fwd, const BatchX* inst, int ninst, long long total, size_t smem,
+                                       cudaStream_t s) {
+  static std::atomic<int> optin_f[kMaxDevices], optin_i[kMaxDevices];
+  XPassParams none;
+  std::memset(&none, 0, sizeof(none));
+  if (fwd) {
+    auto kern = xfwd_kernel<float, N1>;
+    cudaError_t e = smem_optin((const void*)kern, optin_f);
+    if (e != cudaSuccess) return e;
+    kern<<<persistent_grid(kern, smem, false, total), kThreads, smem, s>>>(none, inst, ninst, total);
+  } else {
+    auto kern = xinv_kernel<float, N1>;
+    cudaError_t e = smem_optin((const void*)kern, optin_i);
+    if (e != cudaSuccess) return e;
+    kern<<<persistent_grid(kern, smem, false, total), kThreads, smem, s>>>(none, inst, ninst, total);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, int ninst, long long total, size_t smem,
+                           cudaStream_t s) {
+  switch (n1) {
+    case 4: return launch_x_batch_inst<4>(fwd, inst, ninst, total, smem, s);
+    case 8: return launch_x_batch_inst<8>(fwd, inst, ninst, total, smem, s);
+    case 16: return launch_x_batch_inst<16>(fwd, inst, ninst, total, smem, s);
+    case 32: return launch_x_batch_inst<32>(fwd, inst, ninst, total, smem, s);
+    case 64: return launch_x_batch_inst<64>(fwd, inst, ninst, total, smem, s);
+    case 128: return launch_x_batch_inst<128>(fwd, inst, ninst, total, smem, s);
+    case 256: return launch_x_batch_inst<256>(fwd, inst, ninst, total, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// x-pass rows per block and shared memory of an n1 (float), as a single
+// translation chooses them.
+void x_pass_shape(int n1, int rows, int mult, int* rpb, size_t* smem) {
+  switch (n1) {
+#define FMM_XSHAPE(N)                                   \
+    case N:                                             \
+      *rpb = xpass_rows_per_block<float, N>(rows, mult); \
+      *smem = xpass_smem<float, N>(*rpb);               \
+      return;
+    FMM_XSHAPE(4) FMM_XSHAPE(8) FMM_XSHAPE(16) FMM_XSHAPE(32) FMM_XSHAPE(64) FMM_XSHAPE(128) FMM_XSHAPE(256)
+#undef FMM_XSHAPE
+    default:
+      *rpb = 0;
+      *smem = 0;
+  }
+}
+
+cudaError_t launch_yz_batch(int fmt, const YZParams& P, int n2, int n3, size_t smem, cudaStream_t s,
+                            const BatchYZ* inst, int ninst, long long total) {
+  switch (fmt) {
+    case 0: return launch_yz_batch_f32_0(P, n2, n3, smem, s, inst, ninst, total);
+    case 1: return launch_yz_batch_f32_1(P, n2, n3, smem, s, inst, ninst, total);
+    case 2: return launch_yz_batch_f32_2(P, n2, n3, smem, s, inst, ninst, total);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename R>
