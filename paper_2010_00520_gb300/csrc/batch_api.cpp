@@ -62,7 +62,7 @@ int launch_all(fmmfft_batch_s* b, const void* const* in, void* const* out, const
     }
   }
   b->shared_last = (int)together.size();
-  if (!together.empty() && fmm::launch_translate_batch(together, b->dev, stream) != cudaSuccess) {
+  if (!together.empty() && fmm::launch_translate_batch(together, b->dev, stream, b->side) != cudaSuccess) {
     cudaGetLastError();
     return FMMFFT_ERR_CUDA;
   }

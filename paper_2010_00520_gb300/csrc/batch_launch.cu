@@ -1,22 +1,24 @@
 // Persistent launches of a batch of translations (many independent FMM-FFT
 // instances of uneven grids, ranks and RHS counts; Sec. II.C per instance):
-// the instances are grouped into shape classes and every phase runs one
-// persistent launch per class, walking the work items of all its instances,
-// instead of one launch per instance:
+// the instances are grouped into shape classes (FFT extents, operator kind,
+// restore arithmetic) and every phase runs one persistent launch per class,
+// walking the work items of all the class's instances, instead of one
+// launch per instance:
 //
 //   pre-pass  the restore products of every instance (the steps of Figs. 3-4
 //             that do not depend on x), one batched-GEMM launch per stage
 //             index and arithmetic, their descriptors gathered into one array;
-//   x fwd     per x extent n1: items (instance, field, row block);
-//   yz        per (n2, n3, operator kind, restore arithmetic): items
-//             (instance, x, direction), slab restore and the y/z transforms
-//             with the Hadamard product;
-//   x inv     per x extent, as x fwd.
+//   x fwd     per class: items (instance, field, row block);
+//   yz        per class: items (instance, x, direction), slab restore and
+//             the y/z transforms with the Hadamard product;
+//   x inv     per class, as x fwd.
 //
-// The kernels are the single-translation kernels in their persistent batch
-// mode (translate_kernels.cuh): a block copies the item's instance
-// parameters to shared memory and runs the same per-item code, so a batched
-// translation equals the instances' own translations bit for bit.
+// The classes run on separate streams forked from the caller's, so that one
+// class's HBM-bound x passes overlap another's arithmetic-bound yz pass.  The
+// kernels are the single-translation kernels in their persistent batch mode
+// (translate_kernels.cuh): a block loads the item's instance parameters and
+// runs the same per-item code, so a batched translation equals the
+// instances' own translations bit for bit.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -36,15 +38,13 @@ namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-struct XClass {
+struct Class {
   std::vector<BatchX> fwd, inv;
-  long long total = 0;
-  size_t smem = 0;
-};
-struct YZClass {
-  std::vector<BatchYZ> items;
-  long long total = 0;
-  size_t smem = 0;
+  long long x_total = 0;
+  size_t x_smem = 0;
+  std::vector<BatchYZ> yz;
+  long long yz_total = 0;
+  size_t yz_smem = 0;
 };
 
 }  // namespace
@@ -54,11 +54,12 @@ bool batch_persistent_ok(const TranslateArgs& a) {
   return prec_ok && !a.large && a.p0 == 0 && a.nw == 0 && a.dis == nullptr && a.yz_fmt >= 0 && a.yz_fmt <= 2;
 }
 
-cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, BatchDev& dev, cudaStream_t s) {
+cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, BatchDev& dev, cudaStream_t s,
+                                   const std::vector<cudaStream_t>& lanes) {
   const int n = (int)args.size();
   if (n == 0) return cudaSuccess;
-  std::map<int, XClass> xc;                                   // by n1
-  std::map<std::tuple<int, int, int, int>, YZClass> yc;       // by (n2, n3, yz_fmt, tc)
+  // classes by (n1, n2, n3, yz_fmt, tc)
+  std::map<std::tuple<int, int, int, int, int>, Class> cls;
   for (int i = 0; i < n; ++i) {
     const TranslateArgs& a = args[i];
     const int rows = a.K[1] * a.K[2];
@@ -73,20 +74,23 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     if (X.rows_per_block <= 0) return cudaErrorInvalidValue;
     X.occ = a.occ;
     X.rowocc = a.rowocc;
-    XClass& c = xc[a.n[0]];
+    Class& c = cls[std::make_tuple(a.n[0], a.n[1], a.n[2], a.yz_fmt, a.tc)];
+    // every byte defined (the descriptors are compared bytewise between calls)
     BatchX f, v;
+    std::memset(&f, 0, sizeof(f));
+    std::memset(&v, 0, sizeof(v));
     f.P = X;
     f.P.src = a.s_in;
     f.P.dst = a.inter;
-    f.item0 = c.total;
+    f.item0 = c.x_total;
     v.P = X;
     v.P.src = a.inter;
     v.P.dst = a.s_out;
-    v.item0 = c.total;
+    v.item0 = c.x_total;
     c.fwd.push_back(f);
     c.inv.push_back(v);
-    c.total += (long long)F * ((rows + X.rows_per_block - 1) / X.rows_per_block);
-    c.smem = std::max(c.smem, xs);
+    c.x_total += (long long)F * ((rows + X.rows_per_block - 1) / X.rows_per_block);
+    c.x_smem = std::max(c.x_smem, xs);
     BatchYZ b;
     std::memset(&b, 0, sizeof(b));
     YZParams& Y = b.P;
@@ -107,11 +111,10 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     Y.tc_single = a.tc_single;
     Y.n_dir = a.n_dir;
     Y.p0 = 0;
-    YZClass& z = yc[std::make_tuple(a.n[1], a.n[2], a.yz_fmt, a.tc)];
-    b.item0 = z.total;
-    z.items.push_back(b);
-    z.total += (long long)a.n[0] * a.n_dir;
-    z.smem = std::max(z.smem, yz_smem_bytes(a));
+    b.item0 = c.yz_total;
+    c.yz.push_back(b);
+    c.yz_total += (long long)a.n[0] * a.n_dir;
+    c.yz_smem = std::max(c.yz_smem, yz_smem_bytes(a));
   }
   // pre-pass products of every compressed instance, merged per stage index
   // and arithmetic (tensor cores in 3xTF32 / TF32 or BF16x3, or CUDA cores)
@@ -150,12 +153,17 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     std::memcpy(host.data() + at, p, bytes);
     return at;
   };
-  std::vector<std::pair<size_t, size_t>> xoff;                 // per x class: fwd, inv offsets
-  for (auto& kv : xc)
-    xoff.push_back({put(kv.second.fwd.data(), sizeof(BatchX) * kv.second.fwd.size()),
-                    put(kv.second.inv.data(), sizeof(BatchX) * kv.second.inv.size())});
-  std::vector<size_t> yoff;
-  for (auto& kv : yc) yoff.push_back(put(kv.second.items.data(), sizeof(BatchYZ) * kv.second.items.size()));
+  struct Off {
+    size_t fwd, inv, yz;
+  };
+  std::vector<Off> off;
+  for (auto& kv : cls) {
+    Off o;
+    o.fwd = put(kv.second.fwd.data(), sizeof(BatchX) * kv.second.fwd.size());
+    o.inv = put(kv.second.inv.data(), sizeof(BatchX) * kv.second.inv.size());
+    o.yz = put(kv.second.yz.data(), sizeof(BatchYZ) * kv.second.yz.size());
+    off.push_back(o);
+  }
   size_t n_gemm = 0;
   for (auto& m : merges) n_gemm += m.batch;
   const size_t o_gm = align_up(host.size(), 256);
@@ -167,9 +175,12 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
   for (auto& m : merges)
     for (auto& pr : m.parts) gsrc.push_back(pr.first);
   cudaError_t e;
+  if (!dev.pre && (e = cudaEventCreateWithFlags(&dev.pre, cudaEventDisableTiming)) != cudaSuccess) return e;
   if (host != dev.host || gsrc != dev.gemm_src) {
     // the batch's launches in flight read the old descriptors
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    for (auto l : lanes)
+      if ((e = cudaStreamSynchronize(l)) != cudaSuccess) return e;
     if (bytes > dev.bytes) {
       if (dev.d_desc) cudaFree(dev.d_desc);
       dev.d_desc = nullptr;
@@ -209,44 +220,34 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
       at += m.batch;
     }
   }
-  // x forward, one launch per x extent
-  {
-    size_t k = 0;
-    for (auto& kv : xc) {
-      const XClass& c = kv.second;
-      if ((e = launch_x_batch(true, kv.first, (const BatchX*)(base + xoff[k].first), (int)c.fwd.size(), c.total,
-                              c.smem, s)) != cudaSuccess)
-        return e;
-      ++k;
-    }
-  }
-  // yz, one launch per shape class
-  {
-    size_t k = 0;
-    for (auto& kv : yc) {
-      const YZClass& c = kv.second;
-      const int n2 = std::get<0>(kv.first), n3 = std::get<1>(kv.first), fmt = std::get<2>(kv.first);
-      if ((e = launch_yz_batch(fmt, c.items[0].P, n2, n3, c.smem, s, (const BatchYZ*)(base + yoff[k]),
-                               (int)c.items.size(), c.total)) != cudaSuccess)
-        return e;
-      ++k;
-    }
-  }
-  // x inverse
-  {
-    size_t k = 0;
-    for (auto& kv : xc) {
-      const XClass& c = kv.second;
-      if ((e = launch_x_batch(false, kv.first, (const BatchX*)(base + xoff[k].second), (int)c.inv.size(), c.total,
-                              c.smem, s)) != cudaSuccess)
-        return e;
-      ++k;
-    }
+  // every class waits for the merged pre-pass, then runs its three phases
+  // on its lane
+  if ((e = cudaEventRecord(dev.pre, s)) != cudaSuccess) return e;
+  for (auto l : lanes)
+    if ((e = cudaStreamWaitEvent(l, dev.pre, 0)) != cudaSuccess) return e;
+  size_t k = 0;
+  for (auto& kv : cls) {
+    const Class& c = kv.second;
+    const int n1 = std::get<0>(kv.first), n2 = std::get<1>(kv.first), n3 = std::get<2>(kv.first);
+    const int fmt = std::get<3>(kv.first);
+    cudaStream_t l = lanes.empty() ? s : lanes[k % lanes.size()];
+    if ((e = launch_x_batch(true, n1, (const BatchX*)(base + off[k].fwd), (int)c.fwd.size(), c.x_total, c.x_smem,
+                            l)) != cudaSuccess)
+      return e;
+    if ((e = launch_yz_batch(fmt, c.yz[0].P, n2, n3, c.yz_smem, l, (const BatchYZ*)(base + off[k].yz),
+                             (int)c.yz.size(), c.yz_total)) != cudaSuccess)
+      return e;
+    if ((e = launch_x_batch(false, n1, (const BatchX*)(base + off[k].inv), (int)c.inv.size(), c.x_total, c.x_smem,
+                            l)) != cudaSuccess)
+      return e;
+    ++k;
   }
   return cudaSuccess;
 }
 
 void batch_dev_release(BatchDev& dev) {
+  if (dev.pre) cudaEventDestroy(dev.pre);
+  dev.pre = nullptr;
   if (dev.d_desc) cudaFree(dev.d_desc);
   dev.d_desc = nullptr;
   dev.bytes = 0;

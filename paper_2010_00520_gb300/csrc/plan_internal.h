@@ -174,17 +174,20 @@ struct BatchDev {
   size_t bytes = 0;
   std::vector<unsigned char> host;
   std::vector<const void*> gemm_src;
+  cudaEvent_t pre = nullptr;           // the merged pre-pass is done
 };
 // Whether a translation can join the batch's persistent launches: complex64,
 // y-z planes of the fused yz kernel (not the large-plane one), whole-plan
 // launch.
 bool batch_persistent_ok(const TranslateArgs& a);
-// All translations of `args` grouped into shape classes, one persistent
-// launch per phase and class (merged restore pre-pass, x forward per x
-// extent, yz per plane shape / operator kind / restore arithmetic, x
-// inverse), on stream s.  Uploads the descriptors to dev when they changed,
-// after synchronising s.
-cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, BatchDev& dev, cudaStream_t s);
+// All translations of `args` grouped into shape classes (FFT extents,
+// operator kind, restore arithmetic): the merged restore pre-pass on stream
+// s, then per class one persistent launch per phase (x forward, yz, x
+// inverse) on lanes[class % lanes.size()] (streams already forked from s),
+// so that classes overlap.  Uploads the descriptors to dev when they
+// changed, after synchronising s and the lanes.
+cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, BatchDev& dev, cudaStream_t s,
+                                   const std::vector<cudaStream_t>& lanes);
 void batch_dev_release(BatchDev& dev);
 
 // Aggregation (Eq. 4) and disaggregation (Eq. 6), farfield.cu.  P: patterns

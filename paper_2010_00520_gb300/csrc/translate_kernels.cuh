@@ -155,9 +155,13 @@ __device__ __forceinline__ void xfwd_body(const XPassParams& P, int item, unsign
   }
   __syncthreads();
   // I[f][x][r]: rows contiguous for fixed x; a line with no occupied box has
-  // a zero spectrum
-  for (int i = threadIdx.x; i < N1 * nr; i += kThreads) {
-    const int x = i / nr, r = i - x * nr;
+  // a zero spectrum.  (x, r) from the element number by shift and mask over
+  // the power of two rp2 >= rows per block (no division per element)
+  const int lg = 31 - __clz(P.rows_per_block) + ((P.rows_per_block & (P.rows_per_block - 1)) ? 1 : 0);
+  const int rp2 = 1 << lg;
+  for (int i = threadIdx.x; i < (N1 << lg); i += kThreads) {
+    const int x = i >> lg, r = i & (rp2 - 1);
+    if (r >= nr) continue;
     const bool live = !P.rowocc || P.rowocc[r0 + r];
     dst[((size_t)f * N1 + x) * P.rows + r0 + r] = live ? Q[r * PX + x] : czero<C>();
   }
@@ -172,11 +176,19 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P, const Bat
     xfwd_body<R, N1>(P, blockIdx.x, smem_raw);
     return;
   }
+  // a block's items advance by gridDim.x: the instance is looked up only
+  // when an item leaves the current instance's range
+  long long lo = 1, hi = 0;
+  XPassParams Pi;
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    const int i = find_instance(inst, ninst, item);
-    const XPassParams Pi = inst[i].P;
+    if (item < lo || item >= hi) {
+      const int i = find_instance(inst, ninst, item);
+      lo = inst[i].item0;
+      hi = i + 1 < ninst ? inst[i + 1].item0 : total;
+      Pi = inst[i].P;
+    }
     __syncthreads();                                 // the previous item is done with shared memory
-    xfwd_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
+    xfwd_body<R, N1>(Pi, (int)(item - lo), smem_raw);
   }
 }
 
@@ -196,10 +208,27 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
   const C* src = reinterpret_cast<const C*>(P.src);
   C* dst = reinterpret_cast<C*>(P.dst) + ((size_t)f * P.rows + r0) * P.Kx;
   for (int i = threadIdx.x; i < N1; i += kThreads) tw[i] = reinterpret_cast<const C*>(P.tw)[i];
-  for (int i = threadIdx.x; i < N1 * nr; i += kThreads) {
-    const int x = i / nr, r = i - x * nr;
-    const bool live = !P.rowocc || P.rowocc[r0 + r];
-    Q[r * PX + x] = live ? src[((size_t)f * N1 + x) * P.rows + r0 + r] : czero<C>();
+  // (x, r) by shift and mask over the power of two rp2 >= rows per block;
+  // batches of kLd loads per thread in flight before their shared-memory
+  // stores
+  const int lg = 31 - __clz(P.rows_per_block) + ((P.rows_per_block & (P.rows_per_block - 1)) ? 1 : 0);
+  const int rp2 = 1 << lg;
+  constexpr int kLd = 8;
+  for (int i0 = threadIdx.x; i0 < (N1 << lg); i0 += kLd * kThreads) {
+    C v[kLd];
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int i = i0 + j * kThreads;
+      const int x = i >> lg, r = i & (rp2 - 1);
+      const bool live = i < (N1 << lg) && r < nr && (!P.rowocc || P.rowocc[r0 + r]);
+      v[j] = live ? src[((size_t)f * N1 + x) * P.rows + r0 + r] : czero<C>();
+    }
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int i = i0 + j * kThreads;
+      const int x = i >> lg, r = i & (rp2 - 1);
+      if (i < (N1 << lg) && r < nr) Q[r * PX + x] = v[j];
+    }
   }
   __syncthreads();
   TeamPos<N1> tp;
@@ -210,11 +239,13 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
     line_fft<N1, +1, false>(Q + (line < nr ? line : 0) * PX, 1, xt, tw, tp.t, act, P.Kx);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nr * P.Kx; i += kThreads) {
-    const int r = i / P.Kx, x = i - r * P.Kx;
-    const bool occupied = !P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x];
-    dst[(size_t)r * P.Kx + x] = occupied ? Q[r * PX + x] : czero<C>();
-  }
+  // one row per warp at a time, lanes along x (coalesced, no division)
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < nr; r += kWarps)
+    for (int x = lane; x < P.Kx; x += 32) {
+      const bool occupied = !P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x];
+      dst[(size_t)r * P.Kx + x] = occupied ? Q[r * PX + x] : czero<C>();
+    }
 }
 
 template <typename R, int N1>
@@ -225,11 +256,17 @@ __global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P, const Bat
     xinv_body<R, N1>(P, blockIdx.x, smem_raw);
     return;
   }
+  long long lo = 1, hi = 0;                          // as in xfwd_kernel
+  XPassParams Pi;
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    const int i = find_instance(inst, ninst, item);
-    const XPassParams Pi = inst[i].P;
+    if (item < lo || item >= hi) {
+      const int i = find_instance(inst, ninst, item);
+      lo = inst[i].item0;
+      hi = i + 1 < ninst ? inst[i + 1].item0 : total;
+      Pi = inst[i].P;
+    }
     __syncthreads();                                 // the previous item is done with shared memory
-    xinv_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
+    xinv_body<R, N1>(Pi, (int)(item - lo), smem_raw);
   }
 }
 
@@ -718,12 +755,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yz_kernel(YZ
   if constexpr (FMT != 0 && TC != 0) tc = tc_setup(smem_raw, &tc_bar, &tmem_slot);
   // one code path for both modes; the item's parameters in registers (a
   // shared copy would be re-read after every shared-memory store)
+  // a block's items advance by gridDim.x: the instance is looked up only
+  // when an item leaves the current instance's range
   const long long count = inst ? total : 1;
+  long long lo = 1, hi = 0;
+  YZParams sp = P;
   for (long long item = inst ? blockIdx.x : 0; item < count; item += gridDim.x) {
-    const int i = inst ? find_instance(inst, ninst, item) : 0;
-    const YZParams sp = inst ? inst[i].P : P;
+    if (inst && (item < lo || item >= hi)) {
+      const int i = find_instance(inst, ninst, item);
+      lo = inst[i].item0;
+      hi = i + 1 < ninst ? inst[i + 1].item0 : total;
+      sp = inst[i].P;
+    }
     if (inst) __syncthreads();                       // the previous item is done with shared memory
-    const int local = inst ? (int)(item - inst[i].item0) : 0;
+    const int local = inst ? (int)(item - lo) : 0;
     const int x = inst ? local % sp.n1 : (int)blockIdx.x;
     const int p = inst ? local / sp.n1 : sp.p0 + (int)blockIdx.y;
     if constexpr (FMT != 0 && TC != 0) tc.single = sp.tc_single != 0;
