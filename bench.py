@@ -68,7 +68,7 @@ FORMAT_NAMES = {(3, 1): "tucker3d", (3, 2): "tt3d", (4, 1): "tucker4d", (4, 2): 
                 (0, 0): "none"}
 FAR_NB = 16                  # basis functions per box of the far-field steps (Eqs. 4, 6)
 # version of the yz kernels the committed DRAM-traffic figures were taken on
-YZ_KERNEL_VERSION = 5
+YZ_KERNEL_VERSION = 6
 
 
 def workload(name: str) -> dict:

@@ -482,13 +482,13 @@ int fmmfft_multipole_count(double a, double k0, double eps_re, double eps_im, do
  * with nrhs[i] RHS (device pointers and layouts as fmmfft_translate), all
  * asynchronous on `stream`.  The complex64 instances whose y-z planes fit
  * the fused yz kernel (any format and restore arithmetic) run together: they
- * are grouped into shape classes and every phase runs one persistent launch
- * per class for all its instances -- the merged restore pre-pass (one launch
- * per stage), the forward x pass (per x extent), the yz pass (per plane
- * shape, operator kind and restore arithmetic) and the inverse x pass --
- * each a grid of the SMs' resident blocks walking the work items of every
- * instance of the class, with the same device code as a single translation,
- * so results equal each instance's fmmfft_translate bit for bit.  Any other
+ * are grouped into shape classes and every phase runs one launch per class
+ * for all its instances -- the merged restore pre-pass (one launch per
+ * stage), the forward x pass (per x extent), the yz pass (per plane shape,
+ * operator kind and restore arithmetic) and the inverse x pass -- whose
+ * blocks take the work items of every instance of the class in turn, with
+ * the same device code as a single translation, so results equal each
+ * instance's fmmfft_translate bit for bit.  Any other
  * instance (complex128, or planes of the large-plane kernel) runs its own
  * launches on one of up to four internal streams.  The environment variable
  * FMMFFT_BATCH_SEPARATE=1 at fmmfft_batch_create gives every instance its
@@ -511,7 +511,7 @@ int fmmfft_batch_create(fmmfft_batch* out, const fmmfft_plan* plans, int nplans)
 int fmmfft_batch_translate(fmmfft_batch batch, const void* const* S_in, void* const* S_out,
                            const int* nrhs, void* stream);
 int fmmfft_batch_destroy(fmmfft_batch batch);
-/* Number of instances that ran in the shared (persistent) launches of the
+/* Number of instances that ran in the shared launches of the
  * batch's last fmmfft_batch_translate call (the others ran on their own). */
 int fmmfft_batch_shared_count(fmmfft_batch batch, int* count);
 

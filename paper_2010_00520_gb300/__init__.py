@@ -470,8 +470,8 @@ def fmmfft_translate_disaggregate(plan, S_in, patterns, y, nb, nrhs, stream=None
 
 
 def fmmfft_batch_shared_count(batch) -> int:
-    """Instances of the last batch call that ran in the shared (persistent)
-    launches."""
+    """Instances of the last batch call that ran in the shared launches (one
+    per phase and shape class)."""
     n = ctypes.c_int()
     _check(lib().fmmfft_batch_shared_count(batch, ctypes.byref(n)), "fmmfft_batch_shared_count")
     return n.value

@@ -1,7 +1,7 @@
 // Batched translation of several independent plans (uneven grids, ranks and
-// RHS counts).  The instances that the persistent batch kernels cover
-// (batch_persistent_ok) run together, one launch per phase for all of them
-// (batch_kernels.cu); any other instance runs its own launch sequence on one
+// RHS counts).  The instances that the batch mode of the kernels covers
+// (batch_persistent_ok) run together, one launch per phase and shape class
+// (batch_launch.cu); any other instance runs its own launch sequence on one
 // of a few side streams.  Repeated calls with the same buffers replay one
 // captured CUDA graph.
 #include <algorithm>
@@ -41,7 +41,7 @@ void drop_graph(fmmfft_batch_s* b) {
   b->graph = nullptr;
 }
 
-// Fork from `stream`: the persistent launches of the instances they cover on
+// Fork from `stream`: the shared launches of the instances they cover on
 // `stream`, every other instance on a side stream; join back.
 int launch_all(fmmfft_batch_s* b, const void* const* in, void* const* out, const int* nrhs,
                const std::vector<void*>& inter, const std::vector<size_t>& cap, cudaStream_t stream) {

@@ -1,9 +1,9 @@
-// Persistent launches of a batch of translations (many independent FMM-FFT
+// Shared launches of a batch of translations (many independent FMM-FFT
 // instances of uneven grids, ranks and RHS counts; Sec. II.C per instance):
 // the instances are grouped into shape classes (FFT extents, operator kind,
-// restore arithmetic) and every phase runs one persistent launch per class,
-// walking the work items of all the class's instances, instead of one
-// launch per instance:
+// restore arithmetic) and every phase runs one launch per class over the
+// work items of all the class's instances, instead of one launch per
+// instance:
 //
 //   pre-pass  the restore products of every instance (the steps of Figs. 3-4
 //             that do not depend on x), one batched-GEMM launch per stage
@@ -15,9 +15,9 @@
 //
 // The classes run on separate streams forked from the caller's, so that one
 // class's HBM-bound x passes overlap another's arithmetic-bound yz pass.  The
-// kernels are the single-translation kernels in their persistent batch mode
-// (translate_kernels.cuh): a block loads the item's instance parameters and
-// runs the same per-item code, so a batched translation equals the
+// kernels are the single-translation kernels in their batch mode
+// (translate_kernels.cuh): a block looks up its items' instance parameters
+// and runs the same per-item code, so a batched translation equals the
 // instances' own translations bit for bit.
 #include <algorithm>
 #include <cstring>
@@ -28,8 +28,8 @@
 
 namespace fmm {
 
-cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, int ninst, long long total, size_t smem,
-                           cudaStream_t s);
+cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, const int* hint, int ninst, long long total,
+                           size_t smem, cudaStream_t s);
 void x_pass_shape(int n1, int rows, int mult, int* rpb, size_t* smem);
 cudaError_t launch_yz_batch(int fmt, const YZParams& P, int n2, int n3, size_t smem, cudaStream_t s,
                             const BatchYZ* inst, int ninst, long long total);
@@ -154,7 +154,7 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     return at;
   };
   struct Off {
-    size_t fwd, inv, yz;
+    size_t fwd, inv, yz, hint;
   };
   std::vector<Off> off;
   for (auto& kv : cls) {
@@ -162,6 +162,15 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     o.fwd = put(kv.second.fwd.data(), sizeof(BatchX) * kv.second.fwd.size());
     o.inv = put(kv.second.inv.data(), sizeof(BatchX) * kv.second.inv.size());
     o.yz = put(kv.second.yz.data(), sizeof(BatchYZ) * kv.second.yz.size());
+    // x-pass hints: the instance holding item k << kHintShift
+    const auto& f = kv.second.fwd;
+    std::vector<int> hint((size_t)((kv.second.x_total >> kHintShift) + 1), 0);
+    for (size_t k = 0, i = 0; k < hint.size(); ++k) {
+      const long long item = (long long)k << kHintShift;
+      while (i + 1 < f.size() && f[i + 1].item0 <= item) ++i;
+      hint[k] = (int)i;
+    }
+    o.hint = put(hint.data(), sizeof(int) * hint.size());
     off.push_back(o);
   }
   size_t n_gemm = 0;
@@ -231,14 +240,15 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     const int n1 = std::get<0>(kv.first), n2 = std::get<1>(kv.first), n3 = std::get<2>(kv.first);
     const int fmt = std::get<3>(kv.first);
     cudaStream_t l = lanes.empty() ? s : lanes[k % lanes.size()];
-    if ((e = launch_x_batch(true, n1, (const BatchX*)(base + off[k].fwd), (int)c.fwd.size(), c.x_total, c.x_smem,
-                            l)) != cudaSuccess)
+    const int* hint = (const int*)(base + off[k].hint);
+    if ((e = launch_x_batch(true, n1, (const BatchX*)(base + off[k].fwd), hint, (int)c.fwd.size(), c.x_total,
+                            c.x_smem, l)) != cudaSuccess)
       return e;
     if ((e = launch_yz_batch(fmt, c.yz[0].P, n2, n3, c.yz_smem, l, (const BatchYZ*)(base + off[k].yz),
                              (int)c.yz.size(), c.yz_total)) != cudaSuccess)
       return e;
-    if ((e = launch_x_batch(false, n1, (const BatchX*)(base + off[k].inv), (int)c.inv.size(), c.x_total, c.x_smem,
-                            l)) != cudaSuccess)
+    if ((e = launch_x_batch(false, n1, (const BatchX*)(base + off[k].inv), hint, (int)c.inv.size(), c.x_total,
+                            c.x_smem, l)) != cudaSuccess)
       return e;
     ++k;
   }

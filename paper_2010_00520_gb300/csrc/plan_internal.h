@@ -167,7 +167,7 @@ void plan_set_last_stream(fmmfft_plan p, void* stream);
 int translate_args_for(fmmfft_plan p, const void* S_in, void* S_out, int nrhs, void* scratch, size_t scratch_bytes,
                        TranslateArgs* out);
 
-// Persistent launches of a batch (batch_launch.cu).  BatchDev: the batch's
+// Shared launches of a batch (batch_launch.cu).  BatchDev: the batch's
 // device descriptor buffer and the host copy of what it holds.
 struct BatchDev {
   void* d_desc = nullptr;
@@ -176,13 +176,13 @@ struct BatchDev {
   std::vector<const void*> gemm_src;
   cudaEvent_t pre = nullptr;           // the merged pre-pass is done
 };
-// Whether a translation can join the batch's persistent launches: complex64,
+// Whether a translation can join the batch's shared launches: complex64,
 // y-z planes of the fused yz kernel (not the large-plane one), whole-plan
 // launch.
 bool batch_persistent_ok(const TranslateArgs& a);
 // All translations of `args` grouped into shape classes (FFT extents,
 // operator kind, restore arithmetic): the merged restore pre-pass on stream
-// s, then per class one persistent launch per phase (x forward, yz, x
+// s, then per class one launch per phase (x forward, yz, x
 // inverse) on lanes[class % lanes.size()] (streams already forked from s),
 // so that classes overlap.  Uploads the descriptors to dev when they
 // changed, after synchronising s and the lanes.

@@ -48,33 +48,6 @@ static void finish_ranks(Layout& L) {
   }
 }
 
-// Tucker-like layouts (slab = U3 . (U2 . H_p[x])^T) on y-z planes of at least
-// kFoldPlane points, which the large-plane yz kernel restores slab by slab:
-// the product with U2 moves into the pre-pass as one more batched stage,
-//   H2_p[x] = U2 . H_p[x]   (n2 x r3 for every direction p and x),
-// so that the yz kernel restores a TT-like slab (slab = U3 . H2_p[x]^T) with
-// one product per tile instead of two.  Same sums, in the same order per
-// element; the scratch grows by n1 n2 r3 per direction.
-static constexpr int64_t kFoldPlane = 128 * 128;
-
-static void fold_u2(Layout& L) {
-  if (L.yz_fmt != 1 || (int64_t)L.n[1] * L.n[2] < kFoldPlane) return;
-  const int n1 = L.n[0], n2 = L.n[1];
-  std::vector<GemmSpec> stage;
-  for (auto& s : L.slabs) {
-    BufRef h2 = L.scratch_alloc((int64_t)n1 * n2 * s.rb);
-    for (int x = 0; x < n1; ++x)
-      stage.push_back(gemm(s.u2, offset(s.h, (int64_t)x * s.hx), offset(h2, (int64_t)x * n2 * s.rb), n2, s.rb, s.ra));
-    s.h = h2;
-    s.hx = (int64_t)n2 * s.rb;
-    s.u2 = BufRef();
-    s.ra = 0;
-  }
-  L.stages.push_back(stage);
-  L.yz_fmt = 2;
-  finish_ranks(L);
-}
-
 // ---------------------------------------------------------------------------
 // Tucker-3D (Fig. 3(a)): per direction C_p, U1_p, U2_p, U3_p.
 // Pre-pass: H_p = U1_p . mat(C_p) (n1 x r2 r3).
@@ -109,7 +82,6 @@ void layout_tucker3d(const std::vector<Tucker3>& tk, const int n[3], Layout& L) 
     }
   }
   finish_ranks(L);
-  fold_u2(L);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,7 +156,6 @@ void layout_tucker4d(const Tucker4& tk, const int n[3], int n_dir, Layout& L) {
   for (int i = 0; i < 4; ++i) L.rank[i] = tk.r[i];
   for (int i = 0; i < 3; ++i) L.mean_rank[i] = tk.r[i];
   finish_ranks(L);
-  fold_u2(L);
 }
 
 // ---------------------------------------------------------------------------
@@ -233,7 +204,6 @@ void layout_htucker(const HTucker4& ht, const int n[3], int n_dir, Layout& L) {
   for (int i = 0; i < 6; ++i) L.rank[i] = ht.r[i];
   for (int i = 0; i < 3; ++i) L.mean_rank[i] = ht.r[i];
   finish_ranks(L);
-  fold_u2(L);
 }
 
 // ---------------------------------------------------------------------------

@@ -68,11 +68,11 @@ struct YZParams {
   long long slot_elems;
 };
 
-// Persistent batch mode of the x and yz kernels (batch_launch.cu): the
-// launch walks the work items of several instances of one shape class,
-// items item0 .. next item0 - 1 belonging to the instance; a block copies
-// the instance's parameters to shared memory and runs the same per-item code
-// as a single translation.
+// Batch mode of the x and yz kernels (batch_launch.cu): one launch covers
+// the work items of several instances of one shape class, items item0 ..
+// next item0 - 1 belonging to the instance; a block finds its item's
+// instance (a hint table, then a short scan), takes its parameters and runs
+// the same per-item code as a single translation.
 struct BatchX {
   XPassParams P;
   long long item0;
@@ -167,28 +167,46 @@ __device__ __forceinline__ void xfwd_body(const XPassParams& P, int item, unsign
   }
 }
 
-// One item per block, or (inst != null) the persistent batch mode.
 template <typename R, int N1>
-__global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P, const BatchX* __restrict__ inst, int ninst,
-                                                        long long total) {
+__global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (!inst) {
-    xfwd_body<R, N1>(P, blockIdx.x, smem_raw);
-    return;
-  }
-  // a block's items advance by gridDim.x: the instance is looked up only
-  // when an item leaves the current instance's range
-  long long lo = 1, hi = 0;
-  XPassParams Pi;
-  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    if (item < lo || item >= hi) {
-      const int i = find_instance(inst, ninst, item);
-      lo = inst[i].item0;
+  xfwd_body<R, N1>(P, blockIdx.x, smem_raw);
+}
+
+// Batch mode: block b takes item b of the launch's items.  Its instance: the
+// host's hint for item b / kHintStride (the instance holding that item),
+// advanced past the instances that start at or before b.
+constexpr int kHintShift = 8;                      // one hint per 256 items
+
+template <typename D>
+__device__ __forceinline__ int hinted_instance(const D* inst, const int* hint, int ninst, long long item) {
+  int i = hint[item >> kHintShift];
+  while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
+  return i;
+}
+
+// A block takes kXItems consecutive items (its instance looked up once, and
+// again only where an instance ends among them), which amortises the lookup
+// over several short items and keeps neighbouring blocks on neighbouring data.
+constexpr int kXItems = 4;
+
+template <typename R, int N1>
+__global__ void __launch_bounds__(kThreads) xfwd_batch_kernel(const BatchX* __restrict__ inst,
+                                                              const int* __restrict__ hint, int ninst,
+                                                              long long total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long first = (long long)blockIdx.x * kXItems;
+  int i = hinted_instance(inst, hint, ninst, first);
+  long long hi = i + 1 < ninst ? inst[i + 1].item0 : total;
+  XPassParams Pi = inst[i].P;
+  for (long long item = first; item < first + kXItems && item < total; ++item) {
+    if (item >= hi) {
+      while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
       hi = i + 1 < ninst ? inst[i + 1].item0 : total;
       Pi = inst[i].P;
     }
-    __syncthreads();                                 // the previous item is done with shared memory
-    xfwd_body<R, N1>(Pi, (int)(item - lo), smem_raw);
+    if (item > first) __syncthreads();               // the previous item is done with shared memory
+    xfwd_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
   }
 }
 
@@ -249,24 +267,28 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
 }
 
 template <typename R, int N1>
-__global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P, const BatchX* __restrict__ inst, int ninst,
-                                                        long long total) {
+__global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (!inst) {
-    xinv_body<R, N1>(P, blockIdx.x, smem_raw);
-    return;
-  }
-  long long lo = 1, hi = 0;                          // as in xfwd_kernel
-  XPassParams Pi;
-  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    if (item < lo || item >= hi) {
-      const int i = find_instance(inst, ninst, item);
-      lo = inst[i].item0;
+  xinv_body<R, N1>(P, blockIdx.x, smem_raw);
+}
+
+template <typename R, int N1>
+__global__ void __launch_bounds__(kThreads) xinv_batch_kernel(const BatchX* __restrict__ inst,
+                                                              const int* __restrict__ hint, int ninst,
+                                                              long long total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long first = (long long)blockIdx.x * kXItems;    // as in xfwd_batch_kernel
+  int i = hinted_instance(inst, hint, ninst, first);
+  long long hi = i + 1 < ninst ? inst[i + 1].item0 : total;
+  XPassParams Pi = inst[i].P;
+  for (long long item = first; item < first + kXItems && item < total; ++item) {
+    if (item >= hi) {
+      while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
       hi = i + 1 < ninst ? inst[i + 1].item0 : total;
       Pi = inst[i].P;
     }
-    __syncthreads();                                 // the previous item is done with shared memory
-    xinv_body<R, N1>(Pi, (int)(item - lo), smem_raw);
+    if (item > first) __syncthreads();
+    xinv_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
   }
 }
 
@@ -504,9 +526,9 @@ constexpr size_t kTcGemmSmem = 56 * 1024;
 // contraction chunk of the CUDA-core TT-like slab restore (slab_tt_chunked)
 constexpr int kRestoreKC = 64;
 // complex K per staged tensor-core chunk in the large-plane kernel: its field
-// plane already takes more shared memory than the 64 KB of staging, so the
+// plane already takes more shared memory than the operand staging, so the
 // longer chunk (half the round trips of the fused kernel's 16) costs no
-// occupancy
+// occupancy (48 measured no faster on the 256 x 64 planes)
 constexpr int kTcKCLarge = 32;
 
 template <bool BF16>   // BF16: BF16x3 products, else 3xTF32 (single TF32 with `single`)
@@ -743,7 +765,7 @@ __device__ __forceinline__ void yz_body(const YZParams& P, int x, int p, unsigne
   yz_fields<R, N2, N3, LY::G, false>(P, x, p, plane, xs, tw2, tw3, Tt, 1, PY);
 }
 
-// One (x, p) item per block, or (inst != null) the persistent batch mode over
+// One (x, p) item per block, or (inst != null) the batch mode over
 // the items (instance, x, p), p-major, of instances of this shape class.
 template <typename R, int N2, int N3, int FMT, int TC>   // TC: 0 CUDA cores, 1 3xTF32, 2 BF16x3
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yz_kernel(YZParams P, const BatchYZ* __restrict__ inst, int ninst,
@@ -801,7 +823,8 @@ struct YZLLayout {
   static constexpr size_t plane_elems = (size_t)(N3 / 2) * PY + kWarps * XW;
   static size_t smem_bytes(int fmt, bool tc) {
     size_t work = sizeof(cx<R>) * plane_elems;
-    if (fmt != 0 && tc && tc_smem_bytes<kTcKCLarge>() > work) work = tc_smem_bytes<kTcKCLarge>();
+    constexpr size_t kStage = tc_smem_bytes<kTcKCLarge>();
+    if (fmt != 0 && tc && kStage > work) work = kStage;
     return sizeof(cx<R>) * (N2 + N3) + work;
   }
   // global scratch per block: the slab, then G (rb x N2) of the Tucker-like
@@ -897,25 +920,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
     if (!tc.ok && tid == 0) atomicOr(P.status, kStatusTcTimeout);
     tc_teardown(tc);
   }
-}
-
-// Blocks of a persistent batch launch of `kern`: the SMs times the blocks
-// its shared memory allows (at most four with a tensor-core restore: each
-// block holds 128 of an SM's 512 TMEM columns), at most `total`.
-template <typename K>
-int persistent_grid(K kern, size_t smem, bool tc, long long total) {
-  int dev = 0, sms = 0, per = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    sms = 1;
-    per = 1;
-  }
-  if (per < 1) per = 1;
-  if (tc && per > 4) per = 4;
-  const long long g = (long long)sms * per;
-  return (int)(g < total ? g : total);
 }
 
 }  // namespace fmm

@@ -44,47 +44,47 @@ static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s)
   if (fwd) {
     cudaError_t e = smem_optin((const void*)xfwd_kernel<R, N1>, optin_f);
     if (e != cudaSuccess) return e;
-    xfwd_kernel<R, N1><<<grid, kThreads, smem, s>>>(P, nullptr, 0, 0);
+    xfwd_kernel<R, N1><<<grid, kThreads, smem, s>>>(P);
   } else {
     cudaError_t e = smem_optin((const void*)xinv_kernel<R, N1>, optin_i);
     if (e != cudaSuccess) return e;
-    xinv_kernel<R, N1><<<grid, kThreads, smem, s>>>(P, nullptr, 0, 0);
+    xinv_kernel<R, N1><<<grid, kThreads, smem, s>>>(P);
   }
   return cudaGetLastError();
 }
 
-// Persistent batch mode of the x passes over `total` items of `ninst`
-// instances with this n1 (float).
+// Batch mode of the x passes over the `total` items of `ninst` instances with
+// this n1 (float), kXItems consecutive items per block.
 template <int N1>
-static cudaError_t launch_x_batch_inst(bool fwd, const BatchX* inst, int ninst, long long total, size_t smem,
-                                       cudaStream_t s) {
+static cudaError_t launch_x_batch_inst(bool fwd, const BatchX* inst, const int* hint, int ninst, long long total,
+                                       size_t smem, cudaStream_t s) {
   static std::atomic<int> optin_f[kMaxDevices], optin_i[kMaxDevices];
-  XPassParams none;
-  std::memset(&none, 0, sizeof(none));
+  const long long blocks = (total + kXItems - 1) / kXItems;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (fwd) {
-    auto kern = xfwd_kernel<float, N1>;
+    auto kern = xfwd_batch_kernel<float, N1>;
     cudaError_t e = smem_optin((const void*)kern, optin_f);
     if (e != cudaSuccess) return e;
-    kern<<<persistent_grid(kern, smem, false, total), kThreads, smem, s>>>(none, inst, ninst, total);
+    kern<<<(unsigned)blocks, kThreads, smem, s>>>(inst, hint, ninst, total);
   } else {
-    auto kern = xinv_kernel<float, N1>;
+    auto kern = xinv_batch_kernel<float, N1>;
     cudaError_t e = smem_optin((const void*)kern, optin_i);
     if (e != cudaSuccess) return e;
-    kern<<<persistent_grid(kern, smem, false, total), kThreads, smem, s>>>(none, inst, ninst, total);
+    kern<<<(unsigned)blocks, kThreads, smem, s>>>(inst, hint, ninst, total);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, int ninst, long long total, size_t smem,
-                           cudaStream_t s) {
+cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, const int* hint, int ninst, long long total,
+                           size_t smem, cudaStream_t s) {
   switch (n1) {
-    case 4: return launch_x_batch_inst<4>(fwd, inst, ninst, total, smem, s);
-    case 8: return launch_x_batch_inst<8>(fwd, inst, ninst, total, smem, s);
-    case 16: return launch_x_batch_inst<16>(fwd, inst, ninst, total, smem, s);
-    case 32: return launch_x_batch_inst<32>(fwd, inst, ninst, total, smem, s);
-    case 64: return launch_x_batch_inst<64>(fwd, inst, ninst, total, smem, s);
-    case 128: return launch_x_batch_inst<128>(fwd, inst, ninst, total, smem, s);
-    case 256: return launch_x_batch_inst<256>(fwd, inst, ninst, total, smem, s);
+    case 4: return launch_x_batch_inst<4>(fwd, inst, hint, ninst, total, smem, s);
+    case 8: return launch_x_batch_inst<8>(fwd, inst, hint, ninst, total, smem, s);
+    case 16: return launch_x_batch_inst<16>(fwd, inst, hint, ninst, total, smem, s);
+    case 32: return launch_x_batch_inst<32>(fwd, inst, hint, ninst, total, smem, s);
+    case 64: return launch_x_batch_inst<64>(fwd, inst, hint, ninst, total, smem, s);
+    case 128: return launch_x_batch_inst<128>(fwd, inst, hint, ninst, total, smem, s);
+    case 256: return launch_x_batch_inst<256>(fwd, inst, hint, ninst, total, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,8 +7,8 @@
 
 namespace fmm {
 
-// Single translation (inst = null, the given grid) or persistent batch
-// (inst, ninst instances of this shape class, `total` items; grid chosen here).
+// Single translation (inst = null, the given grid) or batch mode (inst, ninst
+// instances of this shape class, `total` items, one block per item).
 template <typename R, int N2, int N3, int FMT, int TC>
 cudaError_t launch_yz_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t s, const BatchYZ* inst = nullptr,
                          int ninst = 0, long long total = 0) {
@@ -16,7 +16,11 @@ cudaError_t launch_yz_tc(const YZParams& P, dim3 grid, size_t smem, cudaStream_t
   auto kern = yz_kernel<R, N2, N3, FMT, TC>;
   cudaError_t e = smem_optin((const void*)kern, optin);
   if (e != cudaSuccess) return e;
-  if (inst) grid = dim3((unsigned)persistent_grid(kern, smem, FMT != 0 && TC != 0, total));
+  // batch mode: one block per item (the kernel's item loop runs once)
+  if (inst) {
+    if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+    grid = dim3((unsigned)total);
+  }
   kern<<<grid, kThreads, smem, s>>>(P, inst, ninst, total);
   return cudaGetLastError();
 }

@@ -1,7 +1,7 @@
 """GPU checks of the batch API: several independent plans with uneven grids,
 multipole counts, formats and RHS counts translated by one call.  Complex64
-instances run in persistent launches shared by all instances of a shape
-class (one launch per phase and class); complex128 ones run their own
+instances run in launches shared by all instances of a shape class (one
+launch per phase and class); complex128 ones run their own
 launches on internal streams.  Repeated calls with the same buffers are
 captured once as a CUDA graph and replayed.  Every instance must equal its
 own fmmfft_translate result exactly (same device code, same inputs) on the
@@ -105,12 +105,11 @@ def test_batch_rejects_bad_arguments(native, cuda):
         F.fmmfft_plan_destroy(h)
 
 
-def test_persistent_batch_of_uneven_instances(native, cuda, monkeypatch):
+def test_shared_launch_batch_of_uneven_instances(native, cuda, monkeypatch):
     """20 instances of uneven grids (K_i drawn from 8..24 per axis, so FFT
     extents 16, 32 or 64), multipole counts L in 1..4, Tucker-3D at tol 1e-4
     with 3xTF32 or FP32 restores, H-Tucker and plain operators, 1..3 RHS: all
-    of them run in the shared persistent launches (one per phase and shape
-    class), equal their own single translations bit for bit, equal the batch
+    of them run in the shared launches (one per phase and shape class), equal their own single translations bit for bit, equal the batch
     with one launch sequence per instance (FMMFFT_BATCH_SEPARATE=1) bit for
     bit, and sampled fields lie within tol + 1e-5 (plain: 2e-6) of the
     oracle's FP64 translation."""
@@ -140,7 +139,7 @@ def test_persistent_batch_of_uneven_instances(native, cuda, monkeypatch):
                 refs.append(ref)
         stream.synchronize()
         outs = {}
-        for mode in ("persistent", "separate"):
+        for mode in ("shared", "separate"):
             monkeypatch.setenv("FMMFFT_BATCH_SEPARATE", "1" if mode == "separate" else "0")
             b = F.fmmfft_batch_create(plans)
             try:
@@ -152,11 +151,11 @@ def test_persistent_batch_of_uneven_instances(native, cuda, monkeypatch):
                         assert F.fmmfft_poll_status(h) == 0
                         assert torch.equal(y, ref), (mode, call)
                 shared = F.fmmfft_batch_shared_count(b)
-                assert shared == (len(plans) if mode == "persistent" else 0), shared
+                assert shared == (len(plans) if mode == "shared" else 0), shared
                 outs[mode] = [y.clone() for y in ys]
             finally:
                 F.fmmfft_batch_destroy(b)
-        for a, c in zip(outs["persistent"], outs["separate"]):
+        for a, c in zip(outs["shared"], outs["separate"]):
             assert torch.equal(a, c)
         # sampled instances against the oracle's uncompressed FP64 translation
         from oracle import translate as tr
@@ -164,7 +163,7 @@ def test_persistent_batch_of_uneven_instances(native, cuda, monkeypatch):
             K, L, fmt, dec, tol, prec, r = specs[i]
             plan = pl.Plan(K=K, L=L)
             S = xs[i].cpu().numpy().astype(np.complex128)
-            out = outs["persistent"][i].cpu().numpy().astype(np.complex128)
+            out = outs["shared"][i].cpu().numpy().astype(np.complex128)
             dirs = [0, plan.n_dir - 1]
             got, want = [], []
             for p in dirs:

@@ -45,8 +45,7 @@ def _rel(a, b):
     ("4d", "htucker", (6, 5, 7), 3, 1e-4),
     ("4d", "tucker", (8, 8, 8), 4, 1e-3),
     ("4d", "htucker", (8, 8, 8), 4, 1e-3),
-    # y-z planes of 128 x 128: the schedule moves the U2 product into the
-    # pre-pass (H2_p[x] = U2 H_p[x]) and restores TT-like slabs
+    # y-z planes of 128 x 128 (the large-plane kernel's restore schedule)
     ("3d", "tucker", (3, 64, 64), 1, 1e-4),
     ("4d", "htucker", (3, 64, 64), 1, 1e-3),
 ])
