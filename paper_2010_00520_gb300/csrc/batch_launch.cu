@@ -28,8 +28,7 @@
 
 namespace fmm {
 
-cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, const int* hint, int ninst, long long total,
-                           size_t smem, cudaStream_t s);
+cudaError_t launch_x_batch(bool fwd, int n1, const BatchXTable& T, long long total, size_t smem, cudaStream_t s);
 void x_pass_shape(int n1, int rows, int mult, int* rpb, size_t* smem);
 cudaError_t launch_yz_batch(int fmt, const YZParams& P, int n2, int n3, size_t smem, cudaStream_t s,
                             const BatchYZ* inst, int ninst, long long total);
@@ -37,6 +36,26 @@ cudaError_t launch_yz_batch(int fmt, const YZParams& P, int n2, int n3, size_t s
 namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// One x-pass launch per kXTable instances of a class, each with its
+// instances' descriptors as launch parameters (items renumbered from 0).
+cudaError_t x_tables(bool fwd, int n1, const std::vector<BatchX>& d, long long total, size_t smem, cudaStream_t s) {
+  for (size_t i0 = 0; i0 < d.size(); i0 += kXTable) {
+    const size_t n = std::min<size_t>(kXTable, d.size() - i0);
+    BatchXTable T;
+    std::memset(&T, 0, sizeof(T));
+    const long long first = d[i0].item0;
+    const long long end = i0 + n < d.size() ? d[i0 + n].item0 : total;
+    for (size_t j = 0; j < n; ++j) {
+      T.inst[j] = d[i0 + j];
+      T.inst[j].item0 -= first;
+    }
+    T.ninst = (int)n;
+    cudaError_t e = launch_x_batch(fwd, n1, T, end - first, smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 struct Class {
   std::vector<BatchX> fwd, inv;
@@ -153,26 +172,9 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     std::memcpy(host.data() + at, p, bytes);
     return at;
   };
-  struct Off {
-    size_t fwd, inv, yz, hint;
-  };
-  std::vector<Off> off;
-  for (auto& kv : cls) {
-    Off o;
-    o.fwd = put(kv.second.fwd.data(), sizeof(BatchX) * kv.second.fwd.size());
-    o.inv = put(kv.second.inv.data(), sizeof(BatchX) * kv.second.inv.size());
-    o.yz = put(kv.second.yz.data(), sizeof(BatchYZ) * kv.second.yz.size());
-    // x-pass hints: the instance holding item k << kHintShift
-    const auto& f = kv.second.fwd;
-    std::vector<int> hint((size_t)((kv.second.x_total >> kHintShift) + 1), 0);
-    for (size_t k = 0, i = 0; k < hint.size(); ++k) {
-      const long long item = (long long)k << kHintShift;
-      while (i + 1 < f.size() && f[i + 1].item0 <= item) ++i;
-      hint[k] = (int)i;
-    }
-    o.hint = put(hint.data(), sizeof(int) * hint.size());
-    off.push_back(o);
-  }
+  // (the x passes' descriptors travel as launch parameters)
+  std::vector<size_t> off;
+  for (auto& kv : cls) off.push_back(put(kv.second.yz.data(), sizeof(BatchYZ) * kv.second.yz.size()));
   size_t n_gemm = 0;
   for (auto& m : merges) n_gemm += m.batch;
   const size_t o_gm = align_up(host.size(), 256);
@@ -240,16 +242,11 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     const int n1 = std::get<0>(kv.first), n2 = std::get<1>(kv.first), n3 = std::get<2>(kv.first);
     const int fmt = std::get<3>(kv.first);
     cudaStream_t l = lanes.empty() ? s : lanes[k % lanes.size()];
-    const int* hint = (const int*)(base + off[k].hint);
-    if ((e = launch_x_batch(true, n1, (const BatchX*)(base + off[k].fwd), hint, (int)c.fwd.size(), c.x_total,
-                            c.x_smem, l)) != cudaSuccess)
-      return e;
-    if ((e = launch_yz_batch(fmt, c.yz[0].P, n2, n3, c.yz_smem, l, (const BatchYZ*)(base + off[k].yz),
+    if ((e = x_tables(true, n1, c.fwd, c.x_total, c.x_smem, l)) != cudaSuccess) return e;
+    if ((e = launch_yz_batch(fmt, c.yz[0].P, n2, n3, c.yz_smem, l, (const BatchYZ*)(base + off[k]),
                              (int)c.yz.size(), c.yz_total)) != cudaSuccess)
       return e;
-    if ((e = launch_x_batch(false, n1, (const BatchX*)(base + off[k].inv), hint, (int)c.inv.size(), c.x_total,
-                            c.x_smem, l)) != cudaSuccess)
-      return e;
+    if ((e = x_tables(false, n1, c.inv, c.x_total, c.x_smem, l)) != cudaSuccess) return e;
     ++k;
   }
   return cudaSuccess;

@@ -71,8 +71,8 @@ struct YZParams {
 // Batch mode of the x and yz kernels (batch_launch.cu): one launch covers
 // the work items of several instances of one shape class, items item0 ..
 // next item0 - 1 belonging to the instance; a block finds its item's
-// instance (a hint table, then a short scan), takes its parameters and runs
-// the same per-item code as a single translation.
+// instance by bisection, takes its parameters and runs the same per-item
+// code as a single translation.
 struct BatchX {
   XPassParams P;
   long long item0;
@@ -173,41 +173,24 @@ __global__ void __launch_bounds__(kThreads) xfwd_kernel(XPassParams P) {
   xfwd_body<R, N1>(P, blockIdx.x, smem_raw);
 }
 
-// Batch mode: block b takes item b of the launch's items.  Its instance: the
-// host's hint for item b / kHintStride (the instance holding that item),
-// advanced past the instances that start at or before b.
-constexpr int kHintShift = 8;                      // one hint per 256 items
-
-template <typename D>
-__device__ __forceinline__ int hinted_instance(const D* inst, const int* hint, int ninst, long long item) {
-  int i = hint[item >> kHintShift];
-  while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
-  return i;
-}
-
-// A block takes kXItems consecutive items (its instance looked up once, and
-// again only where an instance ends among them), which amortises the lookup
-// over several short items and keeps neighbouring blocks on neighbouring data.
-constexpr int kXItems = 4;
+// Batch mode of the x passes: block b takes item b of the launch's items,
+// as a single translation's x pass does.  The instances' parameters travel
+// in the launch's own parameter space (constant bank), like a single
+// translation's, so the lookup is a few cached constant reads and the item
+// code reads its parameters from the same space; a class with more than
+// kXTable instances runs one launch per kXTable of them.
+constexpr int kXTable = 96;
+struct BatchXTable {
+  BatchX inst[kXTable];        // item0 relative to the launch's first item
+  int ninst;
+};
 
 template <typename R, int N1>
-__global__ void __launch_bounds__(kThreads) xfwd_batch_kernel(const BatchX* __restrict__ inst,
-                                                              const int* __restrict__ hint, int ninst,
-                                                              long long total) {
+__global__ void __launch_bounds__(kThreads) xfwd_batch_kernel(const __grid_constant__ BatchXTable T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long first = (long long)blockIdx.x * kXItems;
-  int i = hinted_instance(inst, hint, ninst, first);
-  long long hi = i + 1 < ninst ? inst[i + 1].item0 : total;
-  XPassParams Pi = inst[i].P;
-  for (long long item = first; item < first + kXItems && item < total; ++item) {
-    if (item >= hi) {
-      while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
-      hi = i + 1 < ninst ? inst[i + 1].item0 : total;
-      Pi = inst[i].P;
-    }
-    if (item > first) __syncthreads();               // the previous item is done with shared memory
-    xfwd_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
-  }
+  const long long item = blockIdx.x;
+  const int i = find_instance(T.inst, T.ninst, item);
+  xfwd_body<R, N1>(T.inst[i].P, (int)(item - T.inst[i].item0), smem_raw);
 }
 
 // Work item `item` of the inverse x pass (as xfwd_body).
@@ -273,23 +256,11 @@ __global__ void __launch_bounds__(kThreads) xinv_kernel(XPassParams P) {
 }
 
 template <typename R, int N1>
-__global__ void __launch_bounds__(kThreads) xinv_batch_kernel(const BatchX* __restrict__ inst,
-                                                              const int* __restrict__ hint, int ninst,
-                                                              long long total) {
+__global__ void __launch_bounds__(kThreads) xinv_batch_kernel(const __grid_constant__ BatchXTable T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long first = (long long)blockIdx.x * kXItems;    // as in xfwd_batch_kernel
-  int i = hinted_instance(inst, hint, ninst, first);
-  long long hi = i + 1 < ninst ? inst[i + 1].item0 : total;
-  XPassParams Pi = inst[i].P;
-  for (long long item = first; item < first + kXItems && item < total; ++item) {
-    if (item >= hi) {
-      while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
-      hi = i + 1 < ninst ? inst[i + 1].item0 : total;
-      Pi = inst[i].P;
-    }
-    if (item > first) __syncthreads();
-    xinv_body<R, N1>(Pi, (int)(item - inst[i].item0), smem_raw);
-  }
+  const long long item = blockIdx.x;                 // as in xfwd_batch_kernel
+  const int i = find_instance(T.inst, T.ninst, item);
+  xinv_body<R, N1>(T.inst[i].P, (int)(item - T.inst[i].item0), smem_raw);
 }
 
 // Shared memory of the x passes (bytes).

@@ -53,38 +53,36 @@ static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s)
   return cudaGetLastError();
 }
 
-// Batch mode of the x passes over the `total` items of `ninst` instances with
-// this n1 (float), kXItems consecutive items per block.
+// Batch mode of the x passes over the `total` items of the table's instances
+// with this n1 (float), one item per block.
 template <int N1>
-static cudaError_t launch_x_batch_inst(bool fwd, const BatchX* inst, const int* hint, int ninst, long long total,
-                                       size_t smem, cudaStream_t s) {
+static cudaError_t launch_x_batch_inst(bool fwd, const BatchXTable& T, long long total, size_t smem,
+                                       cudaStream_t s) {
   static std::atomic<int> optin_f[kMaxDevices], optin_i[kMaxDevices];
-  const long long blocks = (total + kXItems - 1) / kXItems;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (fwd) {
     auto kern = xfwd_batch_kernel<float, N1>;
     cudaError_t e = smem_optin((const void*)kern, optin_f);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, kThreads, smem, s>>>(inst, hint, ninst, total);
+    kern<<<(unsigned)total, kThreads, smem, s>>>(T);
   } else {
     auto kern = xinv_batch_kernel<float, N1>;
     cudaError_t e = smem_optin((const void*)kern, optin_i);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, kThreads, smem, s>>>(inst, hint, ninst, total);
+    kern<<<(unsigned)total, kThreads, smem, s>>>(T);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_x_batch(bool fwd, int n1, const BatchX* inst, const int* hint, int ninst, long long total,
-                           size_t smem, cudaStream_t s) {
+cudaError_t launch_x_batch(bool fwd, int n1, const BatchXTable& T, long long total, size_t smem, cudaStream_t s) {
   switch (n1) {
-    case 4: return launch_x_batch_inst<4>(fwd, inst, hint, ninst, total, smem, s);
-    case 8: return launch_x_batch_inst<8>(fwd, inst, hint, ninst, total, smem, s);
-    case 16: return launch_x_batch_inst<16>(fwd, inst, hint, ninst, total, smem, s);
-    case 32: return launch_x_batch_inst<32>(fwd, inst, hint, ninst, total, smem, s);
-    case 64: return launch_x_batch_inst<64>(fwd, inst, hint, ninst, total, smem, s);
-    case 128: return launch_x_batch_inst<128>(fwd, inst, hint, ninst, total, smem, s);
-    case 256: return launch_x_batch_inst<256>(fwd, inst, hint, ninst, total, smem, s);
+    case 4: return launch_x_batch_inst<4>(fwd, T, total, smem, s);
+    case 8: return launch_x_batch_inst<8>(fwd, T, total, smem, s);
+    case 16: return launch_x_batch_inst<16>(fwd, T, total, smem, s);
+    case 32: return launch_x_batch_inst<32>(fwd, T, total, smem, s);
+    case 64: return launch_x_batch_inst<64>(fwd, T, total, smem, s);
+    case 128: return launch_x_batch_inst<128>(fwd, T, total, smem, s);
+    case 256: return launch_x_batch_inst<256>(fwd, T, total, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -176,3 +176,45 @@ def test_shared_launch_batch_of_uneven_instances(native, cuda, monkeypatch):
     finally:
         for h in plans:
             F.fmmfft_plan_destroy(h)
+
+
+def test_batch_class_larger_than_one_descriptor_table(native, cuda):
+    """130 small instances of one shape class (grids 5..8 per axis, so FFT
+    extents of 16, plain operator, L = 1): more instances than one x-pass
+    launch carries in its parameters, so the class's x passes run as several
+    launches.  Every instance equals its own translation bit for bit."""
+    F, torch = native, cuda
+    rng = np.random.default_rng(5)
+    plans, xs, refs, nrhs = [], [], [], []
+    stream = torch.cuda.Stream()
+    try:
+        for j in range(130):
+            K = tuple(int(k) for k in rng.integers(5, 9, size=3))
+            h = F.fmmfft_plan_create(*K, 0.5, TWO_PI, 1, 0, 0, 0.0)
+            F.fmmfft_compress(h)
+            plans.append(h)
+            r = 1 + j % 2
+            nd = F.fmmfft_plan_stats(h)["n_dir"]
+            xs.append(torch.from_numpy(field_spectra(900 + j, nd, r, K).astype(np.complex64)).to("cuda"))
+            nrhs.append(r)
+        with torch.cuda.stream(stream):
+            for h, x, r in zip(plans, xs, nrhs):
+                ref = torch.empty_like(x)
+                F.fmmfft_translate(h, x, ref, r, stream)
+                refs.append(ref)
+        stream.synchronize()
+        b = F.fmmfft_batch_create(plans)
+        try:
+            ys = [torch.full_like(x, float("nan")) for x in xs]
+            for call in range(2):
+                F.fmmfft_batch_translate(b, xs, ys, nrhs, stream)
+                stream.synchronize()
+                assert F.fmmfft_batch_shared_count(b) == len(plans)
+                for h, y, ref in zip(plans, ys, refs):
+                    assert F.fmmfft_poll_status(h) == 0
+                    assert torch.equal(y, ref), call
+        finally:
+            F.fmmfft_batch_destroy(b)
+    finally:
+        for h in plans:
+            F.fmmfft_plan_destroy(h)
