@@ -67,8 +67,9 @@ DEFAULT_WL = "tucker3d_128x128x32_L6_tol1e-4_2pol_16rhs"
 FORMAT_NAMES = {(3, 1): "tucker3d", (3, 2): "tt3d", (4, 1): "tucker4d", (4, 2): "tt4d", (4, 3): "htucker4d",
                 (0, 0): "none"}
 FAR_NB = 16                  # basis functions per box of the far-field steps (Eqs. 4, 6)
-# version of the yz kernels the committed DRAM-traffic figures were taken on
-YZ_KERNEL_VERSION = 6
+# version of each yz kernel's code the committed DRAM-traffic figures were
+# taken on (a figure counts only while its kernel is unchanged)
+YZ_KERNEL_VERSION = {"yz_kernel": 6, "yzl_kernel": 6}
 
 
 def workload(name: str) -> dict:
@@ -821,7 +822,7 @@ def main():
         with open(prof) as f:
             tj = json.load(f)
         # counters only count for the kernel and launch they were taken on
-        if (tj.get("kernel_version") == YZ_KERNEL_VERSION and nrhs == W["nrhs"]
+        if (tj.get("kernel_version") == YZ_KERNEL_VERSION[kname] and nrhs == W["nrhs"]
                 and tj.get("restore_on_tensor_cores") == st.get("restore_on_tensor_cores")):
             traffic = tj.get("dram_bytes_per_launch")
     tc = int(st.get("restore_on_tensor_cores") or 0)

@@ -109,6 +109,7 @@ cudaError_t launch_translate_batch(const std::vector<TranslateArgs>& args, Batch
     c.fwd.push_back(f);
     c.inv.push_back(v);
     c.x_total += (long long)F * ((rows + X.rows_per_block - 1) / X.rows_per_block);
+    if (X.occ && X.rowocc) xs += xpass_mask_bytes(X.rows_per_block, X.Kx);
     c.x_smem = std::max(c.x_smem, xs);
     BatchYZ b;
     std::memset(&b, 0, sizeof(b));

@@ -25,6 +25,8 @@
 // with R_p = U3 of the direction (TT-3D) or the generated slice S_p^T (TT-4D).
 #pragma once
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "plan_internal.h"
 #include "tc_cgemm.cuh"
@@ -119,6 +121,13 @@ __device__ __forceinline__ void cp_async_elem(C* dst_smem, const C* src) {
 }
 __device__ __forceinline__ void cp_async_drain() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// With an occupancy mask an x-pass block stages its rows' flags after Q in
+// its dynamic shared memory: one byte per x-line (live[r]), then the box
+// flags of its rows (box[r Kx + x]).  Bytes, 16-byte multiple:
+inline size_t xpass_mask_bytes(int rows_per_block, int Kx) {
+  return ((size_t)rows_per_block * (1 + (size_t)Kx) + 15) / 16 * 16;
+}
+
 // Work item `item` (field item / row blocks, row block item % row blocks) of
 // the forward x pass, by the whole block; `smem_raw` holds xpass_smem bytes.
 template <typename R, int N1>
@@ -136,33 +145,51 @@ __device__ __forceinline__ void xfwd_body(const XPassParams& P, int item, unsign
   const C* src = reinterpret_cast<const C*>(P.src) + ((size_t)f * P.rows + r0) * P.Kx;
   C* dst = reinterpret_cast<C*>(P.dst);
   for (int i = threadIdx.x; i < N1; i += kThreads) tw[i] = reinterpret_cast<const C*>(P.tw)[i];
+  // occupancy mask: the block's x-line and box flags staged once (empty
+  // boxes read as zero; empty x-lines are not transformed and their spectra
+  // are written as zeros)
+  const bool masked = P.occ && P.rowocc;
+  unsigned char* live = reinterpret_cast<unsigned char*>(Q + (size_t)P.rows_per_block * PX);
+  unsigned char* box = live + P.rows_per_block;
+  if (masked) {
+    for (int i = threadIdx.x; i < nr; i += kThreads) live[i] = P.rowocc[r0 + i];
+    for (int i = threadIdx.x; i < nr * P.Kx; i += kThreads) box[i] = P.occ[(size_t)r0 * P.Kx + i];
+    __syncthreads();
+  }
   const int half = N1 / 2;
   // batches of kLd loads per thread are issued before their shared-memory
   // stores, so that several global loads are in flight per thread (the rows
-  // are contiguous here; asynchronous copies measured slower)
+  // are contiguous here; asynchronous copies measured slower).  The mask
+  // test is a compile-time branch of its own, so that the unmasked loads
+  // stay batched.
   constexpr int kLd = 8;
-  for (int i0 = threadIdx.x; i0 < nr * half; i0 += kLd * kThreads) {
-    C v[kLd];
+  auto load_rows = [&](auto mask_tag) {
+    constexpr bool kMask = decltype(mask_tag)::value;
+    for (int i0 = threadIdx.x; i0 < nr * half; i0 += kLd * kThreads) {
+      C v[kLd];
 #pragma unroll
-    for (int j = 0; j < kLd; ++j) {
-      const int i = i0 + j * kThreads;
-      const int r = i / half, x = i - r * half;
-      const bool in = i < nr * half && x < P.Kx;
-      v[j] = (in && (!P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x])) ? src[(size_t)r * P.Kx + x] : czero<C>();
-    }
+      for (int j = 0; j < kLd; ++j) {
+        const int i = i0 + j * kThreads;
+        const int r = i / half, x = i - r * half;
+        const bool in = i < nr * half && x < P.Kx && (!kMask || box[r * P.Kx + x]);
+        v[j] = in ? src[(size_t)r * P.Kx + x] : czero<C>();
+      }
 #pragma unroll
-    for (int j = 0; j < kLd; ++j) {
-      const int i = i0 + j * kThreads;
-      const int r = i / half, x = i - r * half;
-      if (i < nr * half) Q[r * PX + x] = v[j];
+      for (int j = 0; j < kLd; ++j) {
+        const int i = i0 + j * kThreads;
+        const int r = i / half, x = i - r * half;
+        if (i < nr * half) Q[r * PX + x] = v[j];
+      }
     }
-  }
+  };
+  if (masked) load_rows(std::true_type{});
+  else load_rows(std::false_type{});
   __syncthreads();
   TeamPos<N1> tp;
   C* xt = tp.xs(xs);
   for (int base = 0; base < nr; base += L::LPI) {
     const int line = base + tp.line;
-    const bool act = line < nr && (!P.rowocc || P.rowocc[r0 + line]);
+    const bool act = line < nr && (!masked || live[line]);
     line_fft<N1, -1, true>(Q + (line < nr ? line : 0) * PX, 1, xt, tw, tp.t, act, N1);
   }
   __syncthreads();
@@ -174,8 +201,8 @@ __device__ __forceinline__ void xfwd_body(const XPassParams& P, int item, unsign
   for (int i = threadIdx.x; i < (N1 << lg); i += kThreads) {
     const int x = i >> lg, r = i & (rp2 - 1);
     if (r >= nr) continue;
-    const bool live = !P.rowocc || P.rowocc[r0 + r];
-    dst[((size_t)f * N1 + x) * P.rows + r0 + r] = live ? Q[r * PX + x] : czero<C>();
+    const bool rl = !masked || live[r];
+    dst[((size_t)f * N1 + x) * P.rows + r0 + r] = rl ? Q[r * PX + x] : czero<C>();
   }
 }
 
@@ -221,6 +248,17 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
   const C* src = reinterpret_cast<const C*>(P.src);
   C* dst = reinterpret_cast<C*>(P.dst) + ((size_t)f * P.rows + r0) * P.Kx;
   for (int i = threadIdx.x; i < N1; i += kThreads) tw[i] = reinterpret_cast<const C*>(P.tw)[i];
+  // occupancy mask: the block's x-line and box flags staged once (empty
+  // x-lines are neither read nor transformed; empty boxes are written as
+  // zeros)
+  const bool masked = P.occ && P.rowocc;
+  unsigned char* live = reinterpret_cast<unsigned char*>(Q + (size_t)P.rows_per_block * PX);
+  unsigned char* box = live + P.rows_per_block;
+  if (masked) {
+    for (int i = threadIdx.x; i < nr; i += kThreads) live[i] = P.rowocc[r0 + i];
+    for (int i = threadIdx.x; i < nr * P.Kx; i += kThreads) box[i] = P.occ[(size_t)r0 * P.Kx + i];
+    __syncthreads();
+  }
   // (x, r) by shift and mask over the power of two rp2 >= rows per block;
   // every load of the block issued at once as an asynchronous copy into its
   // place in Q, then drained: the block reads n1 runs of its rows, one per
@@ -230,10 +268,8 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
   const int rp2 = 1 << lg;
   for (int i = threadIdx.x; i < (N1 << lg); i += kThreads) {
     const int x = i >> lg, r = i & (rp2 - 1);
-    if (r >= nr) continue;
-    C* d = Q + r * PX + x;
-    if (!P.rowocc || P.rowocc[r0 + r]) cp_async_elem(d, src + ((size_t)f * N1 + x) * P.rows + r0 + r);
-    else *d = czero<C>();
+    if (r >= nr || (masked && !live[r])) continue;      // an empty line is not transformed
+    cp_async_elem(Q + r * PX + x, src + ((size_t)f * N1 + x) * P.rows + r0 + r);
   }
   cp_async_drain();
   __syncthreads();
@@ -241,7 +277,7 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
   C* xt = tp.xs(xs);
   for (int base = 0; base < nr; base += L::LPI) {
     const int line = base + tp.line;
-    const bool act = line < nr && (!P.rowocc || P.rowocc[r0 + line]);
+    const bool act = line < nr && (!masked || live[line]);
     line_fft<N1, +1, false>(Q + (line < nr ? line : 0) * PX, 1, xt, tw, tp.t, act, P.Kx);
   }
   __syncthreads();
@@ -249,7 +285,7 @@ __device__ __forceinline__ void xinv_body(const XPassParams& P, int item, unsign
   const int lane = threadIdx.x & 31;
   for (int r = threadIdx.x >> 5; r < nr; r += kWarps)
     for (int x = lane; x < P.Kx; x += 32) {
-      const bool occupied = !P.occ || P.occ[(size_t)(r0 + r) * P.Kx + x];
+      const bool occupied = !masked || box[r * P.Kx + x];
       dst[(size_t)r * P.Kx + x] = occupied ? Q[r * PX + x] : czero<C>();
     }
 }
@@ -279,7 +315,7 @@ constexpr size_t xpass_smem(int rows_per_block) {
 // the rows of a field.
 template <typename R, int N1>
 inline int xpass_rows_per_block(int rows, int mult) {
-  int rpb = (mult > 0 ? mult : 2) * Line<N1>::LPI;
+  int rpb = (mult == 1 || mult == 2 || mult == 4 ? mult : 2) * Line<N1>::LPI;
   while (rpb > Line<N1>::LPI && xpass_smem<R, N1>(rpb) > 96 * 1024) rpb /= 2;
   return rpb < rows ? rpb : rows;
 }

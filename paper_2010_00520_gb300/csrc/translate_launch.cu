@@ -39,7 +39,8 @@ template <typename R, int N1>
 static cudaError_t launch_x_inst(bool fwd, XPassParams P, int F, cudaStream_t s) {
   static std::atomic<int> optin_f[kMaxDevices], optin_i[kMaxDevices];
   P.rows_per_block = xpass_rows_per_block<R, N1>(P.rows, P.rows_per_block);
-  const size_t smem = xpass_smem<R, N1>(P.rows_per_block);
+  const size_t smem =
+      xpass_smem<R, N1>(P.rows_per_block) + (P.occ && P.rowocc ? xpass_mask_bytes(P.rows_per_block, P.Kx) : 0);
   dim3 grid((unsigned)(((P.rows + P.rows_per_block - 1) / P.rows_per_block) * (size_t)F));
   if (fwd) {
     cudaError_t e = smem_optin((const void*)xfwd_kernel<R, N1>, optin_f);
