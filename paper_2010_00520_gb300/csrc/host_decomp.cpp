@@ -11,7 +11,10 @@ namespace fmm {
 // ---------------------------------------------------------------------------
 
 // Implicit-shift QL iterations on the real symmetric tridiagonal matrix with
-// diagonal d[0..n) and off-diagonal e[i] = T[i+1][i] (e[n-1] unused); the
+// diagonal d[0..n) and off-diagonal e[i] = T[i+1][i] (e[n-1] unused), the
+// published method of Bowdler, Martin, Reinsch and Wilkinson ("The QR and QL
+// algorithms for symmetric matrices", Numer. Math. 11, 1968): Wilkinson-type
+// shift from the trailing 2 x 2 block, a chain of plane rotations per sweep; the
 // rotations are accumulated into the eigenvector matrix, stored transposed
 // (Zt[j] is eigenvector j, contiguous) so that a rotation of two vectors
 // touches two contiguous rows.  The rotations of one iteration are recorded
