@@ -193,18 +193,24 @@ struct TcState {
   uint32_t phase;      // parity of the next mbarrier phase
   bool ok;             // false once a wait ran out (results invalid)
   bool single;         // 3xTF32 path: one TF32 product (big x big) only
+  uint32_t mbar2;      // second mbarrier (pipelined GEMM: odd chunks), 0 if none
+  uint32_t phase2;     // parity of its next phase
 };
 
 // Block-wide set-up: `buf` (kTcSmemBytes, 16-byte aligned) holds the operand
 // chunks, `bar` is the mbarrier (8 bytes of shared memory that nothing else
-// uses while the state lives) and `slot` receives the TMEM address.  Warp 0
+// uses while the state lives; `bar2` a second one for tc_cgemm64_pipe) and
+// `slot` receives the TMEM address.  Warp 0
 // allocates kTcCols columns.  All threads call it.
-__device__ __forceinline__ TcState tc_setup(void* buf, uint64_t* bar, uint32_t* slot) {
+__device__ __forceinline__ TcState tc_setup(void* buf, uint64_t* bar, uint32_t* slot, uint64_t* bar2 = nullptr) {
   TcState s;
   s.buf = reinterpret_cast<float*>(buf);
   s.mbar = smem_u32(bar);
+  s.mbar2 = bar2 ? smem_u32(bar2) : 0u;
+  s.phase2 = 0;
   if (threadIdx.x == 0) {
     mbar_init(s.mbar, 1);
+    if (bar2) mbar_init(s.mbar2, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, kTcCols);
@@ -486,6 +492,174 @@ __device__ __forceinline__ void tc_cgemm64(TcState& s, int M, int N, int K, FA a
     s.phase ^= 1u;
     tc_fence_after();
   }
+  tc_epilogue<C_GLOBAL>(s, M, N, C, ldc, scale);
+}
+
+// one complex element (8 bytes) global -> shared, asynchronously; valid =
+// false reads nothing and writes zeros
+__device__ __forceinline__ void cp_async8_zfill(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_groups() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined complex 64 x 64 tile (3xTF32 or BF16x3) for long contractions:
+// chunks of kPipeK complex K; the raw FP32 operands of chunk ch + 1 are
+// copied (cp.async) into one of two ring stages while chunk ch is split, and
+// the split goes to one of two staging buffers, so that chunk ch's split
+// overlaps chunk ch - 1's MMAs.  Chunk ch's MMAs commit to mbarrier
+// (ch even ? s.mbar : s.mbar2); a staging buffer is reused only after the
+// MMAs that read it (two chunks earlier) have completed.  A and B are given
+// by base pointers and element strides in global memory: A(m, k) =
+// A[m am + k ak] (M x K), B(k, n) = B[k bk + n bn] (K x N); elements outside
+// M, N or K are zero-filled by the copies.  Ring rows hold kPipeK complex k,
+// XOR-swizzled by the row so that the split's reads (8 rows x 4 k per warp)
+// and the copies spread over the banks.  Shared memory: s.buf holds the two
+// staging buffers (tc_pipe_staging_bytes) and `ring` kPipeRingBytes; s.mbar2
+// must be set up.  All threads call it.
+// ---------------------------------------------------------------------------
+constexpr int kPipeK = 16;
+constexpr size_t kPipeRingBytes = 2 * 2 * 64 * (size_t)kPipeK * sizeof(float2);
+template <bool BF16>
+constexpr size_t tc_pipe_staging_bytes() {
+  return 2 * 4 * 128 * (size_t)(BF16 ? kPipeK / 2 : kPipeK) * sizeof(uint32_t);
+}
+
+template <bool C_GLOBAL, bool BF16>
+__device__ __forceinline__ void tc_cgemm64_pipe(TcState& s, float2* ring, int M, int N, int K, const float2* A,
+                                                long long am, long long ak, const float2* B, long long bk,
+                                                long long bn, float2* C, int ldc, float scale) {
+  constexpr int KE = kPipeK;                        // complex K per chunk
+  constexpr int KCW = BF16 ? KE / 2 : KE;           // staging words per row
+  constexpr int kTile = 128 * KCW;                  // words per operand part
+  constexpr int kStage = 2 * 64 * KE;               // float2 per ring stage
+  constexpr uint32_t idesc = BF16 ? tc_idesc_bf16_128x128() : tc_idesc_tf32_128x128();
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nchunks = (K + KE - 1) / KE;
+  uint32_t* stg0 = reinterpret_cast<uint32_t*>(s.buf);
+  auto swz = [](int m, int k) { return m * KE + (k ^ ((m & 3) << 2)); };
+  const bool a_rows = am == 1, b_rows = bn == 1;
+  auto issue = [&](int ch) {
+    if (ch < nchunks) {
+      float2* ra = ring + (ch & 1) * kStage;
+      float2* rb = ra + 64 * KE;
+      const int k0 = ch * KE;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = tid + 256 * j, bw = e >> 5;
+        const int mr = (bw & 7) * 8 + (lane & 7), kr = (bw >> 3) * 4 + (lane >> 3);
+        const int mc = e >> 4, kc = e & 15;
+        {
+          const int m = a_rows ? mr : mc, k = a_rows ? kr : kc;
+          const bool v = m < M && k0 + k < K;
+          cp_async8_zfill(ra + swz(m, k), v ? A + m * am + (long long)(k0 + k) * ak : A, v);
+        }
+        {
+          const int n = b_rows ? mr : mc, k = b_rows ? kr : kc;
+          const bool v = n < N && k0 + k < K;
+          cp_async8_zfill(rb + swz(n, k), v ? B + (long long)(k0 + k) * bk + n * bn : B, v);
+        }
+      }
+    }
+    cp_async_commit();                              // one group per chunk, empty or not
+  };
+  // wait for the MMAs of chunk c (the last commit on its mbarrier)
+  auto wait_chunk = [&](int c) {
+    const uint32_t bar = (c & 1) ? s.mbar2 : s.mbar;
+    uint32_t& ph = (c & 1) ? s.phase2 : s.phase;
+    bool timeout = false;
+    if (tid < 32) timeout = !mbar_wait(bar, ph);
+    if (__syncthreads_or(timeout)) s.ok = false;
+    ph ^= 1u;
+    tc_fence_after();
+  };
+  issue(0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    issue(ch + 1);                                  // into the stage chunk ch - 1 was split from
+    cp_async_wait_groups<1>();                      // this thread's copies of chunk ch
+    if (ch >= 2) {
+      wait_chunk(ch - 2);                           // its staging buffer is free again
+    } else {
+      __syncthreads();                              // every thread's copies of chunk ch landed
+    }
+    const float2* ra = ring + (ch & 1) * kStage;
+    const float2* rb = ra + 64 * KE;
+    uint32_t* Ab = stg0 + (ch & 1) * 4 * kTile;
+    uint32_t* As = Ab + kTile;
+    uint32_t* Bb = As + kTile;
+    uint32_t* Bs = Bb + kTile;
+#pragma unroll
+    for (int j = 0; j < 64 * KCW / 256; ++j) {
+      const int i = tid + 256 * j;
+      const int cm = i >> 5, w = i & 31;
+      const int m = (cm / (KCW / 4)) * 8 + (w >> 2);
+      const int kw = (cm % (KCW / 4)) * 4 + (w & 3);
+      const int o0 = i, o1 = o0 + 64 * KCW;
+      if constexpr (BF16) {
+        const float2 a0 = ra[swz(m, 2 * kw)], a1 = ra[swz(m, 2 * kw + 1)];
+        const float2 b0 = rb[swz(m, 2 * kw)], b1 = rb[swz(m, 2 * kw + 1)];
+        uint32_t hi, lo;
+        bf16_split2(a0.x, a1.x, hi, lo);
+        Ab[o0] = hi;
+        As[o0] = lo;
+        bf16_split2(a0.y, a1.y, hi, lo);
+        Ab[o1] = hi;
+        As[o1] = lo;
+        bf16_split2(b0.x, b1.x, hi, lo);
+        Bb[o0] = hi;
+        Bs[o0] = lo;
+        bf16_split2(b0.y, b1.y, hi, lo);
+        Bb[o1] = hi;
+        Bs[o1] = lo;
+      } else {
+        const float2 a = ra[swz(m, kw)], b = rb[swz(m, kw)];
+        const uint32_t arb = to_tf32(a.x), aib = to_tf32(a.y);
+        const uint32_t brb = to_tf32(b.x), bib = to_tf32(b.y);
+        Ab[o0] = arb;
+        Ab[o1] = aib;
+        Bb[o0] = brb;
+        Bb[o1] = bib;
+        if (!s.single) {
+          As[o0] = to_tf32(a.x - __uint_as_float(arb));
+          As[o1] = to_tf32(a.y - __uint_as_float(aib));
+          Bs[o0] = to_tf32(b.x - __uint_as_float(brb));
+          Bs[o1] = to_tf32(b.y - __uint_as_float(bib));
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ab = smem_u32(Ab), as = smem_u32(As), bb = smem_u32(Bb), bs = smem_u32(Bs);
+#pragma unroll
+      for (int ks = 0; ks < KCW / 8; ++ks) {
+        const uint32_t step = ks * 2 * 128;         // two core matrices along K
+        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+        if constexpr (BF16) {
+          tc_mma_bf16(s.tmem, tc_desc<KCW>(ab + step), tc_desc<KCW>(bb + step), idesc, acc0);
+          tc_mma_bf16(s.tmem, tc_desc<KCW>(as + step), tc_desc<KCW>(bb + step), idesc, 1u);
+          tc_mma_bf16(s.tmem, tc_desc<KCW>(ab + step), tc_desc<KCW>(bs + step), idesc, 1u);
+        } else {
+          tc_mma(s.tmem, tc_desc<KCW>(ab + step), tc_desc<KCW>(bb + step), idesc, acc0);
+          if (!s.single) {
+            tc_mma(s.tmem, tc_desc<KCW>(as + step), tc_desc<KCW>(bb + step), idesc, 1u);
+            tc_mma(s.tmem, tc_desc<KCW>(ab + step), tc_desc<KCW>(bs + step), idesc, 1u);
+          }
+        }
+      }
+      tc_commit((ch & 1) ? s.mbar2 : s.mbar);
+    }
+  }
+  cp_async_wait_groups<0>();                        // no copy left in flight
+  if (nchunks >= 2) wait_chunk(nchunks - 2);
+  if (nchunks >= 1) wait_chunk(nchunks - 1);
   tc_epilogue<C_GLOBAL>(s, M, N, C, ldc, scale);
 }
 

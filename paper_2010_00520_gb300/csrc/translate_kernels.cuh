@@ -537,11 +537,27 @@ __device__ __forceinline__ void yz_fields(const YZParams& P, int x, int p, cx<R>
 constexpr size_t kTcGemmSmem = 56 * 1024;
 // contraction chunk of the CUDA-core TT-like slab restore (slab_tt_chunked)
 constexpr int kRestoreKC = 64;
-// complex K per staged tensor-core chunk in the large-plane kernel: its field
-// plane already takes more shared memory than the operand staging, so the
-// longer chunk (half the round trips of the fused kernel's 16) costs no
-// occupancy (48 measured no faster on the 256 x 64 planes)
+// Large-plane restore tiles: a contraction of at least kPipeMinK runs the
+// pipelined tile (tc_cgemm64_pipe: chunks of 16 with the next chunk's copies
+// and split overlapping the previous MMAs), a shorter one the single-buffer
+// tile with chunks of kTcKCLarge, whose fewer round trips win there (64^3
+// TT-4D, K = 541: yz 31.4 -> 29.0 ms pipelined; 64^3 H-Tucker, K <= 61:
+// 9.5 -> 10.5 ms pipelined, so it keeps the long chunks)
+constexpr int kPipeMinK = 128;
 constexpr int kTcKCLarge = 32;
+
+template <bool C_GLOBAL, bool BF16>
+__device__ __forceinline__ void tc_cgemm64_strided(TcState& s, float2* ring, int M, int N, int K, const float2* A,
+                                                   long long am, long long ak, const float2* B, long long bk,
+                                                   long long bn, float2* C, int ldc, float scale) {
+  if (K >= kPipeMinK) {
+    tc_cgemm64_pipe<C_GLOBAL, BF16>(s, ring, M, N, K, A, am, ak, B, bk, bn, C, ldc, scale);
+  } else {
+    tc_cgemm64<C_GLOBAL, BF16, kTcKCLarge>(
+        s, M, N, K, [&](int m, int k) { return A[m * am + k * ak]; },
+        [&](int k, int n) { return B[k * bk + n * bn]; }, C, ldc, scale);
+  }
+}
 
 template <bool BF16>   // BF16: BF16x3 products, else 3xTF32 (single TF32 with `single`)
 __global__ void __launch_bounds__(kThreads) cgemm_batched_tc_kernel(const GemmDesc* __restrict__ descs,
@@ -835,8 +851,12 @@ struct YZLLayout {
   static constexpr size_t plane_elems = (size_t)(N3 / 2) * PY + kWarps * XW;
   static size_t smem_bytes(int fmt, bool tc) {
     size_t work = sizeof(cx<R>) * plane_elems;
+    // tensor-core restore: two staging buffers and the operand ring of the
+    // pipelined tile, or the single-buffer tile's long chunks
+    constexpr size_t kPipe = tc_pipe_staging_bytes<false>() + kPipeRingBytes;
     constexpr size_t kStage = tc_smem_bytes<kTcKCLarge>();
-    if (fmt != 0 && tc && kStage > work) work = kStage;
+    constexpr size_t kTcWork = kPipe > kStage ? kPipe : kStage;
+    if (fmt != 0 && tc && kTcWork > work) work = kTcWork;
     return sizeof(cx<R>) * (N2 + N3) + work;
   }
   // global scratch per block: the slab, then G (rb x N2) of the Tucker-like
@@ -864,10 +884,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
     G = slot + (size_t)N3 * N2;
   }
   __shared__ uint32_t tmem_slot;
-  __shared__ uint64_t tc_bar;
+  __shared__ uint64_t tc_bar[2];
   TcState tc;
   if constexpr (TC != 0) {
-    tc = tc_setup(plane, &tc_bar, &tmem_slot);
+    tc = tc_setup(plane, &tc_bar[0], &tmem_slot, &tc_bar[1]);
     tc.single = P.tc_single != 0;
   }
   const int items = P.n1 * P.n_dir;
@@ -894,22 +914,26 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) yzl_kernel(Y
         const float2* U3f = reinterpret_cast<const float2*>(U3);
         float2* Gf = reinterpret_cast<float2*>(G);
         float2* Sf = reinterpret_cast<float2*>(slot);
-        // slab[y][z] tiles of 64 x 64
+        // slab[y][z] tiles of 64 x 64 on the tensor cores; the staging buffers
+        // (and the pipelined tile's operand ring) take the plane's space
+        constexpr bool kBf = TC == 2;
+        float2* ring = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(plane) +
+                                                 tc_pipe_staging_bytes<kBf>());
         if constexpr (FMT == 1) {
+          // G[c][y] = sum_b H_p[x][b][c] U2[y][b]; slab[y][z] = scale sum_c G[c][y] U3[z][c]
           for (int y0 = 0; y0 < N2; y0 += 64)
-            tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, rb, 64, ra, [&](int c, int b) { return Hf[b * rb + c]; },
-                       [&](int b, int y) { return U2f[(y0 + y) * ra + b]; }, Gf + y0, N2, 1.0f);
+            tc_cgemm64_strided<true, kBf>(tc, ring, rb, 64, ra, Hf, 1, rb, U2f + (size_t)y0 * ra, 1, ra, Gf + y0, N2,
+                                       1.0f);
           for (int y0 = 0; y0 < N2; y0 += 64)
             for (int z0 = 0; z0 < N3; z0 += 64)
-              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int y, int c) { return Gf[c * N2 + y0 + y]; },
-                         [&](int c, int z) { return U3f[(z0 + z) * rb + c]; }, Sf + (size_t)y0 * N3 + z0, N3,
-                         (float)P.scale);
+              tc_cgemm64_strided<true, kBf>(tc, ring, 64, 64, rb, Gf + y0, 1, N2, U3f + (size_t)z0 * rb, 1, rb,
+                                         Sf + (size_t)y0 * N3 + z0, N3, (float)P.scale);
         } else {
+          // slab[y][z] = scale sum_b T1[x][y][b] R_p[z][b]
           for (int y0 = 0; y0 < N2; y0 += 64)
             for (int z0 = 0; z0 < N3; z0 += 64)
-              tc_cgemm64<true, TC == 2, kTcKCLarge>(tc, 64, 64, rb, [&](int y, int b) { return Hf[(y0 + y) * rb + b]; },
-                         [&](int b, int z) { return U3f[(z0 + z) * rb + b]; }, Sf + (size_t)y0 * N3 + z0, N3,
-                         (float)P.scale);
+              tc_cgemm64_strided<true, kBf>(tc, ring, 64, 64, rb, Hf + (size_t)y0 * rb, rb, 1, U3f + (size_t)z0 * rb,
+                                         1, rb, Sf + (size_t)y0 * N3 + z0, N3, (float)P.scale);
         }
       } else {
         if constexpr (FMT == 1) {
